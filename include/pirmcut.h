@@ -1,0 +1,209 @@
+/*
+ * pirmcut.h -- C ABI of libpirmcut, a GB300 (sm_103a) implementation of the
+ * IRLS hot path of PIRMCut (Zhu & Gleich, "A Parallel Min-Cut Algorithm using
+ * Iteratively Reweighted Least Squares", arXiv:1501.03105).
+ *
+ * Problem (Section 2): an undirected graph G = (V, E) with capacities
+ * c(e) >= 0 and two terminals s != t; find S with s in S, t not in S that
+ * minimises cut(S, S-bar) = sum of c over edges with exactly one end in S.
+ *
+ * Method (Section 2.1, Algorithm 1): x^(0) solves the weighted least squares
+ * problem (Eq. constrained-wls) with W^(0) = C; then for l = 1..T each edge
+ * is reweighted from x^(l-1) (Eq. define-reweight-vector) and the reduced
+ * Laplacian system  L~ v = b  (Eq. reduced-laplacian-system: x_s = 1 and
+ * x_t = 0 held as Dirichlet values) is solved by Jacobi-preconditioned
+ * conjugate gradients (Section 3.1), warm-started from v^(l-1).  Finally a
+ * sweep cut over x (Section 3.3) rounds x to a cut.
+ *
+ * Conventions for every entry point:
+ *  - Vertices are 0..n-1 in the caller's numbering; s and t are ordinary
+ *    vertex ids.  Vectors of length n (x, side) use that numbering.
+ *  - mem_kind is PIRMCUT_MEM_HOST for host pointers (pageable or pinned) and
+ *    PIRMCUT_MEM_DEVICE for device pointers on the context's device.
+ *  - All GPU work of a context is ordered on the CUDA stream given at
+ *    creation (NULL = the legacy default stream).  Entry points that return
+ *    host scalars or fill host buffers synchronise that stream before they
+ *    return.
+ *  - The library copies every input; the caller keeps ownership of all
+ *    buffers it passes and of the outputs it receives.
+ *  - Errors are returned as pirmcut_status codes; nothing aborts.  The text
+ *    of the last error of a context is available from pirmcut_last_error().
+ *  - A context is not thread-safe: serialise calls on one context.
+ */
+#ifndef PIRMCUT_H
+#define PIRMCUT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pirmcut_ctx pirmcut_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  PIRMCUT_OK = 0,
+  PIRMCUT_EINVAL = 1,        /* invalid argument or malformed graph */
+  PIRMCUT_EDISCONNECTED = 2, /* a non-terminal component reaches neither s nor t
+                                through positive capacity: L~ would be singular
+                                (Prop. nonsingular) */
+  PIRMCUT_ENOMEM = 3,        /* host or device allocation failed */
+  PIRMCUT_ECUDA = 4,         /* a CUDA runtime call failed */
+  PIRMCUT_ENOCONV = 5,       /* PCG hit pcg_max_iter; the iterate is kept and usable */
+  PIRMCUT_ETIMEOUT = 6,      /* a bounded device-side wait gave up */
+  PIRMCUT_ENUMERIC = 7       /* NaN/Inf or a non-positive curvature p^T L~ p met */
+} pirmcut_status;
+
+enum { PIRMCUT_MEM_HOST = 0, PIRMCUT_MEM_DEVICE = 1 };
+
+/* Reweighting form.  NORTH_STAR: g_e = c_e / sqrt(d_e^2 + eps^2), d = x_u - x_v.
+ * PAPER: the literal Eq. (define-reweight-vector) + Eq. (reweighted-laplacian),
+ * w_e = sqrt((c_e d_e)^2 + eps^2) and g_e = c_e^2 / w_e. */
+enum { PIRMCUT_REWEIGHT_NORTH_STAR = 0, PIRMCUT_REWEIGHT_PAPER = 1 };
+
+/* Arithmetic of the PCG.  FP64: every vector, matrix value and reduction in
+ * FP64.  MIXED: FP32 matrix values and vectors in the inner PCG with
+ * compensated (twice-working-precision) inner products, and FP64 outer
+ * residuals with iterative refinement of an FP64 iterate. */
+enum { PIRMCUT_PREC_FP64 = 0, PIRMCUT_PREC_MIXED = 1 };
+
+/* Storage of L~.  DIA: symmetric diagonal storage, used when the non-terminal
+ * graph in the given numbering has few distinct index offsets (grids).  CSR:
+ * general rows.  AUTO picks DIA when it applies. */
+enum { PIRMCUT_FORMAT_AUTO = 0, PIRMCUT_FORMAT_DIA = 1, PIRMCUT_FORMAT_CSR = 2 };
+
+typedef struct {
+  int reweight_form;   /* PIRMCUT_REWEIGHT_*                                   */
+  int precision;       /* PIRMCUT_PREC_*                                       */
+  double pcg_tol;      /* stop when ||b - L~ v||_2 <= pcg_tol * ||b||_2        */
+  int pcg_max_iter;    /* PCG iteration cap per linear system                  */
+  int warm_start;      /* 1: start PCG of step l from v^(l-1); 0: from zero    */
+  int format;          /* PIRMCUT_FORMAT_*                                     */
+  int track_cut;       /* 1: run a sweep cut after every IRLS step and record
+                          its value in pirmcut_step_info.cut_value             */
+} pirmcut_options;
+
+typedef struct {
+  int step;            /* l (0 for x^(0))                                      */
+  int pcg_iters;       /* PCG iterations spent on this step's system           */
+  double eps;          /* smoothing parameter used (0 for step 0)             */
+  double rel_residual; /* final ||r||_2 / ||b||_2 of the PCG recurrence        */
+  double x_min, x_max; /* range of x over the non-terminals                   */
+  double cut_value;    /* sweep-cut value after the step if track_cut, else NaN */
+  double ms;           /* GPU time of the step in milliseconds                */
+  int status;          /* pirmcut_status of the step                          */
+} pirmcut_step_info;
+
+/* Fill *opt with the defaults: NORTH_STAR, FP64, pcg_tol 1e-10,
+ * pcg_max_iter 20000, warm_start 1, FORMAT_AUTO, track_cut 0. */
+void pirmcut_default_options(pirmcut_options* opt);
+
+/*
+ * Build a solver context for one s-t min-cut instance (Section 2; the
+ * non-terminal graph and terminal edges of Algorithm 1, step 1).
+ *
+ * n        number of vertices (>= 3 and < 2^31), terminals included.
+ * row_ptr  int64[n+1], CSR row offsets, row_ptr[0] = 0, non-decreasing.
+ * col      int32[row_ptr[n]], neighbour ids in [0, n).
+ * c        double[row_ptr[n]], capacities, finite and >= 0.
+ *          The CSR must be symmetric: each undirected edge {u, v} appears in
+ *          row u and in row v with the same total capacity.  Parallel entries
+ *          of one pair are summed; self-loops are rejected.
+ * s, t     source and sink, s != t.
+ * opt      options (NULL = defaults).
+ * mem_kind where row_ptr/col/c live.  Device input is first copied to the
+ *          host: the reduction and packing of the graph run on the host once.
+ * stream   cudaStream_t (as void*) on which all work of the context runs.
+ * out      receives the context on success, NULL on failure.
+ *
+ * The terminal edges are folded into two per-vertex capacity vectors
+ * (c(s,v), c(v,t)) plus the constant c(s,t); the non-terminal graph's
+ * structure is packed once and reused by every step (Section 3.1: the nonzero
+ * structure of L~ never changes).  The context starts with x^(0) unset.
+ * Errors: EINVAL (malformed input), EDISCONNECTED, ENOMEM, ECUDA.
+ */
+pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                              const double* c, int32_t s, int32_t t,
+                              const pirmcut_options* opt, int mem_kind, void* stream,
+                              pirmcut_ctx** out);
+
+/*
+ * Compute x^(0): the WLS solution with W^(0) = C (Section 2.1, Algorithm 1
+ * step 2), i.e. conductances g = c, solved by Jacobi-PCG from zero.
+ * info may be NULL.  Returns OK, ENOCONV (cap reached, iterate kept),
+ * ENUMERIC or ECUDA.
+ */
+pirmcut_status pirmcut_initial(pirmcut_ctx* ctx, pirmcut_step_info* info);
+
+/*
+ * One IRLS iteration (Section 2.1, Steps 1-2; Algorithm 1 step 4): reweight
+ * every edge from the current x with smoothing parameter eps > 0, assemble
+ * L~ and b (x_s = 1, x_t = 0 as Dirichlet values) together with the Jacobi
+ * diagonal, and solve L~ v = b by PCG warm-started from the current x
+ * (Section 3.1).  The current x (from pirmcut_initial, a previous step or
+ * pirmcut_set_x) is replaced by the new iterate.  info may be NULL.
+ * Errors: EINVAL (eps <= 0 or x unset), ENOCONV, ENUMERIC, ECUDA.
+ */
+pirmcut_status pirmcut_irls_step(pirmcut_ctx* ctx, double eps, pirmcut_step_info* info);
+
+/*
+ * Algorithm 1 steps 2-4 on one GPU: x^(0), then T IRLS steps with
+ * eps[0..T-1].  infos (may be NULL) receives T+1 records (x^(0) first).
+ * Returns the worst status met (ENOCONV if any system hit the cap).
+ */
+pirmcut_status pirmcut_solve(pirmcut_ctx* ctx, int T, const double* eps,
+                             pirmcut_step_info* infos);
+
+/*
+ * Sweep cut over the current x (Section 3.3; Algorithm 1 step 6).
+ * Non-terminals are ordered by x descending (vertex id ascending on ties);
+ * the prefixes that end between two strictly different x values, together
+ * with the empty and the full prefix, are the candidate source sides (s
+ * always in, t always out); the candidate of least cut value wins (the
+ * shorter prefix on exact ties of the evaluated values).
+ *
+ * side   uint8[n] (may be NULL): 1 for the source side, 0 for the sink side.
+ * value  (may be NULL) the exact FP64 cut value of the returned side.
+ * tau    (may be NULL) the threshold (x_(k) + x_(k+1))/2 between the last
+ *        vertex taken and the first one left (x_(0) = 1, x_(n~+1) = 0).
+ * Errors: EINVAL (x unset), ECUDA.
+ */
+pirmcut_status pirmcut_cut(pirmcut_ctx* ctx, uint8_t* side, double* value, double* tau,
+                           int mem_kind);
+
+/* Copy the current x (double[n], x_s = 1, x_t = 0) out.  EINVAL if x unset. */
+pirmcut_status pirmcut_get_x(pirmcut_ctx* ctx, double* x, int mem_kind);
+
+/* Set the current x from double[n] (entries at s and t are ignored): a warm
+ * start, a resume from a saved iterate, or a teacher-forced step. */
+pirmcut_status pirmcut_set_x(pirmcut_ctx* ctx, const double* x, int mem_kind);
+
+/*
+ * Replace the capacities of the instance while keeping its structure (a
+ * sequence of related problems, Section 6): c is double[nnz] in the CSR
+ * layout given to pirmcut_create.  The current x is kept as a warm start.
+ * Errors: EINVAL (non-finite, negative or asymmetric c), EDISCONNECTED, ECUDA.
+ */
+pirmcut_status pirmcut_update_weights(pirmcut_ctx* ctx, const double* c, int mem_kind);
+
+/* Sizes of the reduced problem: n~ (non-terminals), e~ (non-terminal
+ * undirected edges), and the storage format chosen (PIRMCUT_FORMAT_DIA/CSR). */
+pirmcut_status pirmcut_problem_size(const pirmcut_ctx* ctx, int64_t* n_nonterminal,
+                                    int64_t* n_edges, int* format);
+
+/* Number of kernel launches the context has issued so far (graph launches
+ * count each kernel node they run). */
+int64_t pirmcut_kernel_launches(const pirmcut_ctx* ctx);
+
+/* Text of the last error of ctx (or of the last failed create when ctx is NULL). */
+const char* pirmcut_last_error(const pirmcut_ctx* ctx);
+
+/* Free every host and device resource of ctx.  NULL is ignored. */
+void pirmcut_destroy(pirmcut_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIRMCUT_H */

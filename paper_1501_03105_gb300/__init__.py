@@ -1,0 +1,25 @@
+"""GB300 (sm_103a) implementation of the PIRMCut IRLS hot path.
+
+The compute path is ``libpirmcut.so`` (CUDA kernels behind the C ABI of
+``include/pirmcut.h``); :mod:`paper_1501_03105_gb300.binding` is its ctypes
+binding and :mod:`paper_1501_03105_gb300.build` compiles it.
+"""
+from .binding import (  # noqa: F401
+    Options,
+    StepInfo,
+    PirmcutError,
+    Solver,
+    pirmcut_default_options,
+    pirmcut_create,
+    pirmcut_initial,
+    pirmcut_irls_step,
+    pirmcut_solve,
+    pirmcut_cut,
+    pirmcut_get_x,
+    pirmcut_set_x,
+    pirmcut_update_weights,
+    pirmcut_problem_size,
+    pirmcut_kernel_launches,
+    pirmcut_last_error,
+    pirmcut_destroy,
+)

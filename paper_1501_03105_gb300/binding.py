@@ -1,0 +1,288 @@
+"""Thin ctypes binding of libpirmcut (the C ABI declared in include/pirmcut.h).
+
+Argument marshalling only: every step of the IRLS path runs in the library's
+CUDA kernels.  The functions carry the names of the C entry points.  Arrays
+are numpy arrays (host memory) or torch tensors (host or CUDA memory); the
+memory kind passed to the library follows the array.  Importing this module
+does not load the library; the first call does, and it raises
+``RuntimeError`` when ``libpirmcut.so`` has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpirmcut.so")
+
+MEM_HOST, MEM_DEVICE = 0, 1
+REWEIGHT_NORTH_STAR, REWEIGHT_PAPER = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+FORMAT_AUTO, FORMAT_DIA, FORMAT_CSR = 0, 1, 2
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "EDISCONNECTED", 3: "ENOMEM", 4: "ECUDA",
+          5: "ENOCONV", 6: "ETIMEOUT", 7: "ENUMERIC"}
+OK, EINVAL, EDISCONNECTED, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, ENUMERIC = range(8)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("reweight_form", ctypes.c_int), ("precision", ctypes.c_int),
+                ("pcg_tol", ctypes.c_double), ("pcg_max_iter", ctypes.c_int),
+                ("warm_start", ctypes.c_int), ("format", ctypes.c_int),
+                ("track_cut", ctypes.c_int)]
+
+
+class StepInfo(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int), ("pcg_iters", ctypes.c_int), ("eps", ctypes.c_double),
+                ("rel_residual", ctypes.c_double), ("x_min", ctypes.c_double),
+                ("x_max", ctypes.c_double), ("cut_value", ctypes.c_double),
+                ("ms", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class PirmcutError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+_LIB = None
+_P = ctypes.c_void_p
+
+
+def lib() -> ctypes.CDLL:
+    """Load libpirmcut.so (once)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run paper_1501_03105_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    i32, i64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    L.pirmcut_default_options.argtypes = [ctypes.POINTER(Options)]
+    L.pirmcut_default_options.restype = None
+    L.pirmcut_create.argtypes = [i64, _P, _P, _P, i32, i32, ctypes.POINTER(Options), ctypes.c_int,
+                                 _P, ctypes.POINTER(_P)]
+    L.pirmcut_create.restype = ctypes.c_int
+    L.pirmcut_initial.argtypes = [_P, ctypes.POINTER(StepInfo)]
+    L.pirmcut_initial.restype = ctypes.c_int
+    L.pirmcut_irls_step.argtypes = [_P, dbl, ctypes.POINTER(StepInfo)]
+    L.pirmcut_irls_step.restype = ctypes.c_int
+    L.pirmcut_solve.argtypes = [_P, ctypes.c_int, _P, _P]
+    L.pirmcut_solve.restype = ctypes.c_int
+    L.pirmcut_cut.argtypes = [_P, _P, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.c_int]
+    L.pirmcut_cut.restype = ctypes.c_int
+    L.pirmcut_get_x.argtypes = [_P, _P, ctypes.c_int]
+    L.pirmcut_get_x.restype = ctypes.c_int
+    L.pirmcut_set_x.argtypes = [_P, _P, ctypes.c_int]
+    L.pirmcut_set_x.restype = ctypes.c_int
+    L.pirmcut_update_weights.argtypes = [_P, _P, ctypes.c_int]
+    L.pirmcut_update_weights.restype = ctypes.c_int
+    L.pirmcut_problem_size.argtypes = [_P, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                       ctypes.POINTER(ctypes.c_int)]
+    L.pirmcut_problem_size.restype = ctypes.c_int
+    L.pirmcut_kernel_launches.argtypes = [_P]
+    L.pirmcut_kernel_launches.restype = i64
+    L.pirmcut_last_error.argtypes = [_P]
+    L.pirmcut_last_error.restype = ctypes.c_char_p
+    L.pirmcut_destroy.argtypes = [_P]
+    L.pirmcut_destroy.restype = None
+    _LIB = L
+    return L
+
+
+def _ptr(a, dtype):
+    """(pointer, mem_kind, keepalive) of a numpy array or torch tensor of ``dtype``."""
+    if a is None:
+        return None, MEM_HOST, None
+    if isinstance(a, np.ndarray):
+        arr = np.ascontiguousarray(a, dtype=dtype)
+        return arr.ctypes.data, MEM_HOST, arr
+    import torch  # only for tensors
+    if not isinstance(a, torch.Tensor):
+        arr = np.ascontiguousarray(np.asarray(a), dtype=dtype)
+        return arr.ctypes.data, MEM_HOST, arr
+    tdt = {np.float64: torch.float64, np.int64: torch.int64, np.int32: torch.int32,
+           np.uint8: torch.uint8}[np.dtype(dtype).type]
+    if a.dtype != tdt or not a.is_contiguous():
+        raise TypeError(f"tensor must be contiguous {tdt}")
+    return a.data_ptr(), (MEM_DEVICE if a.is_cuda else MEM_HOST), a
+
+
+def _check(h, status: int, soft=(OK,)):
+    if status in soft:
+        return status
+    msg = lib().pirmcut_last_error(h)
+    raise PirmcutError(status, msg.decode() if msg else "")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def pirmcut_default_options(**kw) -> Options:
+    o = Options()
+    lib().pirmcut_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def pirmcut_create(n, row_ptr, col, c, s, t, opt: Options | None = None, stream=None):
+    """Create a context; returns the opaque handle (int).  Raises PirmcutError."""
+    prp, k1, a1 = _ptr(row_ptr, np.int64)
+    pcl, k2, a2 = _ptr(col, np.int32)
+    pc, k3, a3 = _ptr(c, np.float64)
+    if len({k1, k2, k3}) != 1:
+        raise ValueError("row_ptr, col and c must live in the same memory")
+    h = _P()
+    st = lib().pirmcut_create(int(n), prp, pcl, pc, int(s), int(t),
+                              ctypes.byref(opt) if opt is not None else None, k1,
+                              _stream_ptr(stream), ctypes.byref(h))
+    _check(None, st)
+    del a1, a2, a3
+    return h.value
+
+
+def pirmcut_initial(h) -> StepInfo:
+    info = StepInfo()
+    _check(h, lib().pirmcut_initial(h, ctypes.byref(info)), soft=(OK, ENOCONV))
+    return info
+
+
+def pirmcut_irls_step(h, eps: float) -> StepInfo:
+    info = StepInfo()
+    _check(h, lib().pirmcut_irls_step(h, float(eps), ctypes.byref(info)), soft=(OK, ENOCONV))
+    return info
+
+
+def pirmcut_solve(h, T: int, eps) -> list:
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    if eps.shape != (T,):
+        raise ValueError("need one eps per step")
+    infos = (StepInfo * (T + 1))()
+    _check(h, lib().pirmcut_solve(h, int(T), eps.ctypes.data, ctypes.addressof(infos)),
+           soft=(OK, ENOCONV))
+    return list(infos)
+
+
+def pirmcut_cut(h, side=None, n=None):
+    """Sweep cut.  ``side``: a uint8 output array/tensor of length n, or None
+    (a numpy array of length ``n`` is allocated when n is given).
+    Returns (side, value, tau)."""
+    if side is None and n is not None:
+        side = np.zeros(int(n), dtype=np.uint8)
+    ps, kind, keep = _ptr(side, np.uint8)
+    if isinstance(side, np.ndarray) and keep is not side:
+        raise TypeError("side must be a contiguous uint8 array")
+    val = ctypes.c_double()
+    tau = ctypes.c_double()
+    _check(h, lib().pirmcut_cut(h, ps, ctypes.byref(val), ctypes.byref(tau), kind))
+    return side, val.value, tau.value
+
+
+def pirmcut_get_x(h, out):
+    p, kind, keep = _ptr(out, np.float64)
+    if isinstance(out, np.ndarray) and keep is not out:
+        raise TypeError("out must be a contiguous float64 array")
+    _check(h, lib().pirmcut_get_x(h, p, kind))
+    return out
+
+
+def pirmcut_set_x(h, x):
+    p, kind, keep = _ptr(x, np.float64)
+    _check(h, lib().pirmcut_set_x(h, p, kind))
+
+
+def pirmcut_update_weights(h, c):
+    p, kind, keep = _ptr(c, np.float64)
+    _check(h, lib().pirmcut_update_weights(h, p, kind))
+
+
+def pirmcut_problem_size(h):
+    a, b, f = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+    _check(h, lib().pirmcut_problem_size(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(f)))
+    return a.value, b.value, f.value
+
+
+def pirmcut_kernel_launches(h) -> int:
+    return int(lib().pirmcut_kernel_launches(h))
+
+
+def pirmcut_last_error(h=None) -> str:
+    m = lib().pirmcut_last_error(h)
+    return m.decode() if m else ""
+
+
+def pirmcut_destroy(h):
+    lib().pirmcut_destroy(h)
+
+
+class Solver:
+    """Convenience owner of one context (same calls, object style)."""
+
+    def __init__(self, graph, opt: Options | None = None, stream=None, **kw):
+        if opt is None:
+            opt = pirmcut_default_options(**kw)
+        self.n = int(graph.n)
+        self.h = pirmcut_create(graph.n, graph.row_ptr, graph.col, graph.c, graph.s, graph.t,
+                                opt, stream)
+
+    def initial(self):
+        return pirmcut_initial(self.h)
+
+    def irls_step(self, eps):
+        return pirmcut_irls_step(self.h, eps)
+
+    def solve(self, T, eps):
+        return pirmcut_solve(self.h, T, eps)
+
+    def cut(self, side=None):
+        return pirmcut_cut(self.h, side, n=self.n if side is None else None)
+
+    def get_x(self, out=None):
+        if out is None:
+            out = np.empty(self.n, dtype=np.float64)
+        return pirmcut_get_x(self.h, out)
+
+    def set_x(self, x):
+        pirmcut_set_x(self.h, x)
+
+    def update_weights(self, c):
+        pirmcut_update_weights(self.h, c)
+
+    def problem_size(self):
+        return pirmcut_problem_size(self.h)
+
+    def kernel_launches(self):
+        return pirmcut_kernel_launches(self.h)
+
+    def close(self):
+        if self.h:
+            pirmcut_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

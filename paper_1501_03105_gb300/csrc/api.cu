@@ -1,0 +1,515 @@
+// extern "C" entry points of libpirmcut (declared in include/pirmcut.h).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+#include "pirmcut.h"
+
+struct pirmcut_ctx {
+  pirmcut::Ctx c;
+  // pinned host staging for small transfers
+  pirmcut::StepCounters* h_ctr = nullptr;
+  double* h_eps = nullptr;
+  double* h_result = nullptr;  // 4
+  std::vector<cudaEvent_t> events;
+  int next_step = 0;           // IRLS index of the next step record
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+using pirmcut::Ctx;
+
+pirmcut_status fail(pirmcut_ctx* h, pirmcut_status st, const std::string& msg) {
+  if (h) h->c.err = msg;
+  else g_create_error = msg;
+  return st;
+}
+
+pirmcut_status cuda_fail(pirmcut_ctx* h, cudaError_t e, const char* where) {
+  return fail(h, e == cudaErrorMemoryAllocation ? PIRMCUT_ENOMEM : PIRMCUT_ECUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call, where)                          \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, sizeof(T) * count);
+}
+
+void free_device(Ctx& c) {
+  void* ps[] = {c.cdia, c.gdia, c.rp, c.col, c.cval, c.gval, c.cs, c.ct, c.x, c.r, c.p,
+                c.q, c.diag, c.dinv, c.partials, c.S, c.C, c.eps_list, c.recs, c.xfull,
+                c.side_full};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  pirmcut::sweep_free(c);
+  if (c.g_init) cudaGraphExecDestroy(c.g_init);
+  if (c.g_step) cudaGraphExecDestroy(c.g_step);
+  if (c.g_cut) cudaGraphExecDestroy(c.g_cut);
+  if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
+  if (c.h_recs) cudaFreeHost(c.h_recs);
+}
+
+pirmcut_status check_options(const pirmcut_options& o, std::string* msg) {
+  if (o.reweight_form != PIRMCUT_REWEIGHT_NORTH_STAR && o.reweight_form != PIRMCUT_REWEIGHT_PAPER) {
+    *msg = "unknown reweight_form";
+    return PIRMCUT_EINVAL;
+  }
+  if (o.precision != PIRMCUT_PREC_FP64) {
+    *msg = "only PIRMCUT_PREC_FP64 is available in this build";
+    return PIRMCUT_EINVAL;
+  }
+  if (!(o.pcg_tol > 0.0) || !std::isfinite(o.pcg_tol)) {
+    *msg = "pcg_tol must be finite and > 0";
+    return PIRMCUT_EINVAL;
+  }
+  if (o.pcg_max_iter < 0 || o.pcg_max_iter > 100000000) {
+    *msg = "pcg_max_iter must be in [0, 1e8]";
+    return PIRMCUT_EINVAL;
+  }
+  if (o.format < PIRMCUT_FORMAT_AUTO || o.format > PIRMCUT_FORMAT_CSR) {
+    *msg = "unknown format";
+    return PIRMCUT_EINVAL;
+  }
+  return PIRMCUT_OK;
+}
+
+// copy a caller buffer (host or device) into a host vector
+template <class T>
+cudaError_t to_host(std::vector<T>& dst, const T* src, size_t count, int mem_kind) {
+  dst.resize(count);
+  if (count == 0) return cudaSuccess;
+  if (mem_kind == PIRMCUT_MEM_DEVICE)
+    return cudaMemcpy(dst.data(), src, sizeof(T) * count, cudaMemcpyDeviceToHost);
+  std::memcpy(dst.data(), src, sizeof(T) * count);
+  return cudaSuccess;
+}
+
+pirmcut_status upload_problem(pirmcut_ctx* h) {
+  Ctx& c = h->c;
+  const pirmcut::HostGraph& g = c.hg;
+  cudaStream_t st = c.stream;
+  if (c.format == PIRMCUT_FORMAT_DIA) {
+    CK(h, cudaMemcpyAsync(c.cdia, g.cdia.data(), sizeof(double) * g.cdia.size(), cudaMemcpyHostToDevice, st), "upload");
+  } else {
+    CK(h, cudaMemcpyAsync(c.rp, g.rp.data(), sizeof(int64_t) * g.rp.size(), cudaMemcpyHostToDevice, st), "upload");
+    CK(h, cudaMemcpyAsync(c.col, g.col.data(), sizeof(int32_t) * g.col.size(), cudaMemcpyHostToDevice, st), "upload");
+    CK(h, cudaMemcpyAsync(c.cval, g.cval.data(), sizeof(double) * g.cval.size(), cudaMemcpyHostToDevice, st), "upload");
+  }
+  CK(h, cudaMemcpyAsync(c.cs, g.cs.data(), sizeof(double) * g.cs.size(), cudaMemcpyHostToDevice, st), "upload");
+  CK(h, cudaMemcpyAsync(c.ct, g.ct.data(), sizeof(double) * g.ct.size(), cudaMemcpyHostToDevice, st), "upload");
+  CK(h, cudaStreamSynchronize(st), "upload");
+  return PIRMCUT_OK;
+}
+
+pirmcut_status ensure_capacity(pirmcut_ctx* h, int steps) {
+  Ctx& c = h->c;
+  if (c.eps_cap < steps) {
+    if (c.eps_list) cudaFree(c.eps_list);
+    c.eps_list = nullptr;
+    c.eps_cap = 0;
+    int cap = 64;
+    while (cap < steps) cap *= 2;
+    CK(h, dalloc(&c.eps_list, cap), "eps buffer");
+    c.eps_cap = cap;
+    // graphs bake the eps pointer: rebuild
+    if (c.g_init) { cudaGraphExecDestroy(c.g_init); c.g_init = nullptr; }
+    if (c.g_step) { cudaGraphExecDestroy(c.g_step); c.g_step = nullptr; }
+  }
+  if (c.rec_cap < steps + 1) {
+    if (c.recs) cudaFree(c.recs);
+    c.recs = nullptr;
+    c.rec_cap = 0;
+    int cap = 64;
+    while (cap < steps + 1) cap *= 2;
+    CK(h, dalloc(&c.recs, cap), "record buffer");
+    c.rec_cap = cap;
+    if (c.h_recs) cudaFreeHost(c.h_recs);
+    c.h_recs = nullptr;
+    CK(h, cudaHostAlloc((void**)&c.h_recs, sizeof(pirmcut::StepRec) * cap, cudaHostAllocDefault), "record buffer");
+    c.h_rec_cap = cap;
+    if (c.g_init) { cudaGraphExecDestroy(c.g_init); c.g_init = nullptr; }
+    if (c.g_step) { cudaGraphExecDestroy(c.g_step); c.g_step = nullptr; }
+    if (c.g_cut) { cudaGraphExecDestroy(c.g_cut); c.g_cut = nullptr; }
+  }
+  return PIRMCUT_OK;
+}
+
+pirmcut_status ensure_graphs(pirmcut_ctx* h, bool need_cut) {
+  Ctx& c = h->c;
+  if (!c.g_init) CK(h, pirmcut::build_step_graph(c, true, &c.g_init, &c.nodes_init), "building the x0 graph");
+  if (!c.g_step) CK(h, pirmcut::build_step_graph(c, false, &c.g_step, &c.nodes_step), "building the step graph");
+  if (need_cut) {
+    CK(h, pirmcut::sweep_alloc(c), "sweep buffers");
+    if (!c.g_cut) CK(h, pirmcut::build_cut_graph(c, &c.g_cut, &c.nodes_cut), "building the sweep graph");
+  }
+  return PIRMCUT_OK;
+}
+
+cudaEvent_t event_at(pirmcut_ctx* h, size_t i) {
+  while (h->events.size() <= i) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->events.push_back(e);
+  }
+  return h->events[i];
+}
+
+void fill_info(const Ctx& c, const pirmcut::StepRec& r, float ms, pirmcut_step_info* info) {
+  info->step = r.step;
+  info->pcg_iters = r.iters;
+  info->eps = r.eps;
+  info->rel_residual = r.bb > 0.0 ? std::sqrt(r.rr / r.bb) : 0.0;
+  info->x_min = r.xmin;
+  info->x_max = r.xmax;
+  info->cut_value = r.cut;
+  info->ms = ms;
+  int st = r.status;
+  if (st == PIRMCUT_OK && r.iters >= c.opt.pcg_max_iter && r.bb > 0.0 &&
+      !(r.rr <= c.opt.pcg_tol * c.opt.pcg_tol * r.bb))
+    st = PIRMCUT_ENOCONV;
+  info->status = st;
+}
+
+// Run x^(0) (when with_initial) and the eps steps already in eps_list[0..T).
+pirmcut_status run_steps(pirmcut_ctx* h, bool with_initial, int T, int first_step,
+                         pirmcut_step_info* infos) {
+  Ctx& c = h->c;
+  const int nrec = T + (with_initial ? 1 : 0);
+  if (nrec == 0) return PIRMCUT_OK;
+  pirmcut_status ps = ensure_graphs(h, c.opt.track_cut != 0);
+  if (ps != PIRMCUT_OK) return ps;
+  h->h_ctr->eps_idx = 0;
+  h->h_ctr->rec_idx = 0;
+  h->h_ctr->step = first_step;
+  h->h_ctr->pad = 0;
+  CK(h, cudaMemcpyAsync(c.C, h->h_ctr, sizeof(pirmcut::StepCounters), cudaMemcpyHostToDevice, c.stream), "counters");
+  cudaEvent_t e0 = event_at(h, 0);
+  if (!e0) return fail(h, PIRMCUT_ECUDA, "cudaEventCreate failed");
+  CK(h, cudaEventRecord(e0, c.stream), "event");
+  for (int k = 0; k < nrec; ++k) {
+    const bool init = with_initial && k == 0;
+    CK(h, cudaGraphLaunch(init ? c.g_init : c.g_step, c.stream), "graph launch");
+    c.launches += init ? c.nodes_init : c.nodes_step;
+    if (c.opt.track_cut) {
+      CK(h, cudaGraphLaunch(c.g_cut, c.stream), "graph launch");
+      c.launches += c.nodes_cut;
+    }
+    cudaEvent_t ek = event_at(h, size_t(k) + 1);
+    if (!ek) return fail(h, PIRMCUT_ECUDA, "cudaEventCreate failed");
+    CK(h, cudaEventRecord(ek, c.stream), "event");
+  }
+  CK(h, cudaMemcpyAsync(c.h_recs, c.recs, sizeof(pirmcut::StepRec) * nrec, cudaMemcpyDeviceToHost, c.stream), "records");
+  CK(h, cudaStreamSynchronize(c.stream), "solve");
+  pirmcut_status worst = PIRMCUT_OK;
+  for (int k = 0; k < nrec; ++k) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->events[k], h->events[k + 1]);
+    pirmcut_step_info info;
+    fill_info(c, c.h_recs[k], ms, &info);
+    c.launches += 3LL * info.pcg_iters;
+    if (infos) infos[k] = info;
+    if (info.status == PIRMCUT_ENUMERIC) worst = PIRMCUT_ENUMERIC;
+    else if (info.status == PIRMCUT_ENOCONV && worst == PIRMCUT_OK) worst = PIRMCUT_ENOCONV;
+  }
+  c.x_set = true;
+  if (worst == PIRMCUT_ENUMERIC) return fail(h, worst, "NaN/Inf or loss of positive definiteness in PCG");
+  if (worst == PIRMCUT_ENOCONV) return fail(h, worst, "PCG reached pcg_max_iter");
+  return PIRMCUT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pirmcut_default_options(pirmcut_options* opt) {
+  if (!opt) return;
+  opt->reweight_form = PIRMCUT_REWEIGHT_NORTH_STAR;
+  opt->precision = PIRMCUT_PREC_FP64;
+  opt->pcg_tol = 1e-10;
+  opt->pcg_max_iter = 20000;
+  opt->warm_start = 1;
+  opt->format = PIRMCUT_FORMAT_AUTO;
+  opt->track_cut = 0;
+}
+
+pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                              const double* c, int32_t s, int32_t t,
+                              const pirmcut_options* opt, int mem_kind, void* stream,
+                              pirmcut_ctx** out) {
+  if (!out) return fail(nullptr, PIRMCUT_EINVAL, "out must not be NULL");
+  *out = nullptr;
+  if (mem_kind != PIRMCUT_MEM_HOST && mem_kind != PIRMCUT_MEM_DEVICE)
+    return fail(nullptr, PIRMCUT_EINVAL, "unknown mem_kind");
+  if (n < 3 || n >= (int64_t(1) << 31)) return fail(nullptr, PIRMCUT_EINVAL, "n must be in [3, 2^31)");
+  if (!row_ptr) return fail(nullptr, PIRMCUT_EINVAL, "row_ptr must not be NULL");
+  pirmcut_options o;
+  pirmcut_default_options(&o);
+  if (opt) o = *opt;
+  std::string msg;
+  if (check_options(o, &msg) != PIRMCUT_OK) return fail(nullptr, PIRMCUT_EINVAL, msg);
+
+  std::vector<int64_t> rp;
+  std::vector<int32_t> cl;
+  std::vector<double> cv;
+  cudaError_t e = to_host(rp, row_ptr, size_t(n) + 1, mem_kind);
+  if (e != cudaSuccess) return fail(nullptr, PIRMCUT_ECUDA, std::string("reading row_ptr: ") + cudaGetErrorString(e));
+  const int64_t nnz = rp[n];
+  if (nnz < 0 || rp[0] != 0) return fail(nullptr, PIRMCUT_EINVAL, "bad row_ptr");
+  if (nnz > 0 && (!col || !c)) return fail(nullptr, PIRMCUT_EINVAL, "col and c must not be NULL");
+  e = to_host(cl, col, size_t(nnz), mem_kind);
+  if (e == cudaSuccess) e = to_host(cv, c, size_t(nnz), mem_kind);
+  if (e != cudaSuccess) return fail(nullptr, PIRMCUT_ECUDA, std::string("reading the graph: ") + cudaGetErrorString(e));
+
+  pirmcut_ctx* h = new (std::nothrow) pirmcut_ctx();
+  if (!h) return fail(nullptr, PIRMCUT_ENOMEM, "out of host memory");
+  Ctx& cx = h->c;
+  pirmcut_status ps = pirmcut::reduce_graph(n, rp.data(), cl.data(), cv.data(), s, t, o.format, &cx.hg, &msg);
+  if (ps != PIRMCUT_OK) {
+    delete h;
+    return fail(nullptr, ps, msg);
+  }
+  cx.opt = o;
+  cx.nt = cx.hg.nt;
+  cx.format = cx.hg.format;
+  cx.K = cx.hg.K;
+  cx.dd.nt = cx.nt;
+  for (int k = 0; k < pirmcut::kMaxDiag; ++k) cx.dd.off[k] = cx.hg.off[k];
+  cx.group = cx.hg.group;
+  cx.in_rp = std::move(rp);
+  cx.in_col = std::move(cl);
+  cx.stream = reinterpret_cast<cudaStream_t>(stream);
+  auto bail = [&](cudaError_t err, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(err);
+    free_device(cx);
+    if (h->h_ctr) cudaFreeHost(h->h_ctr);
+    delete h;
+    return fail(nullptr, err == cudaErrorMemoryAllocation ? PIRMCUT_ENOMEM : PIRMCUT_ECUDA, m);
+  };
+  if ((e = cudaGetDevice(&cx.device)) != cudaSuccess) return bail(e, "cudaGetDevice");
+  if ((e = cudaStreamCreateWithFlags(&cx.cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(e, "cudaStreamCreate");
+  const size_t nt = size_t(cx.nt);
+  if (cx.format == PIRMCUT_FORMAT_DIA) {
+    if ((e = dalloc(&cx.cdia, size_t(cx.K) * nt)) != cudaSuccess) return bail(e, "cudaMalloc");
+    if ((e = dalloc(&cx.gdia, size_t(cx.K) * nt)) != cudaSuccess) return bail(e, "cudaMalloc");
+  } else {
+    const size_t m = cx.hg.col.size();
+    if ((e = dalloc(&cx.rp, nt + 1)) != cudaSuccess) return bail(e, "cudaMalloc");
+    if ((e = dalloc(&cx.col, m)) != cudaSuccess) return bail(e, "cudaMalloc");
+    if ((e = dalloc(&cx.cval, m)) != cudaSuccess) return bail(e, "cudaMalloc");
+    if ((e = dalloc(&cx.gval, m)) != cudaSuccess) return bail(e, "cudaMalloc");
+  }
+  double** vecs[] = {&cx.cs, &cx.ct, &cx.x, &cx.r, &cx.p, &cx.q, &cx.diag, &cx.dinv};
+  for (double** v : vecs)
+    if ((e = dalloc(v, nt)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = dalloc(&cx.partials, 4 * size_t(pirmcut::kMaxBlocks))) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = dalloc(&cx.S, 1)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = dalloc(&cx.C, 1)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = cudaMemset(cx.S, 0, sizeof(pirmcut::PcgState))) != cudaSuccess) return bail(e, "cudaMemset");
+  if ((e = cudaMemset(cx.C, 0, sizeof(pirmcut::StepCounters))) != cudaSuccess) return bail(e, "cudaMemset");
+  if ((e = cudaHostAlloc((void**)&h->h_ctr, sizeof(pirmcut::StepCounters) + 8 * sizeof(double),
+                         cudaHostAllocDefault)) != cudaSuccess)
+    return bail(e, "cudaHostAlloc");
+  h->h_eps = reinterpret_cast<double*>(h->h_ctr + 1);
+  h->h_result = h->h_eps + 2;
+  ps = upload_problem(h);
+  if (ps != PIRMCUT_OK) {
+    std::string m = cx.err;
+    free_device(cx);
+    cudaFreeHost(h->h_ctr);
+    delete h;
+    return fail(nullptr, ps, m);
+  }
+  ps = ensure_capacity(h, 1);
+  if (ps != PIRMCUT_OK) {
+    std::string m = cx.err;
+    free_device(cx);
+    cudaFreeHost(h->h_ctr);
+    delete h;
+    return fail(nullptr, ps, m);
+  }
+  *out = h;
+  return PIRMCUT_OK;
+}
+
+pirmcut_status pirmcut_initial(pirmcut_ctx* h, pirmcut_step_info* info) {
+  if (!h) return fail(nullptr, PIRMCUT_EINVAL, "ctx is NULL");
+  pirmcut_step_info tmp;
+  pirmcut_status st = run_steps(h, true, 0, 0, info ? info : &tmp);
+  if (st == PIRMCUT_OK || st == PIRMCUT_ENOCONV) h->next_step = 1;
+  return st;
+}
+
+pirmcut_status pirmcut_irls_step(pirmcut_ctx* h, double eps, pirmcut_step_info* info) {
+  if (!h) return fail(nullptr, PIRMCUT_EINVAL, "ctx is NULL");
+  Ctx& c = h->c;
+  if (!c.x_set) return fail(h, PIRMCUT_EINVAL, "x is not set: call pirmcut_initial or pirmcut_set_x first");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(h, PIRMCUT_EINVAL, "eps must be finite and > 0");
+  *h->h_eps = eps;
+  CK(h, cudaMemcpyAsync(c.eps_list, h->h_eps, sizeof(double), cudaMemcpyHostToDevice, c.stream), "eps");
+  pirmcut_step_info tmp;
+  pirmcut_status st = run_steps(h, false, 1, h->next_step, info ? info : &tmp);
+  if (st == PIRMCUT_OK || st == PIRMCUT_ENOCONV) h->next_step += 1;
+  return st;
+}
+
+pirmcut_status pirmcut_solve(pirmcut_ctx* h, int T, const double* eps, pirmcut_step_info* infos) {
+  if (!h) return fail(nullptr, PIRMCUT_EINVAL, "ctx is NULL");
+  Ctx& c = h->c;
+  if (T < 0) return fail(h, PIRMCUT_EINVAL, "T must be >= 0");
+  if (T > 0 && !eps) return fail(h, PIRMCUT_EINVAL, "eps must not be NULL");
+  for (int l = 0; l < T; ++l)
+    if (!(eps[l] > 0.0) || !std::isfinite(eps[l])) return fail(h, PIRMCUT_EINVAL, "every eps must be finite and > 0");
+  pirmcut_status ps = ensure_capacity(h, T);
+  if (ps != PIRMCUT_OK) return ps;
+  if (T > 0) CK(h, cudaMemcpyAsync(c.eps_list, eps, sizeof(double) * T, cudaMemcpyHostToDevice, c.stream), "eps");
+  std::vector<pirmcut_step_info> tmp;
+  if (!infos) {
+    tmp.resize(size_t(T) + 1);
+    infos = tmp.data();
+  }
+  pirmcut_status st = run_steps(h, true, T, 0, infos);
+  if (st == PIRMCUT_OK || st == PIRMCUT_ENOCONV) h->next_step = T + 1;
+  return st;
+}
+
+pirmcut_status pirmcut_cut(pirmcut_ctx* h, uint8_t* side, double* value, double* tau, int mem_kind) {
+  if (!h) return fail(nullptr, PIRMCUT_EINVAL, "ctx is NULL");
+  Ctx& c = h->c;
+  if (!c.x_set) return fail(h, PIRMCUT_EINVAL, "x is not set");
+  if (mem_kind != PIRMCUT_MEM_HOST && mem_kind != PIRMCUT_MEM_DEVICE)
+    return fail(h, PIRMCUT_EINVAL, "unknown mem_kind");
+  pirmcut_status ps = ensure_graphs(h, true);
+  if (ps != PIRMCUT_OK) return ps;
+  CK(h, cudaGraphLaunch(c.g_cut, c.stream), "graph launch");
+  c.launches += c.nodes_cut;
+  if (side) {
+    if (mem_kind == PIRMCUT_MEM_DEVICE) {
+      CK(h, pirmcut::launch_side_full(c, side), "side");
+    } else {
+      if (!c.side_full) CK(h, dalloc(&c.side_full, size_t(c.hg.n)), "cudaMalloc");
+      CK(h, pirmcut::launch_side_full(c, c.side_full), "side");
+      CK(h, cudaMemcpyAsync(side, c.side_full, size_t(c.hg.n), cudaMemcpyDeviceToHost, c.stream), "side");
+    }
+  }
+  CK(h, cudaMemcpyAsync(h->h_result, c.sw.result, 4 * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "result");
+  CK(h, cudaStreamSynchronize(c.stream), "cut");
+  if (value) *value = h->h_result[1];
+  if (tau) *tau = h->h_result[2];
+  return PIRMCUT_OK;
+}
+
+pirmcut_status pirmcut_get_x(pirmcut_ctx* h, double* x, int mem_kind) {
+  if (!h) return fail(nullptr, PIRMCUT_EINVAL, "ctx is NULL");
+  Ctx& c = h->c;
+  if (!c.x_set) return fail(h, PIRMCUT_EINVAL, "x is not set");
+  if (!x) return fail(h, PIRMCUT_EINVAL, "x must not be NULL");
+  if (mem_kind == PIRMCUT_MEM_DEVICE) {
+    CK(h, pirmcut::launch_scatter_x(c, x), "get_x");
+  } else if (mem_kind == PIRMCUT_MEM_HOST) {
+    if (!c.xfull) CK(h, dalloc(&c.xfull, size_t(c.hg.n)), "cudaMalloc");
+    CK(h, pirmcut::launch_scatter_x(c, c.xfull), "get_x");
+    CK(h, cudaMemcpyAsync(x, c.xfull, sizeof(double) * c.hg.n, cudaMemcpyDeviceToHost, c.stream), "get_x");
+  } else {
+    return fail(h, PIRMCUT_EINVAL, "unknown mem_kind");
+  }
+  CK(h, cudaStreamSynchronize(c.stream), "get_x");
+  return PIRMCUT_OK;
+}
+
+pirmcut_status pirmcut_set_x(pirmcut_ctx* h, const double* x, int mem_kind) {
+  if (!h) return fail(nullptr, PIRMCUT_EINVAL, "ctx is NULL");
+  Ctx& c = h->c;
+  if (!x) return fail(h, PIRMCUT_EINVAL, "x must not be NULL");
+  if (mem_kind == PIRMCUT_MEM_DEVICE) {
+    CK(h, pirmcut::launch_gather_x(c, x), "set_x");
+  } else if (mem_kind == PIRMCUT_MEM_HOST) {
+    if (!c.xfull) CK(h, dalloc(&c.xfull, size_t(c.hg.n)), "cudaMalloc");
+    CK(h, cudaMemcpyAsync(c.xfull, x, sizeof(double) * c.hg.n, cudaMemcpyHostToDevice, c.stream), "set_x");
+    CK(h, pirmcut::launch_gather_x(c, c.xfull), "set_x");
+  } else {
+    return fail(h, PIRMCUT_EINVAL, "unknown mem_kind");
+  }
+  CK(h, cudaStreamSynchronize(c.stream), "set_x");
+  c.x_set = true;
+  return PIRMCUT_OK;
+}
+
+pirmcut_status pirmcut_update_weights(pirmcut_ctx* h, const double* cnew, int mem_kind) {
+  if (!h) return fail(nullptr, PIRMCUT_EINVAL, "ctx is NULL");
+  Ctx& c = h->c;
+  if (mem_kind != PIRMCUT_MEM_HOST && mem_kind != PIRMCUT_MEM_DEVICE)
+    return fail(h, PIRMCUT_EINVAL, "unknown mem_kind");
+  const int64_t nnz = c.in_rp.back();
+  if (nnz > 0 && !cnew) return fail(h, PIRMCUT_EINVAL, "c must not be NULL");
+  std::vector<double> cv;
+  CK(h, to_host(cv, cnew, size_t(nnz), mem_kind), "reading c");
+  pirmcut::HostGraph ng;
+  std::string msg;
+  pirmcut_status ps = pirmcut::reduce_graph(c.hg.n, c.in_rp.data(), c.in_col.data(), cv.data(),
+                                            c.hg.s, c.hg.t, c.format, &ng, &msg);
+  if (ps != PIRMCUT_OK) return fail(h, ps, msg);
+  bool same = ng.format == c.format && ng.nt == c.nt && ng.K == c.K;
+  for (int k = 0; same && k < c.K; ++k) same = ng.off[k] == c.hg.off[k];
+  if (same && c.format == PIRMCUT_FORMAT_CSR) same = ng.col.size() == c.hg.col.size();
+  if (!same) return fail(h, PIRMCUT_EINVAL, "the new capacities change the stored structure");
+  if (c.format == PIRMCUT_FORMAT_CSR) {
+    ng.rp.swap(c.hg.rp);  // structure unchanged; keep the uploaded copy
+    ng.col.swap(c.hg.col);
+  }
+  c.hg = std::move(ng);
+  if (c.format == PIRMCUT_FORMAT_CSR) {
+    CK(h, cudaMemcpyAsync(c.cval, c.hg.cval.data(), sizeof(double) * c.hg.cval.size(), cudaMemcpyHostToDevice, c.stream), "upload");
+  } else {
+    CK(h, cudaMemcpyAsync(c.cdia, c.hg.cdia.data(), sizeof(double) * c.hg.cdia.size(), cudaMemcpyHostToDevice, c.stream), "upload");
+  }
+  CK(h, cudaMemcpyAsync(c.cs, c.hg.cs.data(), sizeof(double) * c.nt, cudaMemcpyHostToDevice, c.stream), "upload");
+  CK(h, cudaMemcpyAsync(c.ct, c.hg.ct.data(), sizeof(double) * c.nt, cudaMemcpyHostToDevice, c.stream), "upload");
+  CK(h, cudaStreamSynchronize(c.stream), "upload");
+  // the sweep graph bakes c(s,t) and cut(0)
+  if (c.g_cut) {
+    cudaGraphExecDestroy(c.g_cut);
+    c.g_cut = nullptr;
+  }
+  return PIRMCUT_OK;
+}
+
+pirmcut_status pirmcut_problem_size(const pirmcut_ctx* h, int64_t* n_nonterminal, int64_t* n_edges,
+                                    int* format) {
+  if (!h) return PIRMCUT_EINVAL;
+  if (n_nonterminal) *n_nonterminal = h->c.nt;
+  if (n_edges) *n_edges = h->c.hg.n_edges;
+  if (format) *format = h->c.format;
+  return PIRMCUT_OK;
+}
+
+int64_t pirmcut_kernel_launches(const pirmcut_ctx* h) { return h ? h->c.launches : 0; }
+
+const char* pirmcut_last_error(const pirmcut_ctx* h) {
+  return h ? h->c.err.c_str() : g_create_error.c_str();
+}
+
+void pirmcut_destroy(pirmcut_ctx* h) {
+  if (!h) return;
+  if (h->c.stream) cudaStreamSynchronize(h->c.stream);
+  free_device(h->c);
+  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  if (h->h_ctr) cudaFreeHost(h->h_ctr);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+// Device-side building blocks shared by the kernels of libpirmcut:
+// deterministic block reductions (fixed shuffle trees, no float atomics),
+// the "last block finishes the reduction" pattern, and the device-resident
+// PCG state.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace pirmcut {
+
+constexpr int kThreads = 256;       // block size of the streaming kernels
+constexpr int kMaxBlocks = 152 * 8; // cap on grid size (152 SMs x 8 resident blocks)
+
+// Device-resident state of one PCG solve.  Written only by the last block of
+// a kernel (or by the host before a solve); read by every block of the next.
+struct PcgState {
+  double rz;        // (r, z) of the current iterate
+  double rr;        // ||r||^2
+  double bb;        // ||b||^2
+  double pq;        // (p, L~ p)
+  double alpha, beta;
+  double tol2;      // pcg_tol^2
+  double xmin, xmax;
+  int iters;        // iterations done in this solve
+  int maxit;
+  int stop_req;     // set when the recurrence has converged / hit the cap / broke down
+  int stopped;      // set by the first kernel of the iteration after stop_req
+  int status;       // PIRMCUT_OK or PIRMCUT_ENUMERIC
+  int pad;
+  unsigned int counter[4];  // last-block counters (one per reduction site)
+};
+
+// Geometry of the DIA storage (upper diagonals only; L~ is symmetric).
+struct DiaDesc {
+  int64_t nt;
+  int64_t off[kMaxDiag];
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum NV doubles over the block; the result is valid in thread 0.
+// Fixed tree: the sum is bit-identical from run to run.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double sm[32 * NV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) v[j] = warp_sum(v[j]);
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) sm[wid * NV + j] = v[j];
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = warp_sum(lane < nw ? sm[lane * NV + j] : 0.0);
+  }
+  __syncthreads();
+}
+
+// Each block contributes v (NV doubles); the last block to arrive sums the
+// per-block partials in block order and returns true in all of its threads,
+// with the totals in tot (valid in thread 0).  partials holds NV * gridDim.x
+// doubles.  No thread ever waits on another block.
+template <int NV>
+__device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials,
+                                         unsigned int* counter, double (&tot)[NV]) {
+  __shared__ unsigned int s_last;
+  block_sum<NV>(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) partials[j * gridDim.x + blockIdx.x] = v[j];
+    __threadfence();
+    const unsigned int prev = atomicAdd(counter, 1u);
+    s_last = (prev == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) acc[j] = 0.0;
+  for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) acc[j] += __ldcg(partials + j * gridDim.x + b);
+  }
+  block_sum<NV>(acc);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) tot[j] = acc[j];
+    *counter = 0u;
+  }
+  return true;
+}
+
+// Conductance of an edge with capacity c and voltage difference d
+// (Eq. define-reweight-vector with Eq. reweighted-laplacian).
+// form 0: c / sqrt(d^2 + eps^2); form 1: c^2 / sqrt((c d)^2 + eps^2).
+__device__ __forceinline__ double conductance(double c, double d, double eps2, int form) {
+  if (form == PIRMCUT_REWEIGHT_PAPER) {
+    const double cd = c * d;
+    return c * c * rsqrt(fma(cd, cd, eps2));
+  }
+  return c * rsqrt(fma(d, d, eps2));
+}
+
+inline int grid_for(int64_t n, int threads = kThreads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > kMaxBlocks) b = kMaxBlocks;
+  if (b < 1) b = 1;
+  return int(b);
+}
+
+}  // namespace pirmcut

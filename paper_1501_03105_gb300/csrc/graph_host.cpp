@@ -1,0 +1,298 @@
+// Host-side reduction of the input graph: validation, removal of the
+// terminals (the non-terminal graph G~ and the terminal edges of Section 2),
+// the solvability check of Prop. (nonsingular), and the packing of L~'s
+// fixed structure (Section 3.1) into DIA or CSR storage.  Runs once per
+// instance inside pirmcut_create / pirmcut_update_weights.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <thread>
+#include <utility>
+
+#include "internal.h"
+
+namespace pirmcut {
+
+namespace {
+
+struct Entry {
+  int32_t col;
+  double c;
+};
+
+// Run fn(lo, hi) over [0, n) split across the host's cores.
+template <class F>
+void parallel_for(int64_t n, F fn) {
+  unsigned hw = std::thread::hardware_concurrency();
+  int64_t nth = std::max<int64_t>(1, std::min<int64_t>(hw ? hw : 1, 64));
+  if (n < 65536) nth = 1;
+  std::vector<std::thread> th;
+  for (int64_t k = 0; k < nth; ++k) {
+    int64_t lo = n * k / nth, hi = n * (k + 1) / nth;
+    if (k + 1 == nth) {
+      fn(lo, hi);
+    } else {
+      th.emplace_back([=] { fn(lo, hi); });
+    }
+  }
+  for (auto& x : th) x.join();
+}
+
+}  // namespace
+
+pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                            const double* c, int32_t s, int32_t t, int format_req,
+                            HostGraph* out, std::string* err) {
+  if (n < 3 || n >= (int64_t(1) << 31)) {
+    *err = "n must be in [3, 2^31)";
+    return PIRMCUT_EINVAL;
+  }
+  if (s < 0 || t < 0 || s >= n || t >= n || s == t) {
+    *err = "s and t must be distinct vertices";
+    return PIRMCUT_EINVAL;
+  }
+  if (!row_ptr || row_ptr[0] != 0) {
+    *err = "row_ptr[0] must be 0";
+    return PIRMCUT_EINVAL;
+  }
+  for (int64_t v = 0; v < n; ++v) {
+    if (row_ptr[v + 1] < row_ptr[v]) {
+      *err = "row_ptr must be non-decreasing";
+      return PIRMCUT_EINVAL;
+    }
+  }
+  const int64_t nnz = row_ptr[n];
+  if (nnz > 0 && (!col || !c)) {
+    *err = "col and c must be non-null";
+    return PIRMCUT_EINVAL;
+  }
+  HostGraph& g = *out;
+  g = HostGraph();
+  g.n = n;
+  g.nt = n - 2;
+  g.s = s;
+  g.t = t;
+  const int64_t nt = g.nt;
+
+  // ---- per-row pass: validate entries, fold terminal edges, merge parallel
+  // entries of the non-terminal rows (sorted by reduced column).
+  std::vector<int64_t> cnt(nt + 1, 0);
+  std::vector<double> cs(nt, 0.0), ct(nt, 0.0), cs_from_s(nt, 0.0), ct_from_t(nt, 0.0);
+  double cst_s = 0.0, cst_t = 0.0;
+  // pass 1 (parallel): count merged non-terminal entries per row, validate
+  std::vector<uint8_t> row_bad(n, 0);
+  parallel_for(n, [&](int64_t lo, int64_t hi) {
+    std::vector<Entry> buf;
+    for (int64_t v = lo; v < hi; ++v) {
+      const int64_t b = row_ptr[v], e = row_ptr[v + 1];
+      for (int64_t k = b; k < e; ++k) {
+        const int32_t u = col[k];
+        const double w = c[k];
+        if (u < 0 || u >= n) { row_bad[v] = 1; break; }
+        if (u == v) { row_bad[v] = 2; break; }
+        if (!std::isfinite(w) || w < 0.0) { row_bad[v] = 3; break; }
+      }
+      if (row_bad[v] || v == s || v == t) continue;
+      buf.clear();
+      for (int64_t k = b; k < e; ++k) {
+        const int32_t u = col[k];
+        if (u == s || u == t) continue;
+        buf.push_back({(int32_t)reduced_index(u, s, t), c[k]});
+      }
+      bool sorted = true;
+      for (size_t k = 1; k < buf.size(); ++k) sorted &= buf[k - 1].col <= buf[k].col;
+      if (!sorted)
+        std::stable_sort(buf.begin(), buf.end(),
+                         [](const Entry& a, const Entry& b2) { return a.col < b2.col; });
+      int64_t m = 0;
+      for (size_t k = 0; k < buf.size(); ++k)
+        if (k == 0 || buf[k].col != buf[k - 1].col) ++m;
+      cnt[reduced_index(v, s, t) + 1] = m;
+    }
+  });
+  for (int64_t v = 0; v < n; ++v) {
+    if (row_bad[v] == 1) { *err = "column index out of range in row " + std::to_string(v); return PIRMCUT_EINVAL; }
+    if (row_bad[v] == 2) { *err = "self-loop at vertex " + std::to_string(v); return PIRMCUT_EINVAL; }
+    if (row_bad[v] == 3) { *err = "capacity not finite or negative in row " + std::to_string(v); return PIRMCUT_EINVAL; }
+  }
+  std::vector<int64_t> rp(nt + 1, 0);
+  for (int64_t i = 0; i < nt; ++i) rp[i + 1] = rp[i] + cnt[i + 1];
+  const int64_t mnt = rp[nt];
+  std::vector<int32_t> rc(mnt);
+  std::vector<double> rv(mnt);
+  // pass 2 (parallel): fill merged rows and the terminal capacities
+  parallel_for(n, [&](int64_t lo, int64_t hi) {
+    std::vector<Entry> buf;
+    for (int64_t v = lo; v < hi; ++v) {
+      if (v == s || v == t) continue;
+      const int64_t i = reduced_index(v, s, t);
+      buf.clear();
+      double a = 0.0, z = 0.0;
+      for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+        const int32_t u = col[k];
+        if (u == s) a += c[k];
+        else if (u == t) z += c[k];
+        else buf.push_back({(int32_t)reduced_index(u, s, t), c[k]});
+      }
+      cs[i] = a;
+      ct[i] = z;
+      std::stable_sort(buf.begin(), buf.end(),
+                       [](const Entry& x, const Entry& y) { return x.col < y.col; });
+      int64_t o = rp[i];
+      for (size_t k = 0; k < buf.size(); ++k) {
+        if (k > 0 && buf[k].col == buf[k - 1].col) {
+          rv[o - 1] += buf[k].c;
+        } else {
+          rc[o] = buf[k].col;
+          rv[o] = buf[k].c;
+          ++o;
+        }
+      }
+    }
+  });
+  // terminal rows
+  for (int64_t k = row_ptr[s]; k < row_ptr[s + 1]; ++k) {
+    const int32_t u = col[k];
+    if (u == t) cst_s += c[k];
+    else cs_from_s[reduced_index(u, s, t)] += c[k];
+  }
+  for (int64_t k = row_ptr[t]; k < row_ptr[t + 1]; ++k) {
+    const int32_t u = col[k];
+    if (u == s) cst_t += c[k];
+    else ct_from_t[reduced_index(u, s, t)] += c[k];
+  }
+  // ---- symmetry: every pair carries the same total capacity in both rows
+  if (cst_s != cst_t) {
+    *err = "CSR is not symmetric (s-t edge)";
+    return PIRMCUT_EINVAL;
+  }
+  for (int64_t i = 0; i < nt; ++i) {
+    if (cs[i] != cs_from_s[i] || ct[i] != ct_from_t[i]) {
+      *err = "CSR is not symmetric (terminal edge of vertex " +
+             std::to_string(original_index(i, s, t)) + ")";
+      return PIRMCUT_EINVAL;
+    }
+  }
+  std::vector<uint8_t> asym(nt, 0);
+  parallel_for(nt, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i) {
+      for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+        const int64_t j = rc[k];
+        const int32_t* b = rc.data() + rp[j];
+        const int32_t* e = rc.data() + rp[j + 1];
+        const int32_t* f = std::lower_bound(b, e, (int32_t)i);
+        if (f == e || *f != i || rv[rp[j] + (f - b)] != rv[k]) {
+          asym[i] = 1;
+          break;
+        }
+      }
+    }
+  });
+  for (int64_t i = 0; i < nt; ++i) {
+    if (asym[i]) {
+      *err = "CSR is not symmetric (row " + std::to_string(original_index(i, s, t)) + ")";
+      return PIRMCUT_EINVAL;
+    }
+  }
+  // ---- solvability (Prop. nonsingular): every non-terminal reaches a vertex
+  // with a positive terminal capacity through positive-capacity edges.
+  {
+    std::vector<uint8_t> seen(nt, 0);
+    std::vector<int64_t> stack;
+    stack.reserve(1024);
+    for (int64_t i = 0; i < nt; ++i) {
+      if (cs[i] > 0.0 || ct[i] > 0.0) {
+        seen[i] = 1;
+        stack.push_back(i);
+      }
+    }
+    while (!stack.empty()) {
+      const int64_t i = stack.back();
+      stack.pop_back();
+      for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+        const int64_t j = rc[k];
+        if (!seen[j] && rv[k] > 0.0) {
+          seen[j] = 1;
+          stack.push_back(j);
+        }
+      }
+    }
+    for (int64_t i = 0; i < nt; ++i) {
+      if (!seen[i]) {
+        *err = "disconnected: vertex " + std::to_string(original_index(i, s, t)) +
+               " reaches neither s nor t through positive capacity";
+        return PIRMCUT_EDISCONNECTED;
+      }
+    }
+  }
+  g.n_edges = mnt / 2;
+  g.c_st = cst_s;
+  double sc = 0.0;
+  for (int64_t i = 0; i < nt; ++i) sc += cs[i];
+  g.sum_cs = sc + cst_s;
+  g.cs = std::move(cs);
+  g.ct = std::move(ct);
+
+  // ---- storage choice: DIA when the upper entries use few distinct offsets
+  // and fill most of those diagonals, else CSR.
+  int K = 0;
+  int64_t offs[kMaxDiag + 1];
+  bool dia_ok = true;
+  for (int64_t i = 0; i < nt && dia_ok; ++i) {
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+      const int64_t o = int64_t(rc[k]) - i;
+      if (o <= 0) continue;
+      int f = 0;
+      while (f < K && offs[f] != o) ++f;
+      if (f == K) {
+        if (K == kMaxDiag) {
+          dia_ok = false;
+          break;
+        }
+        offs[K++] = o;
+      }
+    }
+  }
+  if (dia_ok && K > 0) {
+    std::sort(offs, offs + K);
+    const double fill = double(g.n_edges) / (double(K) * double(nt));
+    dia_ok = fill >= 0.5;
+  }
+  if (K == 0) dia_ok = false;
+  if (format_req == PIRMCUT_FORMAT_DIA && !dia_ok) {
+    *err = "DIA storage requested but the graph has more than 8 offsets or sparse diagonals";
+    return PIRMCUT_EINVAL;
+  }
+  const bool use_dia = (format_req == PIRMCUT_FORMAT_DIA) ||
+                       (format_req == PIRMCUT_FORMAT_AUTO && dia_ok);
+  if (use_dia) {
+    g.format = PIRMCUT_FORMAT_DIA;
+    g.K = K;
+    for (int k = 0; k < K; ++k) g.off[k] = offs[k];
+    g.cdia.assign(size_t(K) * nt, 0.0);
+    parallel_for(nt, [&](int64_t lo, int64_t hi) {
+      for (int64_t i = lo; i < hi; ++i) {
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+          const int64_t o = int64_t(rc[k]) - i;
+          if (o <= 0) continue;
+          int f = 0;
+          while (g.off[f] != o) ++f;
+          g.cdia[size_t(f) * nt + i] = rv[k];
+        }
+      }
+    });
+  } else {
+    g.format = PIRMCUT_FORMAT_CSR;
+    g.rp = std::move(rp);
+    g.col = std::move(rc);
+    g.cval = std::move(rv);
+    const double avg = nt ? double(mnt) / double(nt) : 0.0;
+    int grp = 1;
+    while (grp < 32 && grp < avg) grp *= 2;
+    g.group = grp;
+  }
+  return PIRMCUT_OK;
+}
+
+}  // namespace pirmcut

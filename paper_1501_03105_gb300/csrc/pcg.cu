@@ -1,0 +1,600 @@
+// FP64 kernels of one IRLS step on the GPU and the CUDA graph that runs it.
+//
+// A step is (Section 2.1, Steps 1-2; Section 3.1):
+//   reweight   g_e from x^(l-1) for every stored edge  (Eq. define-reweight-vector)
+//   assemble   terminal conductances, b_v = g(s,v), Jacobi diagonal and its
+//              inverse, r = b - L~ x, z = D^-1 r, p = z, (r,z), ||r||^2, ||b||^2
+//              (Eq. reduced-laplacian-system with x_s = 1, x_t = 0)
+//   PCG loop   a CUDA-graph WHILE node whose body is three kernels:
+//                spmv      q = L~ p, (p, q) -> alpha
+//                update_r  r -= alpha q, z = D^-1 r, (r, z), ||r||^2 -> beta, stop?
+//                update_xp x += alpha p, p = z + beta p; clears the loop
+//                          condition once stop is requested
+//   step_end   range of x, per-step record.
+// Every reduction is a fixed-order tree over fixed per-thread row sets, so
+// results are bit-identical from run to run.  Scalars (alpha, beta, the stop
+// flag) live in device memory; the host never synchronises inside a solve.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "ctx.h"
+
+namespace pirmcut {
+
+namespace {
+
+__device__ __forceinline__ int64_t gtid() {
+  return int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+}
+__device__ __forceinline__ int64_t gstride() { return int64_t(gridDim.x) * blockDim.x; }
+
+// ---------------------------------------------------------------------------
+// reweighting (Step 1)
+// ---------------------------------------------------------------------------
+
+template <int K>
+__global__ void __launch_bounds__(kThreads)
+k_reweight_dia(DiaDesc d, const double* __restrict__ c, const double* __restrict__ x,
+               const double* __restrict__ eps_list, const StepCounters* __restrict__ C,
+               int form, double* __restrict__ g) {
+  const int64_t nt = d.nt;
+  const double eps = eps_list[C->eps_idx];
+  const double eps2 = eps * eps;
+  for (int64_t i = gtid(); i < nt; i += gstride()) {
+    const double xi = x[i];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int64_t j = i + d.off[k];
+      double gg = 0.0;
+      if (j < nt) gg = conductance(c[k * nt + i], xi - x[j], eps2, form);
+      g[k * nt + i] = gg;
+    }
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(kThreads)
+k_reweight_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+               const double* __restrict__ c, const double* __restrict__ x,
+               const double* __restrict__ eps_list, const StepCounters* __restrict__ C,
+               int form, double* __restrict__ g) {
+  const double eps = eps_list[C->eps_idx];
+  const double eps2 = eps * eps;
+  const int lane = threadIdx.x % G;
+  const int64_t ng = gstride() / G;
+  for (int64_t i = gtid() / G; i < nt; i += ng) {
+    const double xi = x[i];
+    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G)
+      g[e] = conductance(c[e], xi - x[col[e]], eps2, form);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// assembly of L~, b and the Jacobi preconditioner; initial residual
+// ---------------------------------------------------------------------------
+
+struct AssembleArgs {
+  const double* cs;
+  const double* ct;
+  const double* x;
+  const double* eps_list;
+  const StepCounters* C;
+  int form;
+  int initial;     // W^(0) = C: conductances are the capacities
+  int zero_start;  // PCG starts from v = 0 (residual = b)
+  double tol2;
+  int maxit;
+  double* diag;
+  double* dinv;
+  double* r;
+  double* p;
+  double* partials;
+  PcgState* S;
+  cudaGraphConditionalHandle h;
+};
+
+__device__ __forceinline__ void assemble_finish(const AssembleArgs& a, double rz, double rr,
+                                                double bb) {
+  double v[3] = {rz, rr, bb}, tot[3];
+  if (grid_sum<3>(v, a.partials, &a.S->counter[0], tot) && threadIdx.x == 0) {
+    PcgState* S = a.S;
+    S->rz = tot[0];
+    S->rr = tot[1];
+    S->bb = tot[2];
+    S->tol2 = a.tol2;
+    S->maxit = a.maxit;
+    S->iters = 0;
+    S->stopped = 0;
+    S->status = PIRMCUT_OK;
+    S->alpha = 0.0;
+    S->beta = 0.0;
+    int stop = (tot[1] <= a.tol2 * tot[2]) || a.maxit <= 0 || tot[2] == 0.0;
+    if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) {
+      stop = 1;
+      S->status = PIRMCUT_ENUMERIC;
+    }
+    S->stop_req = stop;
+    cudaGraphSetConditional(a.h, stop ? 0u : 1u);
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads)
+k_assemble_dia(DiaDesc d, const double* __restrict__ g, AssembleArgs a) {
+  const int64_t nt = d.nt;
+  const double eps = a.initial ? 0.0 : a.eps_list[a.C->eps_idx];
+  const double eps2 = eps * eps;
+  const double* __restrict__ x = a.x;
+  double rz = 0.0, rr = 0.0, bb = 0.0;
+  for (int64_t i = gtid(); i < nt; i += gstride()) {
+    const double xi = x[i];
+    double gs = a.cs[i], gt = a.ct[i];
+    if (!a.initial) {
+      gs = conductance(gs, 1.0 - xi, eps2, a.form);
+      gt = conductance(gt, xi, eps2, a.form);
+    }
+    double sum = gs + gt, ax = 0.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int64_t o = d.off[k];
+      if (i + o < nt) {
+        const double gg = g[k * nt + i];
+        sum += gg;
+        ax = fma(gg, x[i + o], ax);
+      }
+      if (i >= o) {
+        const double gg = g[k * nt + i - o];
+        sum += gg;
+        ax = fma(gg, x[i - o], ax);
+      }
+    }
+    const double di = 1.0 / sum;
+    const double ri = a.zero_start ? gs : gs - fma(sum, xi, -ax);
+    const double zi = di * ri;
+    a.diag[i] = sum;
+    a.dinv[i] = di;
+    a.r[i] = ri;
+    a.p[i] = zi;
+    rz = fma(ri, zi, rz);
+    rr = fma(ri, ri, rr);
+    bb = fma(gs, gs, bb);
+  }
+  assemble_finish(a, rz, rr, bb);
+}
+
+template <int G>
+__global__ void __launch_bounds__(kThreads)
+k_assemble_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+               const double* __restrict__ g, AssembleArgs a) {
+  const double eps = a.initial ? 0.0 : a.eps_list[a.C->eps_idx];
+  const double eps2 = eps * eps;
+  const double* __restrict__ x = a.x;
+  const int lane = threadIdx.x % G;
+  const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
+  const int64_t ng = gstride() / G;
+  double rz = 0.0, rr = 0.0, bb = 0.0;
+  for (int64_t i = gtid() / G; i < nt; i += ng) {
+    double sum = 0.0, ax = 0.0;
+    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) {
+      const double gg = g[e];
+      sum += gg;
+      ax = fma(gg, x[col[e]], ax);
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+      sum += __shfl_down_sync(mask, sum, o, G);
+      ax += __shfl_down_sync(mask, ax, o, G);
+    }
+    if (lane == 0) {
+      const double xi = x[i];
+      double gs = a.cs[i], gt = a.ct[i];
+      if (!a.initial) {
+        gs = conductance(gs, 1.0 - xi, eps2, a.form);
+        gt = conductance(gt, xi, eps2, a.form);
+      }
+      sum += gs + gt;
+      const double di = 1.0 / sum;
+      const double ri = a.zero_start ? gs : gs - fma(sum, xi, -ax);
+      const double zi = di * ri;
+      a.diag[i] = sum;
+      a.dinv[i] = di;
+      a.r[i] = ri;
+      a.p[i] = zi;
+      rz = fma(ri, zi, rz);
+      rr = fma(ri, ri, rr);
+      bb = fma(gs, gs, bb);
+    }
+  }
+  assemble_finish(a, rz, rr, bb);
+}
+
+// ---------------------------------------------------------------------------
+// PCG iteration
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void spmv_finish(double pq, double* partials, PcgState* S) {
+  double v[1] = {pq}, tot[1];
+  if (grid_sum<1>(v, partials, &S->counter[1], tot) && threadIdx.x == 0) {
+    const double a = S->rz / tot[0];
+    S->pq = tot[0];
+    if (!(tot[0] > 0.0) || !isfinite(a)) {
+      S->alpha = 0.0;
+      S->status = PIRMCUT_ENUMERIC;
+      S->stop_req = 1;
+    } else {
+      S->alpha = a;
+    }
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads)
+k_spmv_dia(DiaDesc d, const double* __restrict__ g, const double* __restrict__ diag,
+           const double* __restrict__ p, double* __restrict__ q, double* partials,
+           PcgState* S) {
+  if (S->stop_req) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) S->stopped = 1;
+    return;
+  }
+  const int64_t nt = d.nt;
+  double pq = 0.0;
+  for (int64_t i = gtid(); i < nt; i += gstride()) {
+    const double pi = p[i];
+    double acc = diag[i] * pi;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int64_t o = d.off[k];
+      if (i + o < nt) acc = fma(-g[k * nt + i], p[i + o], acc);
+      if (i >= o) acc = fma(-g[k * nt + i - o], p[i - o], acc);
+    }
+    q[i] = acc;
+    pq = fma(pi, acc, pq);
+  }
+  spmv_finish(pq, partials, S);
+}
+
+template <int G>
+__global__ void __launch_bounds__(kThreads)
+k_spmv_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+           const double* __restrict__ g, const double* __restrict__ diag,
+           const double* __restrict__ p, double* __restrict__ q, double* partials,
+           PcgState* S) {
+  if (S->stop_req) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) S->stopped = 1;
+    return;
+  }
+  const int lane = threadIdx.x % G;
+  const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
+  const int64_t ng = gstride() / G;
+  double pq = 0.0;
+  for (int64_t i = gtid() / G; i < nt; i += ng) {
+    double acc = 0.0;
+    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) acc = fma(-g[e], p[col[e]], acc);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(mask, acc, o, G);
+    if (lane == 0) {
+      const double pi = p[i];
+      acc = fma(diag[i], pi, acc);
+      q[i] = acc;
+      pq = fma(pi, acc, pq);
+    }
+  }
+  spmv_finish(pq, partials, S);
+}
+
+// r -= alpha q; z = D^-1 r is written over q; (r, z) and ||r||^2 -> beta, stop.
+__global__ void __launch_bounds__(kThreads)
+k_update_r(int64_t nt, double* __restrict__ qz, const double* __restrict__ dinv,
+           double* __restrict__ r, double* partials, PcgState* S) {
+  if (S->stop_req) return;
+  const double alpha = S->alpha;
+  double rz = 0.0, rr = 0.0;
+  for (int64_t i = gtid(); i < nt; i += gstride()) {
+    const double ri = fma(-alpha, qz[i], r[i]);
+    const double zi = dinv[i] * ri;
+    r[i] = ri;
+    qz[i] = zi;
+    rz = fma(ri, zi, rz);
+    rr = fma(ri, ri, rr);
+  }
+  double v[2] = {rz, rr}, tot[2];
+  if (grid_sum<2>(v, partials, &S->counter[2], tot) && threadIdx.x == 0) {
+    const int it = S->iters + 1;
+    S->iters = it;
+    const double beta = tot[0] / S->rz;
+    S->beta = beta;
+    S->rz = tot[0];
+    S->rr = tot[1];
+    int stop = (tot[1] <= S->tol2 * S->bb) || it >= S->maxit;
+    if (!isfinite(tot[1]) || !isfinite(beta)) {
+      stop = 1;
+      S->status = PIRMCUT_ENUMERIC;
+      S->beta = 0.0;
+    }
+    S->stop_req = stop;
+  }
+}
+
+// x += alpha p; p = z + beta p (z read from the q buffer).  Ends the loop
+// once a stop was requested in this or an earlier kernel.
+__global__ void __launch_bounds__(kThreads)
+k_update_xp(int64_t nt, double* __restrict__ x, double* __restrict__ p,
+            const double* __restrict__ z, PcgState* S, cudaGraphConditionalHandle h) {
+  if (!S->stopped) {
+    const double alpha = S->alpha, beta = S->beta;
+    for (int64_t i = gtid(); i < nt; i += gstride()) {
+      const double pi = p[i];
+      x[i] = fma(alpha, pi, x[i]);
+      p[i] = fma(beta, pi, z[i]);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && S->stop_req) cudaGraphSetConditional(h, 0u);
+}
+
+// ---------------------------------------------------------------------------
+// end of a step: range of x, record
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_step_end(int64_t nt, double* __restrict__ x, PcgState* S, StepCounters* C, StepRec* recs,
+           const double* __restrict__ eps_list, int consumes_eps, double* partials) {
+  __shared__ double smn[32], smx[32];
+  __shared__ unsigned int s_last;
+  const bool zero = S->bb == 0.0;  // b = 0: the solution of L~ v = b is v = 0
+  double mn = INFINITY, mx = -INFINITY;
+  for (int64_t i = gtid(); i < nt; i += gstride()) {
+    double xi = x[i];
+    if (zero) {
+      xi = 0.0;
+      x[i] = 0.0;
+    }
+    mn = fmin(mn, xi);
+    mx = fmax(mx, xi);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  mn = warp_min(mn);
+  mx = warp_max(mx);
+  if (lane == 0) {
+    smn[wid] = mn;
+    smx[wid] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      mn = fmin(mn, smn[w]);
+      mx = fmax(mx, smx[w]);
+    }
+    partials[blockIdx.x] = mn;
+    partials[gridDim.x + blockIdx.x] = mx;
+    __threadfence();
+    s_last = (atomicAdd(&S->counter[3], 1u) == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  mn = INFINITY;
+  mx = -INFINITY;
+  for (unsigned int b = 0; b < gridDim.x; ++b) {
+    mn = fmin(mn, __ldcg(partials + b));
+    mx = fmax(mx, __ldcg(partials + gridDim.x + b));
+  }
+  S->counter[3] = 0u;
+  S->xmin = mn;
+  S->xmax = mx;
+  StepRec rec;
+  rec.step = C->step;
+  rec.iters = S->iters;
+  rec.eps = consumes_eps ? eps_list[C->eps_idx] : 0.0;
+  rec.rr = S->rr;
+  rec.bb = S->bb;
+  rec.xmin = mn;
+  rec.xmax = mx;
+  rec.cut = NAN;
+  rec.status = S->status;
+  rec.pad = 0;
+  recs[C->rec_idx] = rec;
+  C->rec_idx += 1;
+  C->step += 1;
+  if (consumes_eps) C->eps_idx += 1;
+}
+
+// ---------------------------------------------------------------------------
+// x in the caller's numbering <-> reduced x
+// ---------------------------------------------------------------------------
+
+__global__ void k_scatter_x(int64_t nt, int32_t s, int32_t t, const double* __restrict__ xr,
+                            double* __restrict__ xf) {
+  const int64_t a = s < t ? s : t, b = s < t ? t : s;
+  for (int64_t i = gtid(); i < nt; i += gstride()) {
+    int64_t v = i;
+    if (v >= a) ++v;
+    if (v >= b) ++v;
+    xf[v] = xr[i];
+  }
+  if (gtid() == 0) {
+    xf[s] = 1.0;
+    xf[t] = 0.0;
+  }
+}
+
+__global__ void k_gather_x(int64_t nt, int32_t s, int32_t t, const double* __restrict__ xf,
+                           double* __restrict__ xr) {
+  const int64_t a = s < t ? s : t, b = s < t ? t : s;
+  for (int64_t i = gtid(); i < nt; i += gstride()) {
+    int64_t v = i;
+    if (v >= a) ++v;
+    if (v >= b) ++v;
+    xr[i] = xf[v];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers (templates dispatched on the DIA width / CSR group size)
+// ---------------------------------------------------------------------------
+
+
+#define PIRMCUT_DISPATCH_K(KVAR, CALL) \
+  switch (KVAR) {                      \
+    case 1: { constexpr int KK = 1; CALL; } break; \
+    case 2: { constexpr int KK = 2; CALL; } break; \
+    case 3: { constexpr int KK = 3; CALL; } break; \
+    case 4: { constexpr int KK = 4; CALL; } break; \
+    case 5: { constexpr int KK = 5; CALL; } break; \
+    case 6: { constexpr int KK = 6; CALL; } break; \
+    case 7: { constexpr int KK = 7; CALL; } break; \
+    default: { constexpr int KK = 8; CALL; } break; \
+  }
+
+#define PIRMCUT_DISPATCH_G(GVAR, CALL) \
+  switch (GVAR) {                      \
+    case 1: { constexpr int GG = 1; CALL; } break; \
+    case 2: { constexpr int GG = 2; CALL; } break; \
+    case 4: { constexpr int GG = 4; CALL; } break; \
+    case 8: { constexpr int GG = 8; CALL; } break; \
+    case 16: { constexpr int GG = 16; CALL; } break; \
+    default: { constexpr int GG = 32; CALL; } break; \
+  }
+
+int row_grid(const Ctx& c) {
+  const int64_t threads = c.format == PIRMCUT_FORMAT_DIA ? c.nt : c.nt * c.group;
+  return grid_for(threads);
+}
+
+}  // namespace
+
+cudaError_t launch_scatter_x(Ctx& c, double* xfull) {
+  k_scatter_x<<<grid_for(c.nt), kThreads, 0, c.stream>>>(c.nt, c.hg.s, c.hg.t, c.x, xfull);
+  c.launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_x(Ctx& c, const double* xfull) {
+  k_gather_x<<<grid_for(c.nt), kThreads, 0, c.stream>>>(c.nt, c.hg.s, c.hg.t, xfull, c.x);
+  c.launches += 1;
+  return cudaGetLastError();
+}
+
+// Build the graph of one IRLS step (initial = x^(0) with W^(0) = C):
+//   [c -> g copy | reweight] -> assemble -> [x = 0] -> WHILE{spmv, update_r, update_xp} -> step_end
+cudaError_t build_step_graph(Ctx& c, bool initial, cudaGraphExec_t* out, int* nodes) {
+  cudaError_t e;
+  cudaStream_t st = c.cap_stream;
+  const int grid = row_grid(c);
+  const bool zero_start = initial || !c.opt.warm_start;
+  double* g = c.format == PIRMCUT_FORMAT_DIA ? c.gdia : c.gval;
+  const double* cap = c.format == PIRMCUT_FORMAT_DIA ? c.cdia : c.cval;
+  const size_t gbytes = sizeof(double) * (c.format == PIRMCUT_FORMAT_DIA
+                                              ? size_t(c.K) * c.nt
+                                              : size_t(c.hg.rp.empty() ? 0 : c.hg.rp.back()));
+  int n_nodes = 0;
+  if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+  cudaGraph_t graph = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaStreamCaptureStatus cst;
+  cudaGraphConditionalHandle h{};
+  cudaGraphNode_t cond_node{};
+  e = cudaStreamGetCaptureInfo(st, &cst, nullptr, &graph, nullptr, nullptr, nullptr);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) {
+    cudaGraph_t dummy;
+    cudaStreamEndCapture(st, &dummy);
+    if (dummy) cudaGraphDestroy(dummy);
+    return e;
+  }
+  if (initial) {
+    cudaMemcpyAsync(g, cap, gbytes, cudaMemcpyDeviceToDevice, st);
+  } else if (c.format == PIRMCUT_FORMAT_DIA) {
+    PIRMCUT_DISPATCH_K(c.K, (k_reweight_dia<KK><<<grid, kThreads, 0, st>>>(
+                                c.dd, c.cdia, c.x, c.eps_list, c.C, c.opt.reweight_form, c.gdia)));
+    ++n_nodes;
+  } else {
+    PIRMCUT_DISPATCH_G(c.group, (k_reweight_csr<GG><<<grid, kThreads, 0, st>>>(
+                                    c.nt, c.rp, c.col, c.cval, c.x, c.eps_list, c.C,
+                                    c.opt.reweight_form, c.gval)));
+    ++n_nodes;
+  }
+  AssembleArgs a;
+  a.cs = c.cs;
+  a.ct = c.ct;
+  a.x = c.x;
+  a.eps_list = c.eps_list;
+  a.C = c.C;
+  a.form = c.opt.reweight_form;
+  a.initial = initial ? 1 : 0;
+  a.zero_start = zero_start ? 1 : 0;
+  a.tol2 = c.opt.pcg_tol * c.opt.pcg_tol;
+  a.maxit = c.opt.pcg_max_iter;
+  a.diag = c.diag;
+  a.dinv = c.dinv;
+  a.r = c.r;
+  a.p = c.p;
+  a.partials = c.partials;
+  a.S = c.S;
+  a.h = h;
+  if (c.format == PIRMCUT_FORMAT_DIA) {
+    PIRMCUT_DISPATCH_K(c.K, (k_assemble_dia<KK><<<grid, kThreads, 0, st>>>(c.dd, g, a)));
+  } else {
+    PIRMCUT_DISPATCH_G(c.group, (k_assemble_csr<GG><<<grid, kThreads, 0, st>>>(c.nt, c.rp, c.col, g, a)));
+  }
+  ++n_nodes;
+  if (zero_start) cudaMemsetAsync(c.x, 0, sizeof(double) * c.nt, st);
+  // WHILE node holding one PCG iteration
+  e = cudaStreamGetCaptureInfo(st, &cst, nullptr, &graph, &deps, nullptr, &ndeps);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&cond_node, graph, deps, nullptr, ndeps, &cp);
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t bs;
+    e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+      e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        if (c.format == PIRMCUT_FORMAT_DIA) {
+          PIRMCUT_DISPATCH_K(c.K, (k_spmv_dia<KK><<<grid, kThreads, 0, bs>>>(
+                                      c.dd, g, c.diag, c.p, c.q, c.partials, c.S)));
+        } else {
+          PIRMCUT_DISPATCH_G(c.group, (k_spmv_csr<GG><<<grid, kThreads, 0, bs>>>(
+                                          c.nt, c.rp, c.col, g, c.diag, c.p, c.q, c.partials, c.S)));
+        }
+        k_update_r<<<grid_for(c.nt), kThreads, 0, bs>>>(c.nt, c.q, c.dinv, c.r, c.partials, c.S);
+        k_update_xp<<<grid_for(c.nt), kThreads, 0, bs>>>(c.nt, c.x, c.p, c.q, c.S, h);
+        cudaGraph_t bg = nullptr;
+        e = cudaStreamEndCapture(bs, &bg);
+      }
+      cudaStreamDestroy(bs);
+    }
+  }
+  if (e == cudaSuccess)
+    e = cudaStreamUpdateCaptureDependencies(st, &cond_node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e == cudaSuccess) {
+    k_step_end<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.x, c.S, c.C, c.recs, c.eps_list,
+                                                    initial ? 0 : 1, c.partials);
+    ++n_nodes;
+  }
+  cudaGraph_t captured = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(st, &captured);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, captured, 0);
+  if (captured) cudaGraphDestroy(captured);
+  *nodes = n_nodes;
+  return e;
+}
+
+}  // namespace pirmcut
