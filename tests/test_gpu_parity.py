@@ -1,0 +1,309 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Bars (from the arithmetic and the method's tolerances):
+* iterate x: max |x_gpu - x_oracle| <= 1e-9 (x lies in [0, 1], so this is the
+  relative error in the max norm), per IRLS step, teacher-forced: both sides
+  start step l from the oracle's x^(l-1); the GPU solves to 1e-13.
+* cut value: |mu_gpu - mu_oracle| <= 1e-9 mu_oracle.
+* cut side: identical on every vertex with |x_v - tau| >= 1e-6 whenever both
+  sides chose the same threshold; otherwise (a tie of cut values between
+  candidates) only the value is compared.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+XTOL = 1e-9
+CUT_RTOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1501_03105_gb300 as pkg
+    from paper_1501_03105_gb300 import binding, build
+    import os
+    if not os.path.exists(binding.LIB_PATH):
+        build.build()
+    return pkg
+
+
+def solver(P, g, **kw):
+    kw.setdefault("pcg_tol", 1e-13)
+    return P.Solver(g, **kw)
+
+
+def check_cut(prob, x, side, value, tau):
+    ref = O.sweep_cut(prob, x)
+    assert abs(value - ref["value"]) <= CUT_RTOL * max(ref["value"], 1e-300), (value, ref["value"])
+    assert abs(O.cut_value(prob, side.astype(bool)) - value) <= 1e-12 * max(value, 1e-300)
+    if abs(tau - ref["tau"]) < 1e-12:
+        far = np.abs(x - ref["tau"]) >= 1e-6
+        far[[prob.s, prob.t]] = True
+        assert np.array_equal(side.astype(bool)[far], ref["side"][far])
+    return ref
+
+
+GRAPHS = [
+    ("grid16", lambda: gen.config_graph(1, scale=16)),
+    ("grid37x41", lambda: gen.segmentation_grid(
+        np.clip(gen.image_disks_2d(37, 41, [(18, 20, 9)]) + np.random.default_rng(7).normal(0, .05, (41, 37)), 0, 1))),
+    ("vol9", lambda: gen.config_graph(3, scale=9)),
+    ("random12", lambda: gen.random_graph(12, 0.3, 11, zero_frac=0.2, st_edge=True)),
+    ("random40", lambda: gen.random_graph(40, 0.1, 12)),
+    ("chunglu", lambda: gen.chung_lu_instance(3000, 5)),
+]
+
+
+@pytest.mark.parametrize("fmt", [0, 2])
+@pytest.mark.parametrize("name,make", GRAPHS)
+def test_x0_matches_oracle(P, name, make, fmt):
+    """x^(0): the WLS with W^(0) = C (Section 2.1), cold-started PCG."""
+    g = make()
+    prob = O.Problem.from_graph(g)
+    x0, _ = O.wls_step(prob, O.initial_conductance(prob))
+    with solver(P, g, format=fmt) as s:
+        info = s.initial()
+        assert info.status == 0
+        x = s.get_x()
+    assert x[g.s] == 1.0 and x[g.t] == 0.0
+    assert np.max(np.abs(x - x0)) <= XTOL
+
+
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("fmt", [0, 2])
+def test_teacher_forced_steps_grid64(P, form, fmt):
+    """Every IRLS step of the 64x64 workload, T = 50, each started from the
+    oracle's previous iterate (Steps 1-2 of Section 2.1)."""
+    g = gen.config_graph(1)
+    prob = O.Problem.from_graph(g)
+    T = 50
+    eps = O.eps_schedule(T)
+    xs, _ = O.irls(prob, T, eps, form=form)
+    with solver(P, g, format=fmt, reweight_form=form) as s:
+        for l in range(1, T + 1):
+            s.set_x(xs[l - 1])
+            info = s.irls_step(eps[l - 1])
+            assert info.status == 0 and info.eps == eps[l - 1]
+            x = s.get_x()
+            assert np.max(np.abs(x - xs[l])) <= XTOL, l
+            assert info.x_min >= -1e-12 and info.x_max <= 1 + 1e-12
+
+
+@pytest.mark.parametrize("name,make", GRAPHS)
+def test_teacher_forced_steps_small(P, name, make):
+    g = make()
+    prob = O.Problem.from_graph(g)
+    T = 20
+    eps = O.eps_schedule(T)
+    xs, _ = O.irls(prob, T, eps)
+    with solver(P, g) as s:
+        for l in range(1, T + 1):
+            s.set_x(xs[l - 1])
+            s.irls_step(eps[l - 1])
+            assert np.max(np.abs(s.get_x() - xs[l])) <= XTOL, l
+
+
+def test_free_running_solve_grid64(P):
+    """Algorithm 1 on the 64x64 workload with its own tolerance (1e-10):
+    the final sweep cut matches the oracle's."""
+    g = gen.config_graph(1)
+    prob = O.Problem.from_graph(g)
+    T = 50
+    eps = O.eps_schedule(T)
+    xs, _ = O.irls(prob, T, eps)
+    with P.Solver(g, pcg_tol=1e-10) as s:
+        infos = s.solve(T, eps)
+        assert [i.step for i in infos] == list(range(T + 1))
+        assert all(i.status == 0 for i in infos)
+        assert all(i.rel_residual <= 1e-10 for i in infos)
+        x = s.get_x()
+        side, value, tau = s.cut()
+    assert np.max(np.abs(x - xs[-1])) <= 1e-6      # free-running: reported, loose
+    ref = check_cut(prob, xs[-1], side, value, tau)
+    mu_star, _ = O.max_flow_min_cut(prob)
+    assert value >= mu_star * (1 - 1e-12)           # a cut is never below the min cut
+    assert abs(value - ref["value"]) <= CUT_RTOL * ref["value"]
+
+
+@pytest.mark.parametrize("name,make", GRAPHS)
+@pytest.mark.parametrize("fmt", [0, 2])
+def test_sweep_cut_on_given_x(P, name, make, fmt):
+    """Sweep cut (Section 3.3) on a seeded x with ties, set through set_x."""
+    g = make()
+    prob = O.Problem.from_graph(g)
+    rng = np.random.default_rng(3)
+    x = np.round(rng.random(g.n) * 16) / 16          # heavy ties
+    x[g.s], x[g.t] = 1.0, 0.0
+    with solver(P, g, format=fmt) as s:
+        s.set_x(x)
+        side, value, tau = s.cut()
+    ref = check_cut(prob, x, side, value, tau)
+    assert abs(tau - ref["tau"]) < 1e-15
+
+
+@pytest.mark.parametrize("nt", [1, 2, 3, 255, 256, 257, 2047, 2048, 2049, 4097])
+def test_sweep_ragged_sizes(P, nt):
+    """Sort tiles and scan tiles with ragged tails (chain graphs)."""
+    rng = np.random.default_rng(nt)
+    n = nt + 2
+    s, t = nt, nt + 1
+    u = list(range(nt - 1)) + list(range(nt)) + list(range(nt))
+    v = list(range(1, nt)) + [s] * nt + [t] * nt
+    c = list(rng.uniform(0.5, 1.5, len(u)))
+    rp, col, cc = gen.csr_from_edges(n, u, v, c)
+    g = gen.Graph(n, rp, col, cc, s, t)
+    prob = O.Problem.from_graph(g)
+    x = rng.random(n)
+    x[:nt:3] = 0.5                                    # ties
+    x[s], x[t] = 1.0, 0.0
+    with solver(P, g) as s_:
+        s_.set_x(x)
+        side, value, tau = s_.cut()
+        info = s_.initial()
+        x0g = s_.get_x()
+    check_cut(prob, x, side, value, tau)
+    x0, _ = O.wls_step(prob, O.initial_conductance(prob))
+    assert np.max(np.abs(x0g - x0)) <= XTOL
+
+
+def test_terminals_anywhere_and_duplicates(P):
+    """s and t in the middle of the numbering, parallel entries, unsorted rows."""
+    g = gen.random_graph(15, 0.3, 21, st_edge=True)
+    perm = np.random.default_rng(1).permutation(g.n)
+    gp = gen.permute_graph(g, perm)
+    # split every edge capacity into two parallel entries and reverse row order
+    rows = np.repeat(np.arange(gp.n), np.diff(gp.row_ptr))
+    m = rows < gp.col
+    u, v, c = rows[m], gp.col[m].astype(np.int64), gp.c[m]
+    rp, col, cc = gen.csr_from_edges(gp.n, np.r_[u, u], np.r_[v, v], np.r_[0.25 * c, 0.75 * c])
+    for r in range(gp.n):
+        col[rp[r]:rp[r + 1]] = col[rp[r]:rp[r + 1]][::-1].copy()
+        cc[rp[r]:rp[r + 1]] = cc[rp[r]:rp[r + 1]][::-1].copy()
+    gd = gen.Graph(gp.n, rp, col, cc, gp.s, gp.t)
+    prob = O.Problem.from_graph(gd)
+    xs, _ = O.irls(prob, 10)
+    with solver(P, gd) as s:
+        s.solve(10, O.eps_schedule(10))
+        x = s.get_x()
+        side, value, tau = s.cut()
+    assert np.max(np.abs(x - xs[-1])) <= XTOL
+    check_cut(prob, xs[-1], side, value, tau)
+
+
+def test_one_vertex_and_no_source_edges(P):
+    """n = 3 (s-v-t) closed form; and b = 0 (no s edges) gives x = 0."""
+    rp, col, c = gen.csr_from_edges(3, [0, 1], [1, 2], [3.0, 1.0])
+    g = gen.Graph(3, rp, col, c, 0, 2)
+    with solver(P, g) as s:
+        s.initial()
+        assert abs(s.get_x()[1] - 0.75) < 1e-15
+        side, value, tau = s.cut()
+        assert value == 1.0 and list(side) == [1, 1, 0]
+    rp, col, c = gen.csr_from_edges(4, [0, 1, 2], [1, 2, 3], [1.0, 1.0, 1.0])
+    with solver(P, gen.Graph(4, rp, col, c, 3, 0)) as s:   # s and t swapped on a path
+        s.initial()
+        x = s.get_x()
+        assert abs(x[2] - 2.0 / 3.0) < 1e-15 and abs(x[1] - 1.0 / 3.0) < 1e-15
+    rp, col, c = gen.csr_from_edges(4, [1, 1, 2], [2, 3, 3], [1.0, 1.0, 1.0])
+    g = gen.Graph(4, rp, col, c, 0, 3)                 # s = 0 isolated: b = 0
+    with solver(P, g) as s:
+        info = s.initial()
+        x = s.get_x()
+        assert np.all(x[[1, 2]] == 0.0) and info.status == 0
+        info = s.irls_step(0.1)
+        assert np.all(s.get_x()[[1, 2]] == 0.0)
+
+
+def test_iteration_cap_and_bad_calls(P):
+    from paper_1501_03105_gb300 import binding as B
+    g = gen.config_graph(1, scale=24)
+    with P.Solver(g, pcg_tol=1e-14, pcg_max_iter=2) as s:
+        info = s.initial()
+        assert info.status == B.ENOCONV and info.pcg_iters == 2
+        assert np.all(np.isfinite(s.get_x()))
+        with pytest.raises(B.PirmcutError) as e:
+            s.irls_step(-1.0)
+        assert e.value.status == B.EINVAL
+    with P.Solver(g) as s:
+        with pytest.raises(B.PirmcutError) as e:
+            s.irls_step(0.1)                           # x not set yet
+        assert e.value.status == B.EINVAL
+        with pytest.raises(B.PirmcutError):
+            s.cut()
+
+
+def test_deterministic(P):
+    g = gen.config_graph(1)
+    eps = O.eps_schedule(30)
+    outs = []
+    for _ in range(2):
+        with P.Solver(g) as s:
+            infos = s.solve(30, eps)
+            outs.append((s.get_x(), [i.pcg_iters for i in infos], s.cut()[1]))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1] and outs[0][2] == outs[1][2]
+
+
+def test_update_weights_matches_fresh_context(P):
+    """A sequence of related problems (Section 6): same structure, new c."""
+    g = gen.config_graph(5, scale=12)
+    g2 = gen.perturb_capacities(g, seed=9, sigma=0.05)
+    eps = O.eps_schedule(10)
+    with P.Solver(g) as s:
+        s.solve(10, eps)
+        s.update_weights(g2.c)
+        s.solve(10, eps)
+        xa = s.get_x()
+        ca = s.cut()[1]
+    with P.Solver(g2) as s:
+        s.solve(10, eps)
+        xb = s.get_x()
+        cb = s.cut()[1]
+    assert np.array_equal(xa, xb) and ca == cb
+    prob = O.Problem.from_graph(g2)
+    xs, _ = O.irls(prob, 10, eps)
+    assert np.max(np.abs(xa - xs[-1])) <= XTOL
+
+
+def test_device_buffers(P):
+    """Inputs and outputs in CUDA memory (torch tensors)."""
+    import torch
+    g = gen.config_graph(1, scale=20)
+    prob = O.Problem.from_graph(g)
+    dev = torch.device("cuda")
+    rp = torch.from_numpy(g.row_ptr).to(dev)
+    col = torch.from_numpy(g.col).to(dev)
+    c = torch.from_numpy(g.c).to(dev)
+    h = P.pirmcut_create(g.n, rp, col, c, g.s, g.t, P.pirmcut_default_options(pcg_tol=1e-13))
+    try:
+        P.pirmcut_solve(h, 5, O.eps_schedule(5))
+        xd = torch.empty(g.n, dtype=torch.float64, device=dev)
+        P.pirmcut_get_x(h, xd)
+        sd = torch.empty(g.n, dtype=torch.uint8, device=dev)
+        _, value, tau = P.pirmcut_cut(h, sd)
+        torch.cuda.synchronize()
+        P.pirmcut_set_x(h, xd)
+    finally:
+        P.pirmcut_destroy(h)
+    xs, _ = O.irls(prob, 5)
+    assert np.max(np.abs(xd.cpu().numpy() - xs[-1])) <= XTOL
+    check_cut(prob, xs[-1], sd.cpu().numpy(), value, tau)
+
+
+def test_track_cut_records_each_step(P):
+    g = gen.config_graph(1, scale=24)
+    prob = O.Problem.from_graph(g)
+    eps = O.eps_schedule(8)
+    xs, _ = O.irls(prob, 8, eps)
+    with P.Solver(g, track_cut=1, pcg_tol=1e-13) as s:
+        infos = s.solve(8, eps)
+    for l, info in enumerate(infos):
+        ref = O.sweep_cut(prob, xs[l])
+        assert abs(info.cut_value - ref["value"]) <= CUT_RTOL * ref["value"]
