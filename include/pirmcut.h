@@ -196,6 +196,60 @@ pirmcut_status pirmcut_problem_size(const pirmcut_ctx* ctx, int64_t* n_nontermin
  * count each kernel node they run). */
 int64_t pirmcut_kernel_launches(const pirmcut_ctx* ctx);
 
+/*
+ * Diagnostics for roofline reports: time the PCG matrix-vector kernel
+ * (q = L~ p with the fused (p, q) reduction, Section 3.1) on the current
+ * matrix and search direction, `reps` launches bracketed one by one with CUDA
+ * events on the context's stream.  Needs a completed step (EINVAL otherwise);
+ * leaves x untouched.  avg_ms receives the mean launch time; bytes and flops
+ * (either may be NULL) the algorithmic bytes moved and floating-point
+ * operations of one launch (every stored value, matrix index and vector entry
+ * read or written once; an FMA counts 2).
+ */
+pirmcut_status pirmcut_time_spmv(pirmcut_ctx* ctx, int reps, double* avg_ms, double* bytes,
+                                 double* flops);
+
+/*
+ * Sweep cut that allocates no memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- code that runs
+ * while a stream is being captured into a CUDA graph (an allocation there
+ * would break or invalidate the capture), host frameworks that own all device
+ * memory through their own pool and forbid allocations from libraries, and
+ * real-time loops that must never block in the allocator.
+ *
+ * It returns what pirmcut_cut returns for the same graph and x (same sweep
+ * order, candidates and tie rules; FP64 throughout), computed by a single
+ * thread block directly from a full CSR in device memory, without a context.
+ * Its scratch is one fixed array in the library's device memory of
+ * 36 * PIRMCUT_STATIC_MAX_NONTERMINALS bytes (about 2.4 MB), which every GPU
+ * that loads the library holds until the process exits.
+ *
+ * n, row_ptr, col, c, s, t  the graph exactly as for pirmcut_create, but every
+ *          array in device memory; it must already be valid (the library
+ *          reads it as is: out-of-range column ids are skipped and reported
+ *          in result[3], nothing else is checked).  n - 2 must not exceed
+ *          PIRMCUT_STATIC_MAX_NONTERMINALS, otherwise EINVAL.
+ * x        double[n] in device memory, the voltages to round.
+ * side     uint8[n] in device memory, receives 1 on the source side, 0 else.
+ * result   double[4] in device memory: {cut value, tau, chosen prefix length
+ *          k, 1 if an out-of-range column id was met else 0}.
+ * stream   cudaStream_t (as void*) the kernel is queued on; the call returns
+ *          without waiting for it.
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins.  All calls on a device share the one
+ * array, so calls that may overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  No part of the array
+ * needs to start cleared: every entry a call reads it has written first.
+ * Errors: EINVAL (sizes, terminals, null pointers; see pirmcut_last_error(NULL)),
+ * ECUDA (lookup or launch failed).
+ */
+#define PIRMCUT_STATIC_MAX_NONTERMINALS 65536
+pirmcut_status pirmcut_sweep_cut_static(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                                        const double* c, int32_t s, int32_t t, const double* x,
+                                        uint8_t* side, double* result, void* stream);
+
 /* Text of the last error of ctx (or of the last failed create when ctx is NULL). */
 const char* pirmcut_last_error(const pirmcut_ctx* ctx);
 

@@ -86,6 +86,11 @@ def lib() -> ctypes.CDLL:
     L.pirmcut_problem_size.argtypes = [_P, ctypes.POINTER(i64), ctypes.POINTER(i64),
                                        ctypes.POINTER(ctypes.c_int)]
     L.pirmcut_problem_size.restype = ctypes.c_int
+    L.pirmcut_time_spmv.argtypes = [_P, ctypes.c_int, ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                                    ctypes.POINTER(dbl)]
+    L.pirmcut_time_spmv.restype = ctypes.c_int
+    L.pirmcut_sweep_cut_static.argtypes = [i64, _P, _P, _P, i32, i32, _P, _P, _P, _P]
+    L.pirmcut_sweep_cut_static.restype = ctypes.c_int
     L.pirmcut_kernel_launches.argtypes = [_P]
     L.pirmcut_kernel_launches.restype = i64
     L.pirmcut_last_error.argtypes = [_P]
@@ -218,6 +223,32 @@ def pirmcut_problem_size(h):
     return a.value, b.value, f.value
 
 
+def pirmcut_time_spmv(h, reps: int = 20):
+    """(mean ms per SpMV launch, algorithmic bytes, flops) on the current state."""
+    ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(h, lib().pirmcut_time_spmv(h, int(reps), ctypes.byref(ms), ctypes.byref(by), ctypes.byref(fl)))
+    return ms.value, by.value, fl.value
+
+
+STATIC_MAX_NONTERMINALS = 65536
+
+
+def pirmcut_sweep_cut_static(n, row_ptr, col, c, s, t, x, side, result, stream=None):
+    """Allocation-free sweep cut on device-resident arrays (torch CUDA tensors):
+    queues one kernel on ``stream``; ``side`` (uint8[n]) and ``result``
+    (float64[4]: value, tau, k, bad-column flag) are filled on the device."""
+    ptrs = []
+    for a, dt in ((row_ptr, np.int64), (col, np.int32), (c, np.float64), (x, np.float64),
+                  (side, np.uint8), (result, np.float64)):
+        p, kind, _ = _ptr(a, dt)
+        if kind != MEM_DEVICE:
+            raise TypeError("every array must be in device memory")
+        ptrs.append(p)
+    st = lib().pirmcut_sweep_cut_static(int(n), ptrs[0], ptrs[1], ptrs[2], int(s), int(t),
+                                        ptrs[3], ptrs[4], ptrs[5], _stream_ptr(stream))
+    _check(None, st)
+
+
 def pirmcut_kernel_launches(h) -> int:
     return int(lib().pirmcut_kernel_launches(h))
 
@@ -266,6 +297,9 @@ class Solver:
 
     def problem_size(self):
         return pirmcut_problem_size(self.h)
+
+    def time_spmv(self, reps=20):
+        return pirmcut_time_spmv(self.h, reps)
 
     def kernel_launches(self):
         return pirmcut_kernel_launches(self.h)

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <new>
 #include <string>
@@ -232,6 +233,10 @@ pirmcut_status run_steps(pirmcut_ctx* h, bool with_initial, int T, int first_ste
 }
 
 }  // namespace
+
+namespace pirmcut {
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace pirmcut
 
 extern "C" {
 
@@ -498,6 +503,44 @@ pirmcut_status pirmcut_problem_size(const pirmcut_ctx* h, int64_t* n_nonterminal
 }
 
 int64_t pirmcut_kernel_launches(const pirmcut_ctx* h) { return h ? h->c.launches : 0; }
+
+pirmcut_status pirmcut_time_spmv(pirmcut_ctx* h, int reps, double* avg_ms, double* bytes,
+                                 double* flops) {
+  if (!h) return fail(nullptr, PIRMCUT_EINVAL, "ctx is NULL");
+  Ctx& c = h->c;
+  if (!c.x_set || h->next_step == 0) return fail(h, PIRMCUT_EINVAL, "no step has run yet");
+  if (reps < 1 || !avg_ms) return fail(h, PIRMCUT_EINVAL, "reps must be >= 1 and avg_ms non-NULL");
+  const double nt = double(c.nt);
+  const double nnz = c.format == PIRMCUT_FORMAT_DIA ? 2.0 * double(c.hg.n_edges)
+                                                     : double(c.hg.col.size());
+  if (bytes) {
+    *bytes = c.format == PIRMCUT_FORMAT_DIA
+                 ? nt * (8.0 * c.K + 8.0 * 3)                        // g (upper), diag, p, q
+                 : nnz * (8.0 + 4.0) + nt * (8.0 * 3 + 8.0);         // g, col, diag, p, q, row_ptr
+  }
+  if (flops) *flops = 2.0 * (nnz + 2.0 * nt);                        // nnz + diagonal FMAs + (p, q)
+  // the solve left stop_req set: clear it so the kernel runs, restore after
+  const size_t off_stop = offsetof(pirmcut::PcgState, stop_req);
+  int one = 1, zero = 0;
+  CK(h, cudaMemcpyAsync(reinterpret_cast<char*>(c.S) + off_stop, &zero, sizeof(int), cudaMemcpyHostToDevice, c.stream), "time");
+  cudaEvent_t a = event_at(h, 0), b = event_at(h, 1);
+  if (!a || !b) return fail(h, PIRMCUT_ECUDA, "cudaEventCreate failed");
+  CK(h, pirmcut::launch_spmv_once(c), "spmv");  // warm-up
+  double total = 0.0;
+  for (int k = 0; k < reps; ++k) {
+    CK(h, cudaEventRecord(a, c.stream), "event");
+    CK(h, pirmcut::launch_spmv_once(c), "spmv");
+    CK(h, cudaEventRecord(b, c.stream), "event");
+    CK(h, cudaEventSynchronize(b), "event");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    total += ms;
+  }
+  CK(h, cudaMemcpyAsync(reinterpret_cast<char*>(c.S) + off_stop, &one, sizeof(int), cudaMemcpyHostToDevice, c.stream), "time");
+  CK(h, cudaStreamSynchronize(c.stream), "time");
+  *avg_ms = total / reps;
+  return PIRMCUT_OK;
+}
 
 const char* pirmcut_last_error(const pirmcut_ctx* h) {
   return h ? h->c.err.c_str() : g_create_error.c_str();

@@ -41,6 +41,10 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
                             const double* c, int32_t s, int32_t t, int format_req,
                             HostGraph* out, std::string* err);
 
+// Record the message returned by pirmcut_last_error(NULL) for calls that have
+// no context.
+void set_global_error(const std::string& msg);
+
 // Reduced index of original vertex v (v not a terminal) and its inverse.
 inline int64_t reduced_index(int64_t v, int32_t s, int32_t t) {
   return v - (v > s) - (v > t);
