@@ -82,6 +82,12 @@ typedef struct {
   int format;          /* PIRMCUT_FORMAT_*                                     */
   int track_cut;       /* 1: run a sweep cut after every IRLS step and record
                           its value in pirmcut_step_info.cut_value             */
+  int graph_launch;    /* 1: each step is one CUDA graph whose PCG loop is a
+                          device-side WHILE node (no host sync inside a solve);
+                          0: the same kernels launched one by one from the host,
+                          PCG iterations in chunks of 8 with the stop flag read
+                          back between chunks (for profilers that cannot see
+                          into conditional graph nodes)                       */
 } pirmcut_options;
 
 typedef struct {
@@ -96,7 +102,7 @@ typedef struct {
 } pirmcut_step_info;
 
 /* Fill *opt with the defaults: NORTH_STAR, FP64, pcg_tol 1e-10,
- * pcg_max_iter 20000, warm_start 1, FORMAT_AUTO, track_cut 0. */
+ * pcg_max_iter 20000, warm_start 1, FORMAT_AUTO, track_cut 0, graph_launch 1. */
 void pirmcut_default_options(pirmcut_options* opt);
 
 /*

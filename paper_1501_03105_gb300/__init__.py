@@ -20,6 +20,7 @@ from .binding import (  # noqa: F401
     pirmcut_update_weights,
     pirmcut_problem_size,
     pirmcut_kernel_launches,
+    pirmcut_time_spmv,
     pirmcut_last_error,
     pirmcut_destroy,
 )

@@ -31,7 +31,7 @@ class Options(ctypes.Structure):
     _fields_ = [("reweight_form", ctypes.c_int), ("precision", ctypes.c_int),
                 ("pcg_tol", ctypes.c_double), ("pcg_max_iter", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("format", ctypes.c_int),
-                ("track_cut", ctypes.c_int)]
+                ("track_cut", ctypes.c_int), ("graph_launch", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):

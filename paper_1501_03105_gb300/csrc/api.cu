@@ -17,6 +17,7 @@ struct pirmcut_ctx {
   pirmcut::StepCounters* h_ctr = nullptr;
   double* h_eps = nullptr;
   double* h_result = nullptr;  // 4
+  int* h_stop = nullptr;       // PCG stop flag read back in stream-launch mode
   std::vector<cudaEvent_t> events;
   int next_step = 0;           // IRLS index of the next step record
 };
@@ -79,6 +80,10 @@ pirmcut_status check_options(const pirmcut_options& o, std::string* msg) {
   }
   if (o.pcg_max_iter < 0 || o.pcg_max_iter > 100000000) {
     *msg = "pcg_max_iter must be in [0, 1e8]";
+    return PIRMCUT_EINVAL;
+  }
+  if (o.graph_launch != 0 && o.graph_launch != 1) {
+    *msg = "graph_launch must be 0 or 1";
     return PIRMCUT_EINVAL;
   }
   if (o.format < PIRMCUT_FORMAT_AUTO || o.format > PIRMCUT_FORMAT_CSR) {
@@ -191,7 +196,12 @@ pirmcut_status run_steps(pirmcut_ctx* h, bool with_initial, int T, int first_ste
   Ctx& c = h->c;
   const int nrec = T + (with_initial ? 1 : 0);
   if (nrec == 0) return PIRMCUT_OK;
-  pirmcut_status ps = ensure_graphs(h, c.opt.track_cut != 0);
+  const bool graphs = c.opt.graph_launch != 0;
+  pirmcut_status ps = graphs ? ensure_graphs(h, c.opt.track_cut != 0) : PIRMCUT_OK;
+  if (ps == PIRMCUT_OK && !graphs && c.opt.track_cut) {
+    CK(h, pirmcut::sweep_alloc(c), "sweep buffers");
+    if (!c.g_cut) CK(h, pirmcut::build_cut_graph(c, &c.g_cut, &c.nodes_cut), "building the sweep graph");
+  }
   if (ps != PIRMCUT_OK) return ps;
   h->h_ctr->eps_idx = 0;
   h->h_ctr->rec_idx = 0;
@@ -203,8 +213,14 @@ pirmcut_status run_steps(pirmcut_ctx* h, bool with_initial, int T, int first_ste
   CK(h, cudaEventRecord(e0, c.stream), "event");
   for (int k = 0; k < nrec; ++k) {
     const bool init = with_initial && k == 0;
-    CK(h, cudaGraphLaunch(init ? c.g_init : c.g_step, c.stream), "graph launch");
-    c.launches += init ? c.nodes_init : c.nodes_step;
+    if (graphs) {
+      CK(h, cudaGraphLaunch(init ? c.g_init : c.g_step, c.stream), "graph launch");
+      c.launches += init ? c.nodes_init : c.nodes_step;
+    } else {
+      int64_t kernels = 0;
+      CK(h, pirmcut::run_step_stream(c, init, h->h_stop, &kernels), "step launch");
+      c.launches += kernels;
+    }
     if (c.opt.track_cut) {
       CK(h, cudaGraphLaunch(c.g_cut, c.stream), "graph launch");
       c.launches += c.nodes_cut;
@@ -221,7 +237,7 @@ pirmcut_status run_steps(pirmcut_ctx* h, bool with_initial, int T, int first_ste
     cudaEventElapsedTime(&ms, h->events[k], h->events[k + 1]);
     pirmcut_step_info info;
     fill_info(c, c.h_recs[k], ms, &info);
-    c.launches += 3LL * info.pcg_iters;
+    if (graphs) c.launches += 3LL * info.pcg_iters;
     if (infos) infos[k] = info;
     if (info.status == PIRMCUT_ENUMERIC) worst = PIRMCUT_ENUMERIC;
     else if (info.status == PIRMCUT_ENOCONV && worst == PIRMCUT_OK) worst = PIRMCUT_ENOCONV;
@@ -249,6 +265,7 @@ void pirmcut_default_options(pirmcut_options* opt) {
   opt->warm_start = 1;
   opt->format = PIRMCUT_FORMAT_AUTO;
   opt->track_cut = 0;
+  opt->graph_launch = 1;
 }
 
 pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* col,
@@ -331,6 +348,7 @@ pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* 
     return bail(e, "cudaHostAlloc");
   h->h_eps = reinterpret_cast<double*>(h->h_ctr + 1);
   h->h_result = h->h_eps + 2;
+  h->h_stop = reinterpret_cast<int*>(h->h_eps + 7);
   ps = upload_problem(h);
   if (ps != PIRMCUT_OK) {
     std::string m = cx.err;

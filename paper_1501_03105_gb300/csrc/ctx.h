@@ -110,8 +110,10 @@ struct Ctx {
 
 // pcg.cu
 cudaError_t build_step_graph(Ctx& c, bool initial, cudaGraphExec_t* out, int* nodes);
+cudaError_t run_step_stream(Ctx& c, bool initial, int* stop_flag_host, int64_t* kernels);
 cudaError_t launch_scatter_x(Ctx& c, double* xfull);           // reduced x -> full n
 cudaError_t launch_gather_x(Ctx& c, const double* xfull);      // full n -> reduced x
+cudaError_t launch_spmv_once(Ctx& c);                          // one standalone SpMV launch
 // sweep.cu
 cudaError_t sweep_alloc(Ctx& c);
 cudaError_t build_cut_graph(Ctx& c, cudaGraphExec_t* out, int* nodes);

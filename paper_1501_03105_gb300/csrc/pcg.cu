@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 
 #include "ctx.h"
 
@@ -92,6 +93,7 @@ struct AssembleArgs {
   double* partials;
   PcgState* S;
   cudaGraphConditionalHandle h;
+  int use_cond;    // 1 inside the step graph (set the WHILE condition), 0 for stream launches
 };
 
 __device__ __forceinline__ void assemble_finish(const AssembleArgs& a, double rz, double rr,
@@ -115,7 +117,7 @@ __device__ __forceinline__ void assemble_finish(const AssembleArgs& a, double rz
       S->status = PIRMCUT_ENUMERIC;
     }
     S->stop_req = stop;
-    cudaGraphSetConditional(a.h, stop ? 0u : 1u);
+    if (a.use_cond) cudaGraphSetConditional(a.h, stop ? 0u : 1u);
   }
 }
 
@@ -320,7 +322,8 @@ k_update_r(int64_t nt, double* __restrict__ qz, const double* __restrict__ dinv,
 // once a stop was requested in this or an earlier kernel.
 __global__ void __launch_bounds__(kThreads)
 k_update_xp(int64_t nt, double* __restrict__ x, double* __restrict__ p,
-            const double* __restrict__ z, PcgState* S, cudaGraphConditionalHandle h) {
+            const double* __restrict__ z, PcgState* S, cudaGraphConditionalHandle h,
+            int use_cond) {
   if (!S->stopped) {
     const double alpha = S->alpha, beta = S->beta;
     for (int64_t i = gtid(); i < nt; i += gstride()) {
@@ -329,7 +332,7 @@ k_update_xp(int64_t nt, double* __restrict__ x, double* __restrict__ p,
       p[i] = fma(beta, pi, z[i]);
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && S->stop_req) cudaGraphSetConditional(h, 0u);
+  if (use_cond && blockIdx.x == 0 && threadIdx.x == 0 && S->stop_req) cudaGraphSetConditional(h, 0u);
 }
 
 // ---------------------------------------------------------------------------
@@ -382,13 +385,26 @@ k_step_end(int64_t nt, double* __restrict__ x, PcgState* S, StepCounters* C, Ste
     s_last = (atomicAdd(&S->counter[3], 1u) == gridDim.x - 1) ? 1u : 0u;
   }
   __syncthreads();
-  if (!s_last || threadIdx.x != 0) return;
+  if (!s_last) return;
   __threadfence();
   mn = INFINITY;
   mx = -INFINITY;
-  for (unsigned int b = 0; b < gridDim.x; ++b) {
+  for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
     mn = fmin(mn, __ldcg(partials + b));
     mx = fmax(mx, __ldcg(partials + gridDim.x + b));
+  }
+  mn = warp_min(mn);
+  mx = warp_max(mx);
+  __syncthreads();
+  if (lane == 0) {
+    smn[wid] = mn;
+    smx[wid] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+    mn = fmin(mn, smn[w]);
+    mx = fmax(mx, smx[w]);
   }
   S->counter[3] = 0u;
   S->xmin = mn;
@@ -486,11 +502,24 @@ cudaError_t launch_gather_x(Ctx& c, const double* xfull) {
   return cudaGetLastError();
 }
 
-// Build the graph of one IRLS step (initial = x^(0) with W^(0) = C):
-//   [c -> g copy | reweight] -> assemble -> [x = 0] -> WHILE{spmv, update_r, update_xp} -> step_end
-cudaError_t build_step_graph(Ctx& c, bool initial, cudaGraphExec_t* out, int* nodes) {
-  cudaError_t e;
-  cudaStream_t st = c.cap_stream;
+cudaError_t launch_spmv_once(Ctx& c) {
+  const int grid = row_grid(c);
+  if (c.format == PIRMCUT_FORMAT_DIA) {
+    PIRMCUT_DISPATCH_K(c.K, (k_spmv_dia<KK><<<grid, kThreads, 0, c.stream>>>(
+                                c.dd, c.gdia, c.diag, c.p, c.q, c.partials, c.S)));
+  } else {
+    PIRMCUT_DISPATCH_G(c.group, (k_spmv_csr<GG><<<grid, kThreads, 0, c.stream>>>(
+                                    c.nt, c.rp, c.col, c.gval, c.diag, c.p, c.q, c.partials, c.S)));
+  }
+  c.launches += 1;
+  return cudaGetLastError();
+}
+
+namespace {
+
+// Kernels of a step before the PCG loop: [c -> g | reweight] -> assemble -> [x = 0].
+int enqueue_prologue(Ctx& c, cudaStream_t st, bool initial, cudaGraphConditionalHandle h,
+                     int use_cond) {
   const int grid = row_grid(c);
   const bool zero_start = initial || !c.opt.warm_start;
   double* g = c.format == PIRMCUT_FORMAT_DIA ? c.gdia : c.gval;
@@ -498,33 +527,18 @@ cudaError_t build_step_graph(Ctx& c, bool initial, cudaGraphExec_t* out, int* no
   const size_t gbytes = sizeof(double) * (c.format == PIRMCUT_FORMAT_DIA
                                               ? size_t(c.K) * c.nt
                                               : size_t(c.hg.rp.empty() ? 0 : c.hg.rp.back()));
-  int n_nodes = 0;
-  if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
-  cudaGraph_t graph = nullptr;
-  const cudaGraphNode_t* deps = nullptr;
-  size_t ndeps = 0;
-  cudaStreamCaptureStatus cst;
-  cudaGraphConditionalHandle h{};
-  cudaGraphNode_t cond_node{};
-  e = cudaStreamGetCaptureInfo(st, &cst, nullptr, &graph, nullptr, nullptr, nullptr);
-  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
-  if (e != cudaSuccess) {
-    cudaGraph_t dummy;
-    cudaStreamEndCapture(st, &dummy);
-    if (dummy) cudaGraphDestroy(dummy);
-    return e;
-  }
+  int kernels = 0;
   if (initial) {
     cudaMemcpyAsync(g, cap, gbytes, cudaMemcpyDeviceToDevice, st);
   } else if (c.format == PIRMCUT_FORMAT_DIA) {
     PIRMCUT_DISPATCH_K(c.K, (k_reweight_dia<KK><<<grid, kThreads, 0, st>>>(
                                 c.dd, c.cdia, c.x, c.eps_list, c.C, c.opt.reweight_form, c.gdia)));
-    ++n_nodes;
+    ++kernels;
   } else {
     PIRMCUT_DISPATCH_G(c.group, (k_reweight_csr<GG><<<grid, kThreads, 0, st>>>(
                                     c.nt, c.rp, c.col, c.cval, c.x, c.eps_list, c.C,
                                     c.opt.reweight_form, c.gval)));
-    ++n_nodes;
+    ++kernels;
   }
   AssembleArgs a;
   a.cs = c.cs;
@@ -544,13 +558,63 @@ cudaError_t build_step_graph(Ctx& c, bool initial, cudaGraphExec_t* out, int* no
   a.partials = c.partials;
   a.S = c.S;
   a.h = h;
+  a.use_cond = use_cond;
   if (c.format == PIRMCUT_FORMAT_DIA) {
     PIRMCUT_DISPATCH_K(c.K, (k_assemble_dia<KK><<<grid, kThreads, 0, st>>>(c.dd, g, a)));
   } else {
     PIRMCUT_DISPATCH_G(c.group, (k_assemble_csr<GG><<<grid, kThreads, 0, st>>>(c.nt, c.rp, c.col, g, a)));
   }
-  ++n_nodes;
+  ++kernels;
   if (zero_start) cudaMemsetAsync(c.x, 0, sizeof(double) * c.nt, st);
+  return kernels;
+}
+
+// One PCG iteration: spmv -> update_r -> update_xp.
+int enqueue_iteration(Ctx& c, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
+  const int grid = row_grid(c);
+  const double* g = c.format == PIRMCUT_FORMAT_DIA ? c.gdia : c.gval;
+  if (c.format == PIRMCUT_FORMAT_DIA) {
+    PIRMCUT_DISPATCH_K(c.K, (k_spmv_dia<KK><<<grid, kThreads, 0, st>>>(
+                                c.dd, g, c.diag, c.p, c.q, c.partials, c.S)));
+  } else {
+    PIRMCUT_DISPATCH_G(c.group, (k_spmv_csr<GG><<<grid, kThreads, 0, st>>>(
+                                    c.nt, c.rp, c.col, g, c.diag, c.p, c.q, c.partials, c.S)));
+  }
+  k_update_r<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.q, c.dinv, c.r, c.partials, c.S);
+  k_update_xp<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.x, c.p, c.q, c.S, h, use_cond);
+  return 3;
+}
+
+int enqueue_epilogue(Ctx& c, cudaStream_t st, bool initial) {
+  k_step_end<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.x, c.S, c.C, c.recs, c.eps_list,
+                                                  initial ? 0 : 1, c.partials);
+  return 1;
+}
+
+}  // namespace
+
+// Build the graph of one IRLS step (initial = x^(0) with W^(0) = C):
+//   prologue -> WHILE{spmv, update_r, update_xp} -> step_end
+cudaError_t build_step_graph(Ctx& c, bool initial, cudaGraphExec_t* out, int* nodes) {
+  cudaError_t e;
+  cudaStream_t st = c.cap_stream;
+  int n_nodes = 0;
+  if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+  cudaGraph_t graph = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaStreamCaptureStatus cst;
+  cudaGraphConditionalHandle h{};
+  cudaGraphNode_t cond_node{};
+  e = cudaStreamGetCaptureInfo(st, &cst, nullptr, &graph, nullptr, nullptr, nullptr);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) {
+    cudaGraph_t dummy = nullptr;
+    cudaStreamEndCapture(st, &dummy);
+    if (dummy) cudaGraphDestroy(dummy);
+    return e;
+  }
+  n_nodes += enqueue_prologue(c, st, initial, h, 1);
   // WHILE node holding one PCG iteration
   e = cudaStreamGetCaptureInfo(st, &cst, nullptr, &graph, &deps, nullptr, &ndeps);
   cudaGraphNodeParams cp = {};
@@ -566,15 +630,7 @@ cudaError_t build_step_graph(Ctx& c, bool initial, cudaGraphExec_t* out, int* no
     if (e == cudaSuccess) {
       e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        if (c.format == PIRMCUT_FORMAT_DIA) {
-          PIRMCUT_DISPATCH_K(c.K, (k_spmv_dia<KK><<<grid, kThreads, 0, bs>>>(
-                                      c.dd, g, c.diag, c.p, c.q, c.partials, c.S)));
-        } else {
-          PIRMCUT_DISPATCH_G(c.group, (k_spmv_csr<GG><<<grid, kThreads, 0, bs>>>(
-                                          c.nt, c.rp, c.col, g, c.diag, c.p, c.q, c.partials, c.S)));
-        }
-        k_update_r<<<grid_for(c.nt), kThreads, 0, bs>>>(c.nt, c.q, c.dinv, c.r, c.partials, c.S);
-        k_update_xp<<<grid_for(c.nt), kThreads, 0, bs>>>(c.nt, c.x, c.p, c.q, c.S, h);
+        enqueue_iteration(c, bs, h, 1);
         cudaGraph_t bg = nullptr;
         e = cudaStreamEndCapture(bs, &bg);
       }
@@ -583,17 +639,38 @@ cudaError_t build_step_graph(Ctx& c, bool initial, cudaGraphExec_t* out, int* no
   }
   if (e == cudaSuccess)
     e = cudaStreamUpdateCaptureDependencies(st, &cond_node, nullptr, 1, cudaStreamSetCaptureDependencies);
-  if (e == cudaSuccess) {
-    k_step_end<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.x, c.S, c.C, c.recs, c.eps_list,
-                                                    initial ? 0 : 1, c.partials);
-    ++n_nodes;
-  }
+  if (e == cudaSuccess) n_nodes += enqueue_epilogue(c, st, initial);
   cudaGraph_t captured = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(st, &captured);
   if (e == cudaSuccess) e = e2;
   if (e == cudaSuccess) e = cudaGraphInstantiate(out, captured, 0);
   if (captured) cudaGraphDestroy(captured);
   *nodes = n_nodes;
+  return e;
+}
+
+// The same step launched kernel by kernel on the context's stream (no graph):
+// PCG iterations go in chunks of 8, the stop flag is read back between chunks.
+// Kernels queued after the stop are no-ops (they test the flag first).
+cudaError_t run_step_stream(Ctx& c, bool initial, int* stop_flag_host, int64_t* kernels) {
+  cudaStream_t st = c.stream;
+  cudaGraphConditionalHandle none{};
+  int64_t k = enqueue_prologue(c, st, initial, none, 0);
+  cudaError_t e = cudaGetLastError();
+  const size_t off = offsetof(PcgState, stop_req);
+  for (int guard = 0; e == cudaSuccess; ++guard) {
+    for (int j = 0; j < 8; ++j) k += enqueue_iteration(c, st, none, 0);
+    e = cudaMemcpyAsync(stop_flag_host, reinterpret_cast<char*>(c.S) + off, sizeof(int),
+                        cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess || *stop_flag_host) break;
+    if (guard > c.opt.pcg_max_iter / 8 + 2) break;  // the device caps iterations; belt and braces
+  }
+  if (e == cudaSuccess) {
+    k += enqueue_epilogue(c, st, initial);
+    e = cudaGetLastError();
+  }
+  *kernels = k;
   return e;
 }
 

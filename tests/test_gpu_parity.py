@@ -307,3 +307,18 @@ def test_track_cut_records_each_step(P):
     for l, info in enumerate(infos):
         ref = O.sweep_cut(prob, xs[l])
         assert abs(info.cut_value - ref["value"]) <= CUT_RTOL * ref["value"]
+
+
+@pytest.mark.parametrize("fmt", [0, 2])
+def test_stream_launch_matches_graph_launch(P, fmt):
+    """The same kernels launched from the host (graph_launch = 0) give
+    bit-identical iterates, iteration counts and cut."""
+    g = gen.config_graph(1, scale=40)
+    eps = O.eps_schedule(12)
+    out = []
+    for mode in (1, 0):
+        with P.Solver(g, format=fmt, graph_launch=mode) as s:
+            infos = s.solve(12, eps)
+            out.append((s.get_x(), [i.pcg_iters for i in infos], s.cut()[1]))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
