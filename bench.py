@@ -216,6 +216,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=15.0)
+    ap.add_argument("--only", default=None, choices=["fp64", "mixed"],
+                    help="time one path only (profiling runs)")
     ap.add_argument("--launch", default="graph", choices=["graph", "stream"],
                     help="graph: one CUDA graph per IRLS step (default); stream: kernels "
                          "launched from the host (for profilers)")
@@ -240,68 +242,117 @@ def main():
     g = make_graph()
     eps = eps_list(T_STEPS)
     stream = torch.cuda.current_stream()
-    opt = B.pirmcut_default_options(pcg_tol=PCG_TOL, graph_launch=int(args.launch == "graph"))
-    solver = B.Solver(g, opt, stream=stream)
-    nt, ne, fmt = solver.problem_size()
-
-    def step():
-        infos = solver.solve(T_STEPS, eps)
-        _, value, _ = solver.cut(side=side_dev)
-        return sum(i.pcg_iters for i in infos), value
-
     side_dev = torch.empty(g.n, dtype=torch.uint8, device="cuda")
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    launches0 = solver.kernel_launches()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    iters = 0
-    cut_value = None
-    with ClockSampler(local) as clk:
+    hbm_peak, peak_kind = peaks()
+
+    def timed(precision, with_clocks):
+        """Warm-up, then K timed steps of one path; returns its measurements."""
+        opt = B.pirmcut_default_options(pcg_tol=PCG_TOL, graph_launch=int(args.launch == "graph"),
+                                        precision=precision)
+        solver = B.Solver(g, opt, stream=stream)
+
+        def step():
+            infos = solver.solve(T_STEPS, eps)
+            _, value, _ = solver.cut(side=side_dev)
+            return sum(i.pcg_iters for i in infos), sum(i.refinements for i in infos), value
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        launches0 = solver.kernel_launches()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        iters = refine = 0
+        cut_value = None
+        clk = ClockSampler(local) if with_clocks else None
+        if clk:
+            clk.__enter__()
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):
-            it, cut_value = step()
+            it, rf, cut_value = step()
             iters += it
+            refine += rf
         ev1.record(stream)
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    launches = solver.kernel_launches() - launches0
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+        if clk:
+            clk.__exit__(None, None, None)
+        ms = ev0.elapsed_time(ev1)
+        launches = solver.kernel_launches() - launches0
+        if dist:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        x_final = solver.get_x()
+        spmv_ms, spmv_bytes, spmv_flops = solver.time_spmv(reps=30)
+        nt, ne, fmt = solver.problem_size()
+        solver.close()
+        # time-to-cut: one more run recording the sweep value after every step
+        opt.track_cut = 1
+        with B.Solver(g, opt, stream=stream) as s2:
+            infos = s2.solve(T_STEPS, eps)
+        return dict(ms=ms, iters=iters, refine=refine, cut=cut_value, launches=launches,
+                    x=x_final, spmv=(spmv_ms, spmv_bytes, spmv_flops), nt=nt, ne=ne, fmt=fmt,
+                    track=[(i.cut_value, i.ms) for i in infos],
+                    clocks=clk.summary() if clk else None)
+
+    if args.only == "mixed":
+        r64 = timed(B.PREC_MIXED, with_clocks=True)
+        rmx = r64
+    else:
+        r64 = timed(B.PREC_FP64, with_clocks=True)
+        rmx = timed(B.PREC_MIXED, with_clocks=False) if args.only is None else r64
+    nt, ne, fmt = r64["nt"], r64["ne"], r64["fmt"]
+    iters, ms, launches, cut_value = r64["iters"], r64["ms"], r64["launches"], r64["cut"]
     ms_step = ms / args.steps
     value = ws * ne * iters / (ms / 1e3)
+    mu_ref = cut_value
+
+    def time_to_cut(track):
+        acc = 0.0
+        for l, (cv, ms_l) in enumerate(track):
+            acc += ms_l
+            if abs(cv - mu_ref) <= 1e-6 * mu_ref:
+                return {"ms": acc, "step": l}
+        return {"ms": None, "step": None}
 
     # roofline of the PCG matrix-vector kernel (its own CUDA events, its stream)
-    spmv_ms, spmv_bytes, spmv_flops = solver.time_spmv(reps=30)
-    hbm_peak, peak_kind = peaks()
+    spmv_ms, spmv_bytes, spmv_flops = r64["spmv"]
     gbs = spmv_bytes / (spmv_ms * 1e-3) / 1e9
     tflops = spmv_flops / (spmv_ms * 1e-3) / 1e12
     hbm_frac = gbs / hbm_peak
     alu_frac = tflops / NOMINAL_FP64_TFLOPS
     src = kernel_source_hash()
     traffic = profile_traffic(src)
-    if alu_frac >= hbm_frac:
-        roof = {"bound": "alu", "achieved": tflops, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": alu_frac, "traffic": traffic,
-                "peak_kind": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)",
-                "kernel": "k_spmv_dia<2> (q = L~p, fused (p,q))",
-                "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": hbm_frac,
-                        "peak_kind": peak_kind},
-                "bytes_per_launch": spmv_bytes, "flops_per_launch": spmv_flops,
-                "launch_ms": spmv_ms}
-    else:
-        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
-                "traffic": traffic, "peak_kind": peak_kind, "kernel": "k_spmv_dia",
-                "bytes_per_launch": spmv_bytes, "flops_per_launch": spmv_flops,
-                "launch_ms": spmv_ms}
-    solver.close()
+    roof = {"bound": "alu", "achieved": tflops, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+            "frac": alu_frac, "traffic": traffic,
+            "peak_kind": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)",
+            "kernel": "k_spmv_dia<2> FP64 (q = L~p, fused (p,q))",
+            "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": hbm_frac,
+                    "peak_kind": peak_kind},
+            "bytes_per_launch": spmv_bytes, "flops_per_launch": spmv_flops, "launch_ms": spmv_ms}
+    m_ms, m_bytes, m_flops = rmx["spmv"]
+    m_gbs = m_bytes / (m_ms * 1e-3) / 1e9
+    mixed = {
+        "value": ws * ne * rmx["iters"] / (rmx["ms"] / 1e3), "unit": UNIT,
+        "ms_per_step": rmx["ms"] / args.steps,
+        "speedup_vs_fp64_per_step": ms_step / (rmx["ms"] / args.steps),
+        "pcg_iters_per_step": rmx["iters"] / args.steps,
+        "refinements_per_step": rmx["refine"] / args.steps,
+        "cut_value": rmx["cut"], "cut_rel_diff_vs_fp64": abs(rmx["cut"] - cut_value) / cut_value,
+        "x_max_abs_diff_vs_fp64": float(np.max(np.abs(rmx["x"] - r64["x"]))),
+        "time_to_cut_1e-6": time_to_cut(rmx["track"]),
+        "gpu_launches": int(rmx["launches"]),
+        "roofline": {"bound": "hbm", "achieved": m_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": m_gbs / hbm_peak, "peak_kind": peak_kind,
+                     "kernel": "k_spmv32_dia<2> FP32 (q = L~p, compensated (p,q))",
+                     "bytes_per_launch": m_bytes, "launch_ms": m_ms},
+        "dtype": "f32 inner PCG + f64 residual/refinement (same FP64 stopping test)",
+    }
+    clk_summary = r64["clocks"]
 
     # end to end through the C ABI from host buffers
     e2e = None
@@ -312,6 +363,7 @@ def main():
         d2h = side_host.nbytes + 8 * 3 + (T_STEPS + 1) * 64
         e_iters = 0
         reps = max(1, min(args.steps, 3))
+        opt = B.pirmcut_default_options(pcg_tol=PCG_TOL, graph_launch=int(args.launch == "graph"))
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -354,10 +406,12 @@ def main():
             "cut_value": cut_value,
             "hbm_gbs_pcg_algorithmic": bytes_iter * iters / args.steps / (ms_step * 1e-3) / 1e9,
             "roofline": roof,
+            "time_to_cut_1e-6": time_to_cut(r64["track"]),
+            "mixed": mixed,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": int(launches),
-            "clocks": clk.summary(),
+            "clocks": clk_summary,
             "kernel_source": src,
         }
         print(json.dumps(line), flush=True)

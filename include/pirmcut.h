@@ -88,6 +88,8 @@ typedef struct {
                           PCG iterations in chunks of 8 with the stop flag read
                           back between chunks (for profilers that cannot see
                           into conditional graph nodes)                       */
+  double inner_tol;    /* MIXED only: each FP32 inner solve reduces its residual
+                          by this factor (or just enough for the FP64 test)   */
 } pirmcut_options;
 
 typedef struct {
@@ -99,10 +101,14 @@ typedef struct {
   double cut_value;    /* sweep-cut value after the step if track_cut, else NaN */
   double ms;           /* GPU time of the step in milliseconds                */
   int status;          /* pirmcut_status of the step                          */
+  int refinements;     /* MIXED: FP64 refinement cycles (FP64 residuals that
+                          started an inner solve); 0 for FP64                 */
 } pirmcut_step_info;
 
 /* Fill *opt with the defaults: NORTH_STAR, FP64, pcg_tol 1e-10,
- * pcg_max_iter 20000, warm_start 1, FORMAT_AUTO, track_cut 0, graph_launch 1. */
+ * pcg_max_iter 20000, warm_start 1, FORMAT_AUTO, track_cut 0, graph_launch 1,
+ * inner_tol 1e-4.  With MIXED, pcg_iters counts FP32 inner iterations, at most
+ * min(pcg_max_iter, 2000) per refinement cycle and 64 cycles per system. */
 void pirmcut_default_options(pirmcut_options* opt);
 
 /*
@@ -204,8 +210,8 @@ int64_t pirmcut_kernel_launches(const pirmcut_ctx* ctx);
 
 /*
  * Diagnostics for roofline reports: time the PCG matrix-vector kernel
- * (q = L~ p with the fused (p, q) reduction, Section 3.1) on the current
- * matrix and search direction, `reps` launches bracketed one by one with CUDA
+ * (q = L~ p with the fused (p, q) reduction, Section 3.1; the FP32 inner one
+ * for MIXED contexts) on the current matrix and search direction, `reps` launches bracketed one by one with CUDA
  * events on the context's stream.  Needs a completed step (EINVAL otherwise);
  * leaves x untouched.  avg_ms receives the mean launch time; bytes and flops
  * (either may be NULL) the algorithmic bytes moved and floating-point

@@ -31,14 +31,15 @@ class Options(ctypes.Structure):
     _fields_ = [("reweight_form", ctypes.c_int), ("precision", ctypes.c_int),
                 ("pcg_tol", ctypes.c_double), ("pcg_max_iter", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("format", ctypes.c_int),
-                ("track_cut", ctypes.c_int), ("graph_launch", ctypes.c_int)]
+                ("track_cut", ctypes.c_int), ("graph_launch", ctypes.c_int),
+                ("inner_tol", ctypes.c_double)]
 
 
 class StepInfo(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int), ("pcg_iters", ctypes.c_int), ("eps", ctypes.c_double),
                 ("rel_residual", ctypes.c_double), ("x_min", ctypes.c_double),
                 ("x_max", ctypes.c_double), ("cut_value", ctypes.c_double),
-                ("ms", ctypes.c_double), ("status", ctypes.c_int)]
+                ("ms", ctypes.c_double), ("status", ctypes.c_int), ("refinements", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -58,6 +58,7 @@ void free_device(Ctx& c) {
   for (void* p : ps)
     if (p) cudaFree(p);
   pirmcut::sweep_free(c);
+  pirmcut::mixed_free(c);
   if (c.g_init) cudaGraphExecDestroy(c.g_init);
   if (c.g_step) cudaGraphExecDestroy(c.g_step);
   if (c.g_cut) cudaGraphExecDestroy(c.g_cut);
@@ -70,8 +71,12 @@ pirmcut_status check_options(const pirmcut_options& o, std::string* msg) {
     *msg = "unknown reweight_form";
     return PIRMCUT_EINVAL;
   }
-  if (o.precision != PIRMCUT_PREC_FP64) {
-    *msg = "only PIRMCUT_PREC_FP64 is available in this build";
+  if (o.precision != PIRMCUT_PREC_FP64 && o.precision != PIRMCUT_PREC_MIXED) {
+    *msg = "unknown precision";
+    return PIRMCUT_EINVAL;
+  }
+  if (o.precision == PIRMCUT_PREC_MIXED && (!(o.inner_tol > 0.0) || !(o.inner_tol < 1.0))) {
+    *msg = "inner_tol must be in (0, 1)";
     return PIRMCUT_EINVAL;
   }
   if (!(o.pcg_tol > 0.0) || !std::isfinite(o.pcg_tol)) {
@@ -156,8 +161,13 @@ pirmcut_status ensure_capacity(pirmcut_ctx* h, int steps) {
 
 pirmcut_status ensure_graphs(pirmcut_ctx* h, bool need_cut) {
   Ctx& c = h->c;
-  if (!c.g_init) CK(h, pirmcut::build_step_graph(c, true, &c.g_init, &c.nodes_init), "building the x0 graph");
-  if (!c.g_step) CK(h, pirmcut::build_step_graph(c, false, &c.g_step, &c.nodes_step), "building the step graph");
+  const bool mixed = c.opt.precision == PIRMCUT_PREC_MIXED;
+  if (!c.g_init)
+    CK(h, mixed ? pirmcut::build_step_graph_mixed(c, true, &c.g_init, &c.nodes_init)
+                : pirmcut::build_step_graph(c, true, &c.g_init, &c.nodes_init), "building the x0 graph");
+  if (!c.g_step)
+    CK(h, mixed ? pirmcut::build_step_graph_mixed(c, false, &c.g_step, &c.nodes_step)
+                : pirmcut::build_step_graph(c, false, &c.g_step, &c.nodes_step), "building the step graph");
   if (need_cut) {
     CK(h, pirmcut::sweep_alloc(c), "sweep buffers");
     if (!c.g_cut) CK(h, pirmcut::build_cut_graph(c, &c.g_cut, &c.nodes_cut), "building the sweep graph");
@@ -184,10 +194,10 @@ void fill_info(const Ctx& c, const pirmcut::StepRec& r, float ms, pirmcut_step_i
   info->cut_value = r.cut;
   info->ms = ms;
   int st = r.status;
-  if (st == PIRMCUT_OK && r.iters >= c.opt.pcg_max_iter && r.bb > 0.0 &&
-      !(r.rr <= c.opt.pcg_tol * c.opt.pcg_tol * r.bb))
+  if (st == PIRMCUT_OK && r.bb > 0.0 && !(r.rr <= c.opt.pcg_tol * c.opt.pcg_tol * r.bb))
     st = PIRMCUT_ENOCONV;
   info->status = st;
+  info->refinements = r.refine;
 }
 
 // Run x^(0) (when with_initial) and the eps steps already in eps_list[0..T).
@@ -218,7 +228,11 @@ pirmcut_status run_steps(pirmcut_ctx* h, bool with_initial, int T, int first_ste
       c.launches += init ? c.nodes_init : c.nodes_step;
     } else {
       int64_t kernels = 0;
-      CK(h, pirmcut::run_step_stream(c, init, h->h_stop, &kernels), "step launch");
+      if (c.opt.precision == PIRMCUT_PREC_MIXED) {
+        CK(h, pirmcut::run_step_stream_mixed(c, init, h->h_stop, &kernels), "step launch");
+      } else {
+        CK(h, pirmcut::run_step_stream(c, init, h->h_stop, &kernels), "step launch");
+      }
       c.launches += kernels;
     }
     if (c.opt.track_cut) {
@@ -237,7 +251,8 @@ pirmcut_status run_steps(pirmcut_ctx* h, bool with_initial, int T, int first_ste
     cudaEventElapsedTime(&ms, h->events[k], h->events[k + 1]);
     pirmcut_step_info info;
     fill_info(c, c.h_recs[k], ms, &info);
-    if (graphs) c.launches += 3LL * info.pcg_iters;
+    if (graphs)
+      c.launches += 3LL * info.pcg_iters + 2LL * info.refinements;
     if (infos) infos[k] = info;
     if (info.status == PIRMCUT_ENUMERIC) worst = PIRMCUT_ENUMERIC;
     else if (info.status == PIRMCUT_ENOCONV && worst == PIRMCUT_OK) worst = PIRMCUT_ENOCONV;
@@ -266,6 +281,7 @@ void pirmcut_default_options(pirmcut_options* opt) {
   opt->format = PIRMCUT_FORMAT_AUTO;
   opt->track_cut = 0;
   opt->graph_launch = 1;
+  opt->inner_tol = 1e-4;
 }
 
 pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* col,
@@ -342,6 +358,8 @@ pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* 
   if ((e = dalloc(&cx.S, 1)) != cudaSuccess) return bail(e, "cudaMalloc");
   if ((e = dalloc(&cx.C, 1)) != cudaSuccess) return bail(e, "cudaMalloc");
   if ((e = cudaMemset(cx.S, 0, sizeof(pirmcut::PcgState))) != cudaSuccess) return bail(e, "cudaMemset");
+  if (o.precision == PIRMCUT_PREC_MIXED && (e = pirmcut::mixed_alloc(cx)) != cudaSuccess)
+    return bail(e, "cudaMalloc");
   if ((e = cudaMemset(cx.C, 0, sizeof(pirmcut::StepCounters))) != cudaSuccess) return bail(e, "cudaMemset");
   if ((e = cudaHostAlloc((void**)&h->h_ctr, sizeof(pirmcut::StepCounters) + 8 * sizeof(double),
                          cudaHostAllocDefault)) != cudaSuccess)
@@ -531,23 +549,29 @@ pirmcut_status pirmcut_time_spmv(pirmcut_ctx* h, int reps, double* avg_ms, doubl
   const double nt = double(c.nt);
   const double nnz = c.format == PIRMCUT_FORMAT_DIA ? 2.0 * double(c.hg.n_edges)
                                                      : double(c.hg.col.size());
+  const bool mx = c.opt.precision == PIRMCUT_PREC_MIXED;
+  const double V = mx ? 4.0 : 8.0;
+  // vectors read/written once per row: diag, p, q (the FP32 inner system is
+  // scaled to unit diagonal: p and q only)
+  const double nvec = mx ? 2.0 : 3.0;
   if (bytes) {
-    *bytes = c.format == PIRMCUT_FORMAT_DIA
-                 ? nt * (8.0 * c.K + 8.0 * 3)                        // g (upper), diag, p, q
-                 : nnz * (8.0 + 4.0) + nt * (8.0 * 3 + 8.0);         // g, col, diag, p, q, row_ptr
+    *bytes = c.format == PIRMCUT_FORMAT_DIA ? nt * (V * c.K + V * nvec)
+                                            : nnz * (V + 4.0) + nt * (V * nvec + 8.0);
   }
-  if (flops) *flops = 2.0 * (nnz + 2.0 * nt);                        // nnz + diagonal FMAs + (p, q)
+  // nnz + diagonal FMAs (an add when scaled), plus the (p, q) FMA per row
+  if (flops) *flops = 2.0 * (nnz + 2.0 * nt);
   // the solve left stop_req set: clear it so the kernel runs, restore after
   const size_t off_stop = offsetof(pirmcut::PcgState, stop_req);
   int one = 1, zero = 0;
   CK(h, cudaMemcpyAsync(reinterpret_cast<char*>(c.S) + off_stop, &zero, sizeof(int), cudaMemcpyHostToDevice, c.stream), "time");
   cudaEvent_t a = event_at(h, 0), b = event_at(h, 1);
   if (!a || !b) return fail(h, PIRMCUT_ECUDA, "cudaEventCreate failed");
-  CK(h, pirmcut::launch_spmv_once(c), "spmv");  // warm-up
+  const bool m = c.opt.precision == PIRMCUT_PREC_MIXED;
+  CK(h, m ? pirmcut::launch_spmv32_once(c) : pirmcut::launch_spmv_once(c), "spmv");  // warm-up
   double total = 0.0;
   for (int k = 0; k < reps; ++k) {
     CK(h, cudaEventRecord(a, c.stream), "event");
-    CK(h, pirmcut::launch_spmv_once(c), "spmv");
+    CK(h, m ? pirmcut::launch_spmv32_once(c) : pirmcut::launch_spmv_once(c), "spmv");
     CK(h, cudaEventRecord(b, c.stream), "event");
     CK(h, cudaEventSynchronize(b), "event");
     float ms = 0.f;

@@ -21,7 +21,22 @@ struct StepRec {
   double xmin, xmax;
   double cut;
   int status;
-  int pad;
+  int refine;   // FP64 refinement cycles (mixed precision), 0 otherwise
+};
+
+// State of the FP64 iterative-refinement loop around the FP32 inner PCG.
+struct OuterState {
+  double rr64;      // ||b - L~ x||^2 in FP64 at the last loop head
+  double bb;        // ||b||^2
+  double tol2;      // pcg_tol^2
+  double eta2;      // inner_tol^2
+  int outer_iters;  // refinement cycles run in this solve
+  int max_outer;
+  int total_inner;  // FP32 PCG iterations summed over cycles
+  int outer_stop;
+  int status;
+  int inner_maxit;
+  unsigned int counter[2];
 };
 
 // Counters that sequence the steps of one solve on the device.
@@ -84,6 +99,17 @@ struct Ctx {
   double* dinv = nullptr;
   double* partials = nullptr;   // 4 * kMaxBlocks
   PcgState* S = nullptr;
+  // mixed precision: FP32 CG on the Jacobi-scaled system D^-1/2 L~ D^-1/2
+  // (unit diagonal) inside FP64 iterative refinement
+  float* g32 = nullptr;         // scaled conductances g_uv / sqrt(d_u d_v) (DIA K*nt or CSR nnz)
+  double* s64 = nullptr;        // d_v^-1/2
+  float* s32 = nullptr;
+  float* r32 = nullptr;         // scaled inner residual
+  float* p32 = nullptr;
+  float* q32 = nullptr;
+  float* d32 = nullptr;         // scaled correction
+  double* b64 = nullptr;        // right-hand side (FP64)
+  OuterState* O = nullptr;
   StepCounters* C = nullptr;
   double* eps_list = nullptr;   // capacity eps_cap
   int eps_cap = 0;
@@ -109,11 +135,23 @@ struct Ctx {
 };
 
 // pcg.cu
+inline int row_grid(const Ctx& c) {
+  const int64_t threads = c.format == PIRMCUT_FORMAT_DIA ? c.nt : c.nt * c.group;
+  return grid_for(threads);
+}
+int enqueue_reweight(Ctx& c, cudaStream_t st, bool initial);
+int enqueue_step_end(Ctx& c, cudaStream_t st, bool initial, const OuterState* O);
 cudaError_t build_step_graph(Ctx& c, bool initial, cudaGraphExec_t* out, int* nodes);
 cudaError_t run_step_stream(Ctx& c, bool initial, int* stop_flag_host, int64_t* kernels);
 cudaError_t launch_scatter_x(Ctx& c, double* xfull);           // reduced x -> full n
 cudaError_t launch_gather_x(Ctx& c, const double* xfull);      // full n -> reduced x
 cudaError_t launch_spmv_once(Ctx& c);                          // one standalone SpMV launch
+// mixed.cu
+cudaError_t mixed_alloc(Ctx& c);
+void mixed_free(Ctx& c);
+cudaError_t build_step_graph_mixed(Ctx& c, bool initial, cudaGraphExec_t* out, int* nodes);
+cudaError_t run_step_stream_mixed(Ctx& c, bool initial, int* flag_host, int64_t* kernels);
+cudaError_t launch_spmv32_once(Ctx& c);
 // sweep.cu
 cudaError_t sweep_alloc(Ctx& c);
 cudaError_t build_cut_graph(Ctx& c, cudaGraphExec_t* out, int* nodes);

@@ -112,6 +112,35 @@ __device__ __forceinline__ double conductance(double c, double d, double eps2, i
   return c * rsqrt(fma(d, d, eps2));
 }
 
+// Compile-time dispatch of the DIA width K (1..8) and the CSR group size G.
+#define PIRMCUT_DISPATCH_K(KVAR, CALL) \
+  switch (KVAR) {                      \
+    case 1: { constexpr int KK = 1; CALL; } break; \
+    case 2: { constexpr int KK = 2; CALL; } break; \
+    case 3: { constexpr int KK = 3; CALL; } break; \
+    case 4: { constexpr int KK = 4; CALL; } break; \
+    case 5: { constexpr int KK = 5; CALL; } break; \
+    case 6: { constexpr int KK = 6; CALL; } break; \
+    case 7: { constexpr int KK = 7; CALL; } break; \
+    default: { constexpr int KK = 8; CALL; } break; \
+  }
+
+#define PIRMCUT_DISPATCH_G(GVAR, CALL) \
+  switch (GVAR) {                      \
+    case 1: { constexpr int GG = 1; CALL; } break; \
+    case 2: { constexpr int GG = 2; CALL; } break; \
+    case 4: { constexpr int GG = 4; CALL; } break; \
+    case 8: { constexpr int GG = 8; CALL; } break; \
+    case 16: { constexpr int GG = 16; CALL; } break; \
+    default: { constexpr int GG = 32; CALL; } break; \
+  }
+
+// Lane mask of the G-thread group that owns a row (G divides 32).
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+  return (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
+}
+
 inline int grid_for(int64_t n, int threads = kThreads) {
   int64_t b = (n + threads - 1) / threads;
   if (b > kMaxBlocks) b = kMaxBlocks;

@@ -352,7 +352,8 @@ __device__ __forceinline__ double warp_max(double v) {
 
 __global__ void __launch_bounds__(kThreads)
 k_step_end(int64_t nt, double* __restrict__ x, PcgState* S, StepCounters* C, StepRec* recs,
-           const double* __restrict__ eps_list, int consumes_eps, double* partials) {
+           const double* __restrict__ eps_list, int consumes_eps, double* partials,
+           const OuterState* O) {
   __shared__ double smn[32], smx[32];
   __shared__ unsigned int s_last;
   const bool zero = S->bb == 0.0;  // b = 0: the solution of L~ v = b is v = 0
@@ -419,7 +420,7 @@ k_step_end(int64_t nt, double* __restrict__ x, PcgState* S, StepCounters* C, Ste
   rec.xmax = mx;
   rec.cut = NAN;
   rec.status = S->status;
-  rec.pad = 0;
+  rec.refine = O ? O->outer_iters : 0;
   recs[C->rec_idx] = rec;
   C->rec_idx += 1;
   C->step += 1;
@@ -461,33 +462,6 @@ __global__ void k_gather_x(int64_t nt, int32_t s, int32_t t, const double* __res
 // ---------------------------------------------------------------------------
 
 
-#define PIRMCUT_DISPATCH_K(KVAR, CALL) \
-  switch (KVAR) {                      \
-    case 1: { constexpr int KK = 1; CALL; } break; \
-    case 2: { constexpr int KK = 2; CALL; } break; \
-    case 3: { constexpr int KK = 3; CALL; } break; \
-    case 4: { constexpr int KK = 4; CALL; } break; \
-    case 5: { constexpr int KK = 5; CALL; } break; \
-    case 6: { constexpr int KK = 6; CALL; } break; \
-    case 7: { constexpr int KK = 7; CALL; } break; \
-    default: { constexpr int KK = 8; CALL; } break; \
-  }
-
-#define PIRMCUT_DISPATCH_G(GVAR, CALL) \
-  switch (GVAR) {                      \
-    case 1: { constexpr int GG = 1; CALL; } break; \
-    case 2: { constexpr int GG = 2; CALL; } break; \
-    case 4: { constexpr int GG = 4; CALL; } break; \
-    case 8: { constexpr int GG = 8; CALL; } break; \
-    case 16: { constexpr int GG = 16; CALL; } break; \
-    default: { constexpr int GG = 32; CALL; } break; \
-  }
-
-int row_grid(const Ctx& c) {
-  const int64_t threads = c.format == PIRMCUT_FORMAT_DIA ? c.nt : c.nt * c.group;
-  return grid_for(threads);
-}
-
 }  // namespace
 
 cudaError_t launch_scatter_x(Ctx& c, double* xfull) {
@@ -517,29 +491,48 @@ cudaError_t launch_spmv_once(Ctx& c) {
 
 namespace {
 
+}  // namespace
+
+// Step 1 (reweighting) into the FP64 conductance array; for x^(0) the
+// capacities are copied instead (W^(0) = C).  Returns the kernels enqueued.
+int enqueue_reweight(Ctx& c, cudaStream_t st, bool initial) {
+  const int grid = row_grid(c);
+  double* g = c.format == PIRMCUT_FORMAT_DIA ? c.gdia : c.gval;
+  const double* cap = c.format == PIRMCUT_FORMAT_DIA ? c.cdia : c.cval;
+  const size_t gbytes = sizeof(double) * (c.format == PIRMCUT_FORMAT_DIA
+                                              ? size_t(c.K) * c.nt
+                                              : size_t(c.hg.rp.empty() ? 0 : c.hg.rp.back()));
+  if (initial) {
+    cudaMemcpyAsync(g, cap, gbytes, cudaMemcpyDeviceToDevice, st);
+    return 0;
+  }
+  if (c.format == PIRMCUT_FORMAT_DIA) {
+    PIRMCUT_DISPATCH_K(c.K, (k_reweight_dia<KK><<<grid, kThreads, 0, st>>>(
+                                c.dd, c.cdia, c.x, c.eps_list, c.C, c.opt.reweight_form, c.gdia)));
+  } else {
+    PIRMCUT_DISPATCH_G(c.group, (k_reweight_csr<GG><<<grid, kThreads, 0, st>>>(
+                                    c.nt, c.rp, c.col, c.cval, c.x, c.eps_list, c.C,
+                                    c.opt.reweight_form, c.gval)));
+  }
+  return 1;
+}
+
+// Epilogue of a step: range of x and the step record.
+int enqueue_step_end(Ctx& c, cudaStream_t st, bool initial, const OuterState* O) {
+  k_step_end<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.x, c.S, c.C, c.recs, c.eps_list,
+                                                  initial ? 0 : 1, c.partials, O);
+  return 1;
+}
+
+namespace {
+
 // Kernels of a step before the PCG loop: [c -> g | reweight] -> assemble -> [x = 0].
 int enqueue_prologue(Ctx& c, cudaStream_t st, bool initial, cudaGraphConditionalHandle h,
                      int use_cond) {
   const int grid = row_grid(c);
   const bool zero_start = initial || !c.opt.warm_start;
   double* g = c.format == PIRMCUT_FORMAT_DIA ? c.gdia : c.gval;
-  const double* cap = c.format == PIRMCUT_FORMAT_DIA ? c.cdia : c.cval;
-  const size_t gbytes = sizeof(double) * (c.format == PIRMCUT_FORMAT_DIA
-                                              ? size_t(c.K) * c.nt
-                                              : size_t(c.hg.rp.empty() ? 0 : c.hg.rp.back()));
-  int kernels = 0;
-  if (initial) {
-    cudaMemcpyAsync(g, cap, gbytes, cudaMemcpyDeviceToDevice, st);
-  } else if (c.format == PIRMCUT_FORMAT_DIA) {
-    PIRMCUT_DISPATCH_K(c.K, (k_reweight_dia<KK><<<grid, kThreads, 0, st>>>(
-                                c.dd, c.cdia, c.x, c.eps_list, c.C, c.opt.reweight_form, c.gdia)));
-    ++kernels;
-  } else {
-    PIRMCUT_DISPATCH_G(c.group, (k_reweight_csr<GG><<<grid, kThreads, 0, st>>>(
-                                    c.nt, c.rp, c.col, c.cval, c.x, c.eps_list, c.C,
-                                    c.opt.reweight_form, c.gval)));
-    ++kernels;
-  }
+  int kernels = enqueue_reweight(c, st, initial);
   AssembleArgs a;
   a.cs = c.cs;
   a.ct = c.ct;
@@ -583,12 +576,6 @@ int enqueue_iteration(Ctx& c, cudaStream_t st, cudaGraphConditionalHandle h, int
   k_update_r<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.q, c.dinv, c.r, c.partials, c.S);
   k_update_xp<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.x, c.p, c.q, c.S, h, use_cond);
   return 3;
-}
-
-int enqueue_epilogue(Ctx& c, cudaStream_t st, bool initial) {
-  k_step_end<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.x, c.S, c.C, c.recs, c.eps_list,
-                                                  initial ? 0 : 1, c.partials);
-  return 1;
 }
 
 }  // namespace
@@ -639,7 +626,7 @@ cudaError_t build_step_graph(Ctx& c, bool initial, cudaGraphExec_t* out, int* no
   }
   if (e == cudaSuccess)
     e = cudaStreamUpdateCaptureDependencies(st, &cond_node, nullptr, 1, cudaStreamSetCaptureDependencies);
-  if (e == cudaSuccess) n_nodes += enqueue_epilogue(c, st, initial);
+  if (e == cudaSuccess) n_nodes += enqueue_step_end(c, st, initial, nullptr);
   cudaGraph_t captured = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(st, &captured);
   if (e == cudaSuccess) e = e2;
@@ -667,7 +654,7 @@ cudaError_t run_step_stream(Ctx& c, bool initial, int* stop_flag_host, int64_t* 
     if (guard > c.opt.pcg_max_iter / 8 + 2) break;  // the device caps iterations; belt and braces
   }
   if (e == cudaSuccess) {
-    k += enqueue_epilogue(c, st, initial);
+    k += enqueue_step_end(c, st, initial, nullptr);
     e = cudaGetLastError();
   }
   *kernels = k;

@@ -55,6 +55,9 @@ GRAPHS = [
     ("grid37x41", lambda: gen.segmentation_grid(
         np.clip(gen.image_disks_2d(37, 41, [(18, 20, 9)]) + np.random.default_rng(7).normal(0, .05, (41, 37)), 0, 1))),
     ("vol9", lambda: gen.config_graph(3, scale=9)),
+    ("vol8", lambda: gen.config_graph(3, scale=8)),          # n~ % 4 == 0: vectorised kernels
+    ("grid12x20", lambda: gen.segmentation_grid(
+        np.clip(gen.image_disks_2d(12, 20, [(6, 9, 4)]) + np.random.default_rng(8).normal(0, .05, (20, 12)), 0, 1))),
     ("random12", lambda: gen.random_graph(12, 0.3, 11, zero_frac=0.2, st_edge=True)),
     ("random40", lambda: gen.random_graph(40, 0.1, 12)),
     ("chunglu", lambda: gen.chung_lu_instance(3000, 5)),
@@ -322,3 +325,77 @@ def test_stream_launch_matches_graph_launch(P, fmt):
             out.append((s.get_x(), [i.pcg_iters for i in infos], s.cut()[1]))
     assert np.array_equal(out[0][0], out[1][0])
     assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
+
+
+# ---------------------------------------------------------------------------
+# mixed precision: FP32 inner PCG, FP64 refinement to the same FP64 criterion
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("fmt", [0, 2])
+def test_mixed_teacher_forced_steps_grid64(P, fmt):
+    """Every IRLS step of the 64x64 workload with the mixed-precision solver:
+    the FP64 residual test at 1e-13 makes x agree with the exact WLS solution
+    to the same 1e-9 bar as the FP64 path."""
+    g = gen.config_graph(1)
+    prob = O.Problem.from_graph(g)
+    T = 50
+    eps = O.eps_schedule(T)
+    xs, _ = O.irls(prob, T, eps)
+    with solver(P, g, format=fmt, precision=1) as s:
+        for l in range(1, T + 1):
+            s.set_x(xs[l - 1])
+            info = s.irls_step(eps[l - 1])
+            assert info.status == 0, (l, info.status)
+            assert info.rel_residual <= 1e-13
+            assert np.max(np.abs(s.get_x() - xs[l])) <= XTOL, l
+
+
+@pytest.mark.parametrize("name,make", GRAPHS)
+def test_mixed_x0_and_steps_small(P, name, make):
+    g = make()
+    prob = O.Problem.from_graph(g)
+    T = 12
+    eps = O.eps_schedule(T)
+    xs, _ = O.irls(prob, T, eps)
+    with solver(P, g, precision=1) as s:
+        info = s.initial()
+        assert info.status == 0 and info.refinements >= 1
+        assert np.max(np.abs(s.get_x() - xs[0])) <= XTOL
+        for l in range(1, T + 1):
+            s.set_x(xs[l - 1])
+            s.irls_step(eps[l - 1])
+            assert np.max(np.abs(s.get_x() - xs[l])) <= XTOL, l
+
+
+def test_mixed_free_running_matches_fp64(P):
+    """Algorithm 1 on grid64 at the workload's tolerance (1e-10): the mixed
+    solver's cut equals the oracle's and its iterate stays within 1e-6 of the
+    FP64 GPU path's."""
+    g = gen.config_graph(1)
+    prob = O.Problem.from_graph(g)
+    T = 50
+    eps = O.eps_schedule(T)
+    xs, _ = O.irls(prob, T, eps)
+    with P.Solver(g, pcg_tol=1e-10) as s:
+        s.solve(T, eps)
+        x64 = s.get_x()
+    with P.Solver(g, pcg_tol=1e-10, precision=1) as s:
+        infos = s.solve(T, eps)
+        assert all(i.status == 0 and i.rel_residual <= 1e-10 for i in infos)
+        xm = s.get_x()
+        side, value, tau = s.cut()
+    assert np.max(np.abs(xm - x64)) <= 1e-6
+    check_cut(prob, xs[-1], side, value, tau)
+
+
+@pytest.mark.parametrize("fmt", [0, 2])
+def test_mixed_stream_matches_graph(P, fmt):
+    g = gen.config_graph(1, scale=40)
+    eps = O.eps_schedule(12)
+    out = []
+    for mode in (1, 0):
+        with P.Solver(g, format=fmt, graph_launch=mode, precision=1) as s:
+            infos = s.solve(12, eps)
+            out.append((s.get_x(), [(i.pcg_iters, i.refinements) for i in infos]))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
