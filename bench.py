@@ -216,6 +216,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=15.0)
+    ap.add_argument("--inner-tol", type=float, default=1e-5,
+                    help="mixed path: relative reduction of each FP32 inner solve")
     ap.add_argument("--only", default=None, choices=["fp64", "mixed"],
                     help="time one path only (profiling runs)")
     ap.add_argument("--launch", default="graph", choices=["graph", "stream"],
@@ -248,7 +250,7 @@ def main():
     def timed(precision, with_clocks):
         """Warm-up, then K timed steps of one path; returns its measurements."""
         opt = B.pirmcut_default_options(pcg_tol=PCG_TOL, graph_launch=int(args.launch == "graph"),
-                                        precision=precision)
+                                        precision=precision, inner_tol=args.inner_tol)
         solver = B.Solver(g, opt, stream=stream)
 
         def step():

@@ -107,7 +107,7 @@ typedef struct {
 
 /* Fill *opt with the defaults: NORTH_STAR, FP64, pcg_tol 1e-10,
  * pcg_max_iter 20000, warm_start 1, FORMAT_AUTO, track_cut 0, graph_launch 1,
- * inner_tol 1e-4.  With MIXED, pcg_iters counts FP32 inner iterations, at most
+ * inner_tol 1e-5.  With MIXED, pcg_iters counts FP32 inner iterations, at most
  * min(pcg_max_iter, 2000) per refinement cycle and 64 cycles per system. */
 void pirmcut_default_options(pirmcut_options* opt);
 

@@ -32,8 +32,9 @@ def nvcc() -> str:
 def _compile(src: str) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     path = os.path.join(CSRC, src)
+    extra = os.environ.get("PIRMCUT_NVCC_FLAGS", "").split()  # optional tuning defines
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-           "-I", INCLUDE, "-I", CSRC, "-c", path, "-o", obj]
+           "-I", INCLUDE, "-I", CSRC, *extra, "-c", path, "-o", obj]
     if src.endswith(".cpp"):
         cmd = [nvcc(), "-x", "c++", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
                "-I", INCLUDE, "-I", CSRC, "-c", path, "-o", obj]

@@ -281,7 +281,7 @@ void pirmcut_default_options(pirmcut_options* opt) {
   opt->format = PIRMCUT_FORMAT_AUTO;
   opt->track_cut = 0;
   opt->graph_launch = 1;
-  opt->inner_tol = 1e-4;
+  opt->inner_tol = 1e-5;
 }
 
 pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* col,

@@ -33,9 +33,21 @@
 
 #include "ctx.h"
 
+// Minimum resident blocks per SM requested for the FP32 inner kernels
+// (register cap = 65536 / (256 * this)); chosen by measurement.
+#ifndef PIRMCUT_INNER_MINB
+#define PIRMCUT_INNER_MINB 1
+#endif
+// Unroll factor of the vectorised SpMV's row loop (more loads in flight).
+#ifndef PIRMCUT_SPMV_UNROLL
+#define PIRMCUT_SPMV_UNROLL 1
+#endif
+
 namespace pirmcut {
 
 namespace {
+
+constexpr int kSpmvUnroll = PIRMCUT_SPMV_UNROLL;
 
 __device__ __forceinline__ int64_t gtid() { return int64_t(blockIdx.x) * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t gstride() { return int64_t(gridDim.x) * blockDim.x; }
@@ -438,7 +450,7 @@ k_spmv32_dia(DiaDesc d, const float* __restrict__ g, const float* __restrict__ p
 // For offset 1 the neighbours of rows i..i+3 come from the same float4 plus one
 // scalar at each end.
 template <int K>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, PIRMCUT_INNER_MINB)
 k_spmv32v_dia(DiaDesc d, const float* __restrict__ g, const float* __restrict__ p,
               float* __restrict__ q, double* partials, PcgState* S) {
   if (S->stop_req) {
@@ -447,6 +459,7 @@ k_spmv32v_dia(DiaDesc d, const float* __restrict__ g, const float* __restrict__ 
   }
   const int64_t nt = d.nt, n4 = nt >> 2;
   FF pq{0.f, 0.f};
+#pragma unroll kSpmvUnroll
   for (int64_t t = gtid(); t < n4; t += gstride()) {
     const int64_t i0 = t << 2;
     const float4 p4 = ld4(p + i0);
@@ -545,7 +558,7 @@ __device__ __forceinline__ void update32_finish(FF rr, double* partials, PcgStat
 
 // r -= alpha q; ||r||^2 -> beta and the stop test.  vec selects the float4
 // loop (n~ % 4 == 0).
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, PIRMCUT_INNER_MINB)
 k_update32_r(int64_t nt, int vec, const float* __restrict__ q, float* __restrict__ r,
              double* partials, PcgState* S) {
   if (S->stop_req) return;
@@ -574,7 +587,7 @@ k_update32_r(int64_t nt, int vec, const float* __restrict__ q, float* __restrict
 }
 
 // d += alpha p; p = r + beta p.  Ends the inner loop once a stop was requested.
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, PIRMCUT_INNER_MINB)
 k_update32_xp(int64_t nt, int vec, float* __restrict__ d, float* __restrict__ p,
               const float* __restrict__ r, PcgState* S, cudaGraphConditionalHandle h, int use_cond) {
   if (!S->stopped) {
