@@ -12,6 +12,7 @@ from .graphs import (  # noqa: F401
     segmentation_grid,
     random_graph,
     chung_lu_instance,
+    chung_lu_batch,
     config_graph,
     perturb_capacities,
     permute_graph,

@@ -194,7 +194,7 @@ def random_graph(n_nt: int, p_edge: float, seed: int, p_term: float = 0.5,
 def chung_lu_instance(n: int, seed: int, exponent: float = 2.5,
                       avg_degree: float = 10.0, seed_frac: float = 0.05,
                       s_scale: float = 1.0, t_scale: float = 0.05,
-                      cmin: float = 0.5, cmax: float = 1.5) -> Graph:
+                      cmin: float = 0.5, cmax: float = 1.5, float32_caps: bool = False) -> Graph:
     """FlowImprove-style instance on a Chung-Lu power-law graph.
 
     Expected degrees w_i proportional to (i + 1)^(-1/(exponent-1)), scaled to
@@ -202,8 +202,10 @@ def chung_lu_instance(n: int, seed: int, exponent: float = 2.5,
     min(1, w_i w_j / sum(w)) via a per-vertex Bernoulli sweep (sampled as a
     Poisson number of endpoint draws, duplicates and self-loops removed).
     The largest connected component is kept and relabelled.  Edge capacities
-    are U[cmin, cmax].  A seed set is grown by BFS from a random vertex
-    (neighbours in index order) until ceil(seed_frac * n) vertices; s ties to
+    are U[cmin, cmax] (rounded to float32 when ``float32_caps``).  A seed set
+    is grown by BFS from a random vertex (neighbours in index order, the
+    vertex count taken over the kept component) until ceil(seed_frac * n)
+    vertices; s ties to
     every seed vertex with capacity s_scale * d_v and t ties to every other
     vertex with capacity t_scale * d_v, d_v being the weighted degree.
     """
@@ -220,44 +222,28 @@ def chung_lu_instance(n: int, seed: int, exponent: float = 2.5,
     lo, hi = np.minimum(a, b), np.maximum(a, b)
     key = np.unique(lo.astype(np.int64) * n + hi)
     u, v = key // n, key % n
-    # largest connected component (union-find over edges)
-    parent = np.arange(n)
-
-    def find(x):
-        while parent[x] != x:
-            parent[x] = parent[parent[x]]
-            x = parent[x]
-        return x
-    for x, y in zip(u, v):
-        rx, ry = find(x), find(y)
-        if rx != ry:
-            parent[rx] = ry
-    roots = np.array([find(x) for x in range(n)])
-    big = np.bincount(roots).argmax()
-    keepv = np.nonzero(roots == big)[0]
+    # largest connected component
+    import scipy.sparse as sp
+    import scipy.sparse.csgraph as csg
+    adj = sp.csr_matrix((np.ones(u.shape[0]), (u, v)), shape=(n, n))
+    ncomp, lab = csg.connected_components(adj, directed=False)
+    big = np.bincount(lab).argmax()
+    keepv = np.nonzero(lab == big)[0]
     relabel = -np.ones(n, dtype=np.int64)
     relabel[keepv] = np.arange(keepv.shape[0])
     ke = (relabel[u] >= 0) & (relabel[v] >= 0)
     u, v = relabel[u[ke]], relabel[v[ke]]
     nn = keepv.shape[0]
     cap = rng.uniform(cmin, cmax, u.shape[0])
+    if float32_caps:
+        cap = cap.astype(np.float32).astype(np.float64)
     deg = np.bincount(u, weights=cap, minlength=nn) + np.bincount(v, weights=cap, minlength=nn)
     rp, cl, _ = csr_from_edges(nn, u, v, cap)
     start = int(rng.integers(nn))
     want = int(np.ceil(seed_frac * nn))
-    seen = np.zeros(nn, dtype=bool)
-    seen[start] = True
-    order = [start]
-    head = 0
-    while head < len(order) and len(order) < want:
-        x = order[head]
-        head += 1
-        for y in cl[rp[x]:rp[x + 1]]:
-            if not seen[y]:
-                seen[y] = True
-                order.append(int(y))
-                if len(order) >= want:
-                    break
+    # BFS order from the start vertex, neighbours in index order
+    sym = sp.csr_matrix((np.ones(cl.shape[0]), cl, rp), shape=(nn, nn))
+    order = csg.breadth_first_order(sym, start, directed=False, return_predecessors=False)[:want]
     in_seed = np.zeros(nn, dtype=bool)
     in_seed[order] = True
     s, t = nn, nn + 1
@@ -269,6 +255,17 @@ def chung_lu_instance(n: int, seed: int, exponent: float = 2.5,
     c_all = np.concatenate([cap, s_scale * deg[seedv], t_scale * deg[rest]])
     row_ptr, col, c = csr_from_edges(nn + 2, u_all, v_all, c_all)
     return Graph(nn + 2, row_ptr, col, c, s, t, name=f"chunglu{n}_{seed}")
+
+
+def chung_lu_batch(count: int = 64, seed: int = 4, nmin: float = 1e4, nmax: float = 1e6,
+                   **kw) -> list:
+    """``count`` Chung-Lu FlowImprove-style instances with sizes n_i drawn
+    log-uniformly in [nmin, nmax] (rounded), instance i seeded with seed*1000+i,
+    float32 capacities."""
+    rng = np.random.default_rng(seed)
+    sizes = np.round(10.0 ** rng.uniform(np.log10(nmin), np.log10(nmax), count)).astype(np.int64)
+    return [chung_lu_instance(int(sizes[i]), seed * 1000 + i, float32_caps=True, **kw)
+            for i in range(count)]
 
 
 def perturb_capacities(g: Graph, seed: int, sigma: float = 0.01) -> Graph:

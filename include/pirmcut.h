@@ -262,6 +262,42 @@ pirmcut_status pirmcut_sweep_cut_static(int64_t n, const int64_t* row_ptr, const
                                         const double* c, int32_t s, int32_t t, const double* x,
                                         uint8_t* side, double* result, void* stream);
 
+/*
+ * Batches of independent instances (Section 6: sequences and batches of
+ * related FlowImprove problems).  All instances of a batch are solved together:
+ * every kernel launch covers all of them, each instance keeps its own PCG
+ * scalars and stopping test, and one CUDA graph per IRLS step runs until every
+ * instance has converged.  FP64 solver, CSR storage; options as for
+ * pirmcut_create (precision must be FP64).
+ *
+ * pirmcut_batch_create: count instances; n[i], row_ptr[i], col[i], c[i],
+ * s[i], t[i] describe instance i exactly as the arguments of pirmcut_create
+ * (host memory).  At creation an autotuner times the batched SpMV for several
+ * (threads per row, tile height) pairs and keeps the fastest.
+ * Errors: EINVAL (with the failing instance in the message), EDISCONNECTED,
+ * ENOMEM, ECUDA.
+ */
+typedef struct pirmcut_batch pirmcut_batch;
+pirmcut_status pirmcut_batch_create(int count, const int64_t* n, const int64_t* const* row_ptr,
+                                    const int32_t* const* col, const double* const* c,
+                                    const int32_t* s, const int32_t* t, const pirmcut_options* opt,
+                                    void* stream, pirmcut_batch** out);
+/* x^(0) and T IRLS steps for every instance (Algorithm 1 steps 2-4).  infos
+ * (may be NULL) receives count * (T+1) records, instance-major; their ms field
+ * is the step's time for the whole batch. */
+pirmcut_status pirmcut_batch_solve(pirmcut_batch* b, int T, const double* eps,
+                                   pirmcut_step_info* infos);
+/* Sweep cut of instance index (host outputs; side is uint8[n_index] or NULL). */
+pirmcut_status pirmcut_batch_cut(pirmcut_batch* b, int index, uint8_t* side, double* value,
+                                 double* tau);
+/* x of instance index, double[n_index] in host memory (x_s = 1, x_t = 0). */
+pirmcut_status pirmcut_batch_get_x(pirmcut_batch* b, int index, double* x);
+/* Totals and the autotuner's choice. */
+pirmcut_status pirmcut_batch_info(const pirmcut_batch* b, int64_t* total_rows, int64_t* total_nnz,
+                                  int* threads_per_row, int* tile_rows, int* tiles);
+int64_t pirmcut_batch_kernel_launches(const pirmcut_batch* b);
+void pirmcut_batch_destroy(pirmcut_batch* b);
+
 /* Text of the last error of ctx (or of the last failed create when ctx is NULL). */
 const char* pirmcut_last_error(const pirmcut_ctx* ctx);
 

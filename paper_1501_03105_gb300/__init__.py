@@ -9,6 +9,14 @@ from .binding import (  # noqa: F401
     StepInfo,
     PirmcutError,
     Solver,
+    Batch,
+    pirmcut_batch_create,
+    pirmcut_batch_solve,
+    pirmcut_batch_cut,
+    pirmcut_batch_get_x,
+    pirmcut_batch_info,
+    pirmcut_batch_kernel_launches,
+    pirmcut_batch_destroy,
     pirmcut_default_options,
     pirmcut_create,
     pirmcut_initial,

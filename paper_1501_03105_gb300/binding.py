@@ -92,6 +92,24 @@ def lib() -> ctypes.CDLL:
     L.pirmcut_time_spmv.restype = ctypes.c_int
     L.pirmcut_sweep_cut_static.argtypes = [i64, _P, _P, _P, i32, i32, _P, _P, _P, _P]
     L.pirmcut_sweep_cut_static.restype = ctypes.c_int
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    L.pirmcut_batch_create.argtypes = [ctypes.c_int, _P, PP, PP, PP, _P, _P, ctypes.POINTER(Options),
+                                       _P, ctypes.POINTER(_P)]
+    L.pirmcut_batch_create.restype = ctypes.c_int
+    L.pirmcut_batch_solve.argtypes = [_P, ctypes.c_int, _P, _P]
+    L.pirmcut_batch_solve.restype = ctypes.c_int
+    L.pirmcut_batch_cut.argtypes = [_P, ctypes.c_int, _P, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+    L.pirmcut_batch_cut.restype = ctypes.c_int
+    L.pirmcut_batch_get_x.argtypes = [_P, ctypes.c_int, _P]
+    L.pirmcut_batch_get_x.restype = ctypes.c_int
+    L.pirmcut_batch_info.argtypes = [_P, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int)]
+    L.pirmcut_batch_info.restype = ctypes.c_int
+    L.pirmcut_batch_kernel_launches.argtypes = [_P]
+    L.pirmcut_batch_kernel_launches.restype = i64
+    L.pirmcut_batch_destroy.argtypes = [_P]
+    L.pirmcut_batch_destroy.restype = None
     L.pirmcut_kernel_launches.argtypes = [_P]
     L.pirmcut_kernel_launches.restype = i64
     L.pirmcut_last_error.argtypes = [_P]
@@ -261,6 +279,117 @@ def pirmcut_last_error(h=None) -> str:
 
 def pirmcut_destroy(h):
     lib().pirmcut_destroy(h)
+
+
+def pirmcut_batch_create(graphs, opt: Options | None = None, stream=None):
+    """Create a batch from a list of graphs (host numpy arrays)."""
+    k = len(graphs)
+    keep = []
+    ns = np.array([g.n for g in graphs], dtype=np.int64)
+    ss = np.array([g.s for g in graphs], dtype=np.int32)
+    ts = np.array([g.t for g in graphs], dtype=np.int32)
+    arrs = []
+    for dt, attr in ((np.int64, "row_ptr"), (np.int32, "col"), (np.float64, "c")):
+        ptrs = (ctypes.c_void_p * k)()
+        for i, g in enumerate(graphs):
+            a = np.ascontiguousarray(getattr(g, attr), dtype=dt)
+            keep.append(a)
+            ptrs[i] = a.ctypes.data
+        arrs.append(ptrs)
+    h = _P()
+    st = lib().pirmcut_batch_create(k, ns.ctypes.data, arrs[0], arrs[1], arrs[2], ss.ctypes.data,
+                                    ts.ctypes.data, ctypes.byref(opt) if opt is not None else None,
+                                    _stream_ptr(stream), ctypes.byref(h))
+    _check(None, st)
+    return h.value
+
+
+def pirmcut_batch_solve(h, count: int, T: int, eps):
+    """Returns infos as a list (per instance) of lists of T+1 StepInfo."""
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    infos = (StepInfo * (count * (T + 1)))()
+    st = lib().pirmcut_batch_solve(h, int(T), eps.ctypes.data, ctypes.addressof(infos))
+    if st not in (OK, ENOCONV):
+        msg = lib().pirmcut_last_error(None)
+        raise PirmcutError(st, msg.decode() if msg else "")
+    return [list(infos[i * (T + 1):(i + 1) * (T + 1)]) for i in range(count)]
+
+
+def pirmcut_batch_cut(h, index: int, n: int):
+    side = np.zeros(int(n), dtype=np.uint8)
+    val, tau = ctypes.c_double(), ctypes.c_double()
+    st = lib().pirmcut_batch_cut(h, int(index), side.ctypes.data, ctypes.byref(val), ctypes.byref(tau))
+    if st != OK:
+        msg = lib().pirmcut_last_error(None)
+        raise PirmcutError(st, msg.decode() if msg else "")
+    return side, val.value, tau.value
+
+
+def pirmcut_batch_get_x(h, index: int, n: int):
+    x = np.empty(int(n), dtype=np.float64)
+    st = lib().pirmcut_batch_get_x(h, int(index), x.ctypes.data)
+    if st != OK:
+        msg = lib().pirmcut_last_error(None)
+        raise PirmcutError(st, msg.decode() if msg else "")
+    return x
+
+
+def pirmcut_batch_info(h):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    g, t, nt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    lib().pirmcut_batch_info(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(g), ctypes.byref(t),
+                             ctypes.byref(nt))
+    return dict(rows=a.value, nnz=b.value, threads_per_row=g.value, tile_rows=t.value, tiles=nt.value)
+
+
+def pirmcut_batch_kernel_launches(h) -> int:
+    return int(lib().pirmcut_batch_kernel_launches(h))
+
+
+def pirmcut_batch_destroy(h):
+    lib().pirmcut_batch_destroy(h)
+
+
+class Batch:
+    """Owner of one batch context."""
+
+    def __init__(self, graphs, opt: Options | None = None, stream=None, **kw):
+        if opt is None:
+            opt = pirmcut_default_options(**kw)
+        self.ns = [int(g.n) for g in graphs]
+        self.h = pirmcut_batch_create(graphs, opt, stream)
+
+    def solve(self, T, eps):
+        return pirmcut_batch_solve(self.h, len(self.ns), T, eps)
+
+    def cut(self, i):
+        return pirmcut_batch_cut(self.h, i, self.ns[i])
+
+    def get_x(self, i):
+        return pirmcut_batch_get_x(self.h, i, self.ns[i])
+
+    def info(self):
+        return pirmcut_batch_info(self.h)
+
+    def kernel_launches(self):
+        return pirmcut_batch_kernel_launches(self.h)
+
+    def close(self):
+        if self.h:
+            pirmcut_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Solver:

@@ -154,6 +154,7 @@ cudaError_t run_step_stream_mixed(Ctx& c, bool initial, int* flag_host, int64_t*
 cudaError_t launch_spmv32_once(Ctx& c);
 // sweep.cu
 cudaError_t sweep_alloc(Ctx& c);
+cudaError_t enqueue_sweep(Ctx& c, cudaStream_t st, bool record, int* nodes);
 cudaError_t build_cut_graph(Ctx& c, cudaGraphExec_t* out, int* nodes);
 cudaError_t launch_side_full(Ctx& c, uint8_t* side_full);
 void sweep_free(Ctx& c);

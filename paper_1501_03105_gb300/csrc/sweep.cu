@@ -524,26 +524,26 @@ void sweep_free(Ctx& c) {
   b = SweepBuf();
 }
 
-// Graph of the whole sweep; writes result[0..3] = {prefix value, exact value,
-// tau, k}, the reduced side vector, and (when record) the cut of the last step record.
-cudaError_t build_cut_graph(Ctx& c, cudaGraphExec_t* out, int* nodes) {
+// Enqueue the whole sweep on st; writes result[0..3] = {prefix value, exact
+// value, tau, k}, the reduced side vector, and (when record) the cut of the
+// last step record.  Tile counts follow c.nt; the scratch may be larger.
+cudaError_t enqueue_sweep(Ctx& c, cudaStream_t st, bool record, int* nodes) {
   SweepBuf& b = c.sw;
-  cudaStream_t st = c.cap_stream;
   const int64_t nt = c.nt;
+  const int nblocks_sort = int((nt + RS_TILE - 1) / RS_TILE);
+  const int ntiles = int((nt + SC_TILE - 1) / SC_TILE);
   int n_nodes = 0;
   unsigned int* counters = reinterpret_cast<unsigned int*>(b.result + 4);
-  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return e;
   k_sweep_init<<<grid_for(nt), kThreads, 0, st>>>(nt, c.x, b.keys[0], b.vals[0]);
   ++n_nodes;
   int cur = 0;
   for (int pass = 0; pass < 8; ++pass) {
     const int shift = 8 * pass;
-    k_radix_hist<<<b.nblocks_sort, RS_THREADS, 0, st>>>(b.keys[cur], nt, shift, b.hist, b.nblocks_sort);
-    k_radix_scan<<<256, 1024, 0, st>>>(b.hist, b.nblocks_sort, b.digit_tot);
-    k_radix_scatter<<<b.nblocks_sort, RS_THREADS, 0, st>>>(b.keys[cur], b.vals[cur], b.keys[cur ^ 1],
-                                                           b.vals[cur ^ 1], nt, shift, b.hist,
-                                                           b.digit_tot, b.nblocks_sort);
+    k_radix_hist<<<nblocks_sort, RS_THREADS, 0, st>>>(b.keys[cur], nt, shift, b.hist, nblocks_sort);
+    k_radix_scan<<<256, 1024, 0, st>>>(b.hist, nblocks_sort, b.digit_tot);
+    k_radix_scatter<<<nblocks_sort, RS_THREADS, 0, st>>>(b.keys[cur], b.vals[cur], b.keys[cur ^ 1],
+                                                         b.vals[cur ^ 1], nt, shift, b.hist,
+                                                         b.digit_tot, nblocks_sort);
     n_nodes += 3;
     cur ^= 1;
   }
@@ -558,10 +558,10 @@ cudaError_t build_cut_graph(Ctx& c, cudaGraphExec_t* out, int* nodes) {
                                                                           c.ct, b.rank, b.delta)));
   }
   ++n_nodes;
-  k_tile_sum<<<b.ntiles, kThreads, 0, st>>>(nt, order, b.delta, b.blk);
-  k_tile_scan<<<1, 1024, 0, st>>>(b.ntiles, b.blk);
-  k_tile_argmin<<<b.ntiles, kThreads, 0, st>>>(nt, order, b.delta, c.x, b.blk, c.hg.sum_cs,
-                                               b.blk + b.ntiles, b.blk_k, counters + 0, b.result);
+  k_tile_sum<<<ntiles, kThreads, 0, st>>>(nt, order, b.delta, b.blk);
+  k_tile_scan<<<1, 1024, 0, st>>>(ntiles, b.blk);
+  k_tile_argmin<<<ntiles, kThreads, 0, st>>>(nt, order, b.delta, c.x, b.blk, c.hg.sum_cs,
+                                             b.blk + ntiles, b.blk_k, counters + 0, b.result);
   k_side<<<grid_for(nt), kThreads, 0, st>>>(nt, order, b.result, b.side_red);
   n_nodes += 4;
   CutArgs a;
@@ -569,23 +569,32 @@ cudaError_t build_cut_graph(Ctx& c, cudaGraphExec_t* out, int* nodes) {
   a.ct = c.ct;
   a.side = b.side_red;
   a.c_st = c.hg.c_st;
-  a.partials = b.blk + b.ntiles;
+  a.partials = b.blk + ntiles;
   a.counter = counters + 1;
   a.result = b.result;
   a.C = c.C;
   a.recs = c.recs;
-  a.record = 1;
+  a.record = record ? 1 : 0;
   if (c.format == PIRMCUT_FORMAT_DIA) {
     SW_DISPATCH_K(c.K, (k_cut_dia<KK><<<rgrid, kThreads, 0, st>>>(c.dd, c.cdia, a)));
   } else {
     SW_DISPATCH_G(c.group, (k_cut_csr<GG><<<rgrid, kThreads, 0, st>>>(c.nt, c.rp, c.col, c.cval, a)));
   }
   ++n_nodes;
+  if (nodes) *nodes = n_nodes;
+  return cudaGetLastError();
+}
+
+// The sweep as a CUDA graph (records the cut of the last step record).
+cudaError_t build_cut_graph(Ctx& c, cudaGraphExec_t* out, int* nodes) {
+  cudaStream_t st = c.cap_stream;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  enqueue_sweep(c, st, true, nodes);
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(st, &g);
   if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
   if (g) cudaGraphDestroy(g);
-  *nodes = n_nodes;
   return e;
 }
 
