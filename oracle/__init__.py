@@ -27,5 +27,7 @@ from .pirmcut import (  # noqa: F401
     cut_value,
     sweep_cut,
     sweep_cut_by_definition,
+    kmeans_1d,
+    two_level_rounding,
 )
 from .exact import brute_force_min_cut, max_flow_min_cut  # noqa: F401

@@ -387,3 +387,75 @@ def sweep_cut(prob: Problem, x: np.ndarray):
     side[order[:k]] = True
     return dict(value=cut_value(prob, side), prefix_value=float(vals[j]), side=side, k=k,
                 tau=_threshold(xs_sorted, k), order=order)
+
+
+def kmeans_1d(values: np.ndarray, c0: float = 0.1, c1: float = 0.9, max_iter: int = 100):
+    """Two-centre K-means (Lloyd) on a 1-D sample, started at c0 and c1 (Section 3.3).
+
+    Each value goes to the nearer centre (the lower one on an exact tie); each
+    centre becomes the mean of its values (kept when it has none); stops when
+    the assignment no longer changes.  Returns (c0, c1).
+    """
+    v = np.asarray(values, dtype=np.float64)
+    assign = None
+    for _ in range(max_iter):
+        new = np.abs(v - c1) < np.abs(v - c0)           # True -> upper centre
+        if assign is not None and np.array_equal(new, assign):
+            break
+        assign = new
+        if np.any(~assign):
+            c0 = float(np.mean(v[~assign]))
+        if np.any(assign):
+            c1 = float(np.mean(v[assign]))
+    return c0, c1
+
+
+def two_level_rounding(prob: Problem, x: np.ndarray, delta: float = 0.05):
+    """Two-level rounding (Section 3.3).
+
+    gamma0 = c0 + delta and gamma1 = c1 - delta from 1-D K-means on x (centres
+    started at 0.1 and 0.9); S0 = {x <= gamma0} (holds t), S1 = {x >= gamma1}
+    (holds s), Sc = the rest.  The coarse graph G_c has the vertices of Sc
+    plus s_c (S1 contracted) and t_c (S0 contracted), with the four kinds of
+    edges of the paper: Sc-Sc edges kept, {s_c, u} of weight sum_{v in S1} c(u,v),
+    {t_c, u} of weight sum_{v in S0} c(u,v), {s_c, t_c} of weight
+    sum_{u in S1, v in S0} c(u,v).  An s_c-t_c min cut of G_c (max-flow) induces
+    the cut S1 + (its source side within Sc) of G.
+    Returns dict(value, side, gamma0, gamma1, coarse_vertices).
+    """
+    from .exact import max_flow_min_cut
+    c0, c1 = kmeans_1d(x)
+    g0, g1 = c0 + delta, c1 - delta
+    lab = np.full(prob.n, 2, dtype=np.int64)
+    lab[x <= g0] = 0
+    lab[x >= g1] = 1
+    lab[prob.s] = 1
+    lab[prob.t] = 0
+    sc = np.nonzero(lab == 2)[0]
+    cid = np.full(prob.n, -1, dtype=np.int64)
+    cid[sc] = np.arange(sc.shape[0])
+    nc = sc.shape[0] + 2
+    sC, tC = sc.shape[0], sc.shape[0] + 1
+    # map every edge to its coarse endpoints; drop edges inside S0 or S1
+    def coarse(vtx):
+        return np.where(lab[vtx] == 2, cid[vtx], np.where(lab[vtx] == 1, sC, tC))
+    cu, cv = coarse(prob.eu), coarse(prob.ev)
+    keep = cu != cv
+    u, v, c = cu[keep], cv[keep], prob.cap[keep]
+    lo, hi = np.minimum(u, v), np.maximum(u, v)
+    key = lo * nc + hi
+    uk, inv = np.unique(key, return_inverse=True)
+    w = np.bincount(inv, weights=c, minlength=uk.shape[0])
+    ru, rv = uk // nc, uk % nc
+    rows = np.concatenate([ru, rv])
+    cols = np.concatenate([rv, ru])
+    vals = np.concatenate([w, w])
+    order = np.lexsort((cols, rows))
+    rp = np.zeros(nc + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=nc), out=rp[1:])
+    coarse_prob = Problem(nc, rp, cols[order], vals[order], sC, tC)
+    _, cside = max_flow_min_cut(coarse_prob)
+    side = lab == 1
+    side[sc] = cside[:sc.shape[0]]
+    return dict(value=cut_value(prob, side), side=side, gamma0=g0, gamma1=g1,
+                coarse_vertices=nc)

@@ -407,3 +407,68 @@ def test_input_validation():
     c2[0] = 5.0                                                          # asymmetric
     with pytest.raises(ValueError):
         O.Problem(3, rp, col, c2, 0, 2)
+
+
+# ---------------------------------------------------------------------------
+# two-level rounding (Section 3.3)
+# ---------------------------------------------------------------------------
+
+def test_kmeans_1d_closed_forms():
+    """Symmetric clusters around 0.1 and 0.9 stay put; an outlier moves only
+    its own centre: [0, 0, 0.3, 1] from (0.1, 0.9) -> c0 = mean(0, 0, 0.3) = 0.1,
+    c1 = 1; a tie at the midpoint goes to the lower centre."""
+    c0, c1 = O.kmeans_1d(np.array([0.0, 0.1, 0.2, 0.8, 0.9, 1.0]))
+    assert abs(c0 - 0.1) < 1e-15 and abs(c1 - 0.9) < 1e-15
+    c0, c1 = O.kmeans_1d(np.array([0.0, 0.0, 0.3, 1.0]))
+    assert abs(c0 - 0.1) < 1e-15 and c1 == 1.0
+    c0, c1 = O.kmeans_1d(np.array([0.0, 0.5, 1.0]))
+    assert abs(c0 - 0.25) < 1e-15 and c1 == 1.0
+
+
+def _constrained_min_cut(P, lab):
+    """Brute force over the free vertices (lab == 2) with lab 1 on the source
+    side and lab 0 on the sink side."""
+    free = np.nonzero(lab == 2)[0]
+    best = np.inf
+    for code in range(1 << free.shape[0]):
+        side = lab == 1
+        side[free] = ((code >> np.arange(free.shape[0])) & 1).astype(bool)
+        best = min(best, O.cut_value(P, side))
+    return best
+
+
+def test_two_level_equals_constrained_brute_force():
+    """The coarse min cut is the least cut of G among the cuts that keep S1 on
+    the source side and S0 on the sink side (contraction preserves those cut
+    values; the max-flow is exact)."""
+    for seed in range(6):
+        g = gen.random_graph(12, 0.3, 600 + seed, st_edge=seed % 2 == 0)
+        P = O.Problem.from_graph(g)
+        xs, _ = O.irls(P, 6)
+        x = xs[2]
+        r = O.two_level_rounding(P, x)
+        lab = np.full(P.n, 2)
+        lab[x <= r["gamma0"]] = 0
+        lab[x >= r["gamma1"]] = 1
+        lab[P.s], lab[P.t] = 1, 0
+        assert (lab == 2).sum() <= 14
+        assert abs(r["value"] - _constrained_min_cut(P, lab)) <= 1e-12 * r["value"]
+        assert r["coarse_vertices"] == (lab == 2).sum() + 2
+
+
+def test_two_level_proposition_recovers_min_cut():
+    """Proposition (Section 3.3): when S1 lies on the source side and S0 on the
+    sink side of some min cut, the coarse min cut induces a min cut of G."""
+    hits = 0
+    for seed in range(12):
+        g = gen.random_graph(11, 0.35, 700 + seed)
+        P = O.Problem.from_graph(g)
+        mu, mins = O.brute_force_min_cut(P)
+        xs, _ = O.irls(P, 30)
+        r = O.two_level_rounding(P, xs[-1])
+        lab0 = xs[-1] <= r["gamma0"]
+        lab1 = xs[-1] >= r["gamma1"]
+        if any(np.all(m[lab1]) and not np.any(m[lab0]) for m in mins):
+            hits += 1
+            assert abs(r["value"] - mu) <= 1e-12 * mu
+    assert hits >= 6
