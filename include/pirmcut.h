@@ -222,6 +222,25 @@ pirmcut_status pirmcut_time_spmv(pirmcut_ctx* ctx, int reps, double* avg_ms, dou
                                  double* flops);
 
 /*
+ * Two-level rounding (Section 3.3) of the current x: 1-D K-means on x with
+ * centres started at 0.1 and 0.9 (each value to the nearer centre, the lower
+ * on a tie; centres = means; until the assignment is stable; s and t included
+ * with x_s = 1, x_t = 0) gives gamma0 = c0 + 0.05 and gamma1 = c1 - 0.05.
+ * Vertices with x <= gamma0 are contracted into t, x >= gamma1 into s; the
+ * coarse graph keeps every edge between the remaining vertices and sums the
+ * rest per the paper's four cases; its s-t min cut (exact max-flow, host side)
+ * induces the returned cut of G.
+ *
+ * side   uint8[n] (may be NULL) in mem_kind memory: 1 on the source side.
+ * value  (may be NULL) exact FP64 cut value of the returned side.
+ * gamma  (may be NULL) double[2] = {gamma0, gamma1}.
+ * coarse_vertices (may be NULL) number of vertices of the coarse graph.
+ * Errors: EINVAL (x unset), ENOMEM, ECUDA.
+ */
+pirmcut_status pirmcut_cut_two_level(pirmcut_ctx* ctx, uint8_t* side, double* value, double* gamma,
+                                     int64_t* coarse_vertices, int mem_kind);
+
+/*
  * Sweep cut that allocates no memory.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc -- code that runs
  * while a stream is being captured into a CUDA graph (an allocation there

@@ -23,6 +23,7 @@ from .binding import (  # noqa: F401
     pirmcut_irls_step,
     pirmcut_solve,
     pirmcut_cut,
+    pirmcut_cut_two_level,
     pirmcut_get_x,
     pirmcut_set_x,
     pirmcut_update_weights,

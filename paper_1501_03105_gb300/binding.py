@@ -92,6 +92,8 @@ def lib() -> ctypes.CDLL:
     L.pirmcut_time_spmv.restype = ctypes.c_int
     L.pirmcut_sweep_cut_static.argtypes = [i64, _P, _P, _P, i32, i32, _P, _P, _P, _P]
     L.pirmcut_sweep_cut_static.restype = ctypes.c_int
+    L.pirmcut_cut_two_level.argtypes = [_P, _P, ctypes.POINTER(dbl), _P, ctypes.POINTER(i64), ctypes.c_int]
+    L.pirmcut_cut_two_level.restype = ctypes.c_int
     PP = ctypes.POINTER(ctypes.c_void_p)
     L.pirmcut_batch_create.argtypes = [ctypes.c_int, _P, PP, PP, PP, _P, _P, ctypes.POINTER(Options),
                                        _P, ctypes.POINTER(_P)]
@@ -216,6 +218,18 @@ def pirmcut_cut(h, side=None, n=None):
     tau = ctypes.c_double()
     _check(h, lib().pirmcut_cut(h, ps, ctypes.byref(val), ctypes.byref(tau), kind))
     return side, val.value, tau.value
+
+
+def pirmcut_cut_two_level(h, side=None, n=None):
+    """Two-level rounding.  Returns (side, value, (gamma0, gamma1), coarse_vertices)."""
+    if side is None and n is not None:
+        side = np.zeros(int(n), dtype=np.uint8)
+    ps, kind, keep = _ptr(side, np.uint8)
+    val = ctypes.c_double()
+    gam = np.zeros(2, dtype=np.float64)
+    nc = ctypes.c_int64()
+    _check(h, lib().pirmcut_cut_two_level(h, ps, ctypes.byref(val), gam.ctypes.data, ctypes.byref(nc), kind))
+    return side, val.value, (float(gam[0]), float(gam[1])), nc.value
 
 
 def pirmcut_get_x(h, out):
@@ -418,6 +432,9 @@ class Solver:
         if out is None:
             out = np.empty(self.n, dtype=np.float64)
         return pirmcut_get_x(self.h, out)
+
+    def cut_two_level(self, side=None):
+        return pirmcut_cut_two_level(self.h, side, n=self.n if side is None else None)
 
     def set_x(self, x):
         pirmcut_set_x(self.h, x)

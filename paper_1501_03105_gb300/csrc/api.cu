@@ -11,16 +11,6 @@
 #include "ctx.h"
 #include "pirmcut.h"
 
-struct pirmcut_ctx {
-  pirmcut::Ctx c;
-  // pinned host staging for small transfers
-  pirmcut::StepCounters* h_ctr = nullptr;
-  double* h_eps = nullptr;
-  double* h_result = nullptr;  // 4
-  int* h_stop = nullptr;       // PCG stop flag read back in stream-launch mode
-  std::vector<cudaEvent_t> events;
-  int next_step = 0;           // IRLS index of the next step record
-};
 
 namespace {
 

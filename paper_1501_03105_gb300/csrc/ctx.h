@@ -155,8 +155,21 @@ cudaError_t launch_spmv32_once(Ctx& c);
 // sweep.cu
 cudaError_t sweep_alloc(Ctx& c);
 cudaError_t enqueue_sweep(Ctx& c, cudaStream_t st, bool record, int* nodes);
+cudaError_t enqueue_cut_value(Ctx& c, cudaStream_t st, const uint8_t* side_red);
 cudaError_t build_cut_graph(Ctx& c, cudaGraphExec_t* out, int* nodes);
 cudaError_t launch_side_full(Ctx& c, uint8_t* side_full);
 void sweep_free(Ctx& c);
 
 }  // namespace pirmcut
+
+// The opaque handle of include/pirmcut.h.
+struct pirmcut_ctx {
+  pirmcut::Ctx c;
+  // pinned host staging for small transfers
+  pirmcut::StepCounters* h_ctr = nullptr;
+  double* h_eps = nullptr;
+  double* h_result = nullptr;  // 4
+  int* h_stop = nullptr;       // PCG stop flag read back in stream-launch mode
+  std::vector<cudaEvent_t> events;
+  int next_step = 0;           // IRLS index of the next step record
+};

@@ -585,6 +585,32 @@ cudaError_t enqueue_sweep(Ctx& c, cudaStream_t st, bool record, int* nodes) {
   return cudaGetLastError();
 }
 
+// Exact FP64 cut value of a given reduced side vector (s on the source side,
+// t on the sink side) into result[1]; uses the sweep's scratch.
+cudaError_t enqueue_cut_value(Ctx& c, cudaStream_t st, const uint8_t* side_red) {
+  SweepBuf& b = c.sw;
+  const int ntiles = int((c.nt + SC_TILE - 1) / SC_TILE);
+  unsigned int* counters = reinterpret_cast<unsigned int*>(b.result + 4);
+  CutArgs a;
+  a.cs = c.cs;
+  a.ct = c.ct;
+  a.side = side_red;
+  a.c_st = c.hg.c_st;
+  a.partials = b.blk + ntiles;
+  a.counter = counters + 1;
+  a.result = b.result;
+  a.C = c.C;
+  a.recs = c.recs;
+  a.record = 0;
+  const int rgrid = grid_for(c.format == PIRMCUT_FORMAT_DIA ? c.nt : c.nt * c.group);
+  if (c.format == PIRMCUT_FORMAT_DIA) {
+    SW_DISPATCH_K(c.K, (k_cut_dia<KK><<<rgrid, kThreads, 0, st>>>(c.dd, c.cdia, a)));
+  } else {
+    SW_DISPATCH_G(c.group, (k_cut_csr<GG><<<rgrid, kThreads, 0, st>>>(c.nt, c.rp, c.col, c.cval, a)));
+  }
+  return cudaGetLastError();
+}
+
 // The sweep as a CUDA graph (records the cut of the last step record).
 cudaError_t build_cut_graph(Ctx& c, cudaGraphExec_t* out, int* nodes) {
   cudaStream_t st = c.cap_stream;

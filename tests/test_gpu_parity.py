@@ -399,3 +399,40 @@ def test_mixed_stream_matches_graph(P, fmt):
             out.append((s.get_x(), [(i.pcg_iters, i.refinements) for i in infos]))
     assert np.array_equal(out[0][0], out[1][0])
     assert out[0][1] == out[1][1]
+
+
+# ---------------------------------------------------------------------------
+# two-level rounding (Section 3.3)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("fmt", [0, 2])
+@pytest.mark.parametrize("name,make", GRAPHS)
+def test_two_level_rounding_matches_oracle(P, name, make, fmt):
+    g = make()
+    prob = O.Problem.from_graph(g)
+    xs, _ = O.irls(prob, 6)
+    for l in (0, 3, 6):
+        ref = O.two_level_rounding(prob, xs[l])
+        with solver(P, g, format=fmt) as s:
+            s.set_x(xs[l])
+            side, value, gam, nc = s.cut_two_level()
+        assert abs(gam[0] - ref["gamma0"]) <= 1e-12 and abs(gam[1] - ref["gamma1"]) <= 1e-12
+        assert nc == ref["coarse_vertices"]
+        assert abs(value - ref["value"]) <= CUT_RTOL * ref["value"], (name, l)
+        assert abs(O.cut_value(prob, side.astype(bool)) - value) <= 1e-12 * value
+        assert side[g.s] == 1 and side[g.t] == 0
+
+
+def test_two_level_on_grid64_after_irls(P):
+    """After the full IRLS run the coarse graph is tiny and the two-level cut
+    is the exact min cut (the Edmonds-Karp value of the oracle)."""
+    g = gen.config_graph(1)
+    prob = O.Problem.from_graph(g)
+    mu_star, _ = O.max_flow_min_cut(prob)
+    with P.Solver(g) as s:
+        s.solve(50, O.eps_schedule(50))
+        side, value, gam, nc = s.cut_two_level()
+        _, sweep_value, _ = s.cut()
+    assert nc < 100
+    assert abs(value - mu_star) <= 1e-9 * mu_star
+    assert value <= sweep_value * (1 + 1e-12)
