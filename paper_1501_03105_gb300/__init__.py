@@ -29,6 +29,13 @@ from .binding import (  # noqa: F401
     pirmcut_update_weights,
     pirmcut_problem_size,
     pirmcut_kernel_launches,
+    pirmcut_mlp_enable,
+    pirmcut_mlp_configure,
+    pirmcut_mlp_predict,
+    pirmcut_mlp_weights,
+    pirmcut_mlp_stats,
+    pirmcut_mlp_features,
+    MlpInfo,
     pirmcut_time_spmv,
     pirmcut_last_error,
     pirmcut_destroy,

@@ -21,6 +21,8 @@ MEM_HOST, MEM_DEVICE = 0, 1
 REWEIGHT_NORTH_STAR, REWEIGHT_PAPER = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 FORMAT_AUTO, FORMAT_DIA, FORMAT_CSR = 0, 1, 2
+MLP_PREDICT, MLP_TRAIN = 1, 2
+MLP_FEATURES, MLP_PARAMS = 6, 4673
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "EDISCONNECTED", 3: "ENOMEM", 4: "ECUDA",
           5: "ENOCONV", 6: "ETIMEOUT", 7: "ENUMERIC"}
@@ -40,6 +42,15 @@ class StepInfo(ctypes.Structure):
                 ("rel_residual", ctypes.c_double), ("x_min", ctypes.c_double),
                 ("x_max", ctypes.c_double), ("cut_value", ctypes.c_double),
                 ("ms", ctypes.c_double), ("status", ctypes.c_int), ("refinements", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class MlpInfo(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("used", ctypes.c_int), ("train_steps", ctypes.c_int),
+                ("loss", ctypes.c_float), ("res_plain", ctypes.c_double),
+                ("res_candidate", ctypes.c_double), ("mean_log_ratio", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -112,6 +123,18 @@ def lib() -> ctypes.CDLL:
     L.pirmcut_batch_kernel_launches.restype = i64
     L.pirmcut_batch_destroy.argtypes = [_P]
     L.pirmcut_batch_destroy.restype = None
+    L.pirmcut_mlp_enable.argtypes = [_P, ctypes.c_int, ctypes.c_uint64]
+    L.pirmcut_mlp_enable.restype = ctypes.c_int
+    L.pirmcut_mlp_configure.argtypes = [_P, ctypes.c_int, ctypes.c_float]
+    L.pirmcut_mlp_configure.restype = ctypes.c_int
+    L.pirmcut_mlp_predict.argtypes = [_P, _P, i64, _P, ctypes.c_int]
+    L.pirmcut_mlp_predict.restype = ctypes.c_int
+    L.pirmcut_mlp_weights.argtypes = [_P, _P, ctypes.c_int]
+    L.pirmcut_mlp_weights.restype = ctypes.c_int
+    L.pirmcut_mlp_stats.argtypes = [_P, ctypes.POINTER(MlpInfo)]
+    L.pirmcut_mlp_stats.restype = ctypes.c_int
+    L.pirmcut_mlp_features.argtypes = [_P, _P]
+    L.pirmcut_mlp_features.restype = ctypes.c_int
     L.pirmcut_kernel_launches.argtypes = [_P]
     L.pirmcut_kernel_launches.restype = i64
     L.pirmcut_last_error.argtypes = [_P]
@@ -134,7 +157,7 @@ def _ptr(a, dtype):
         arr = np.ascontiguousarray(np.asarray(a), dtype=dtype)
         return arr.ctypes.data, MEM_HOST, arr
     tdt = {np.float64: torch.float64, np.int64: torch.int64, np.int32: torch.int32,
-           np.uint8: torch.uint8}[np.dtype(dtype).type]
+           np.uint8: torch.uint8, np.float32: torch.float32}[np.dtype(dtype).type]
     if a.dtype != tdt or not a.is_contiguous():
         raise TypeError(f"tensor must be contiguous {tdt}")
     return a.data_ptr(), (MEM_DEVICE if a.is_cuda else MEM_HOST), a
@@ -280,6 +303,57 @@ def pirmcut_sweep_cut_static(n, row_ptr, col, c, s, t, x, side, result, stream=N
     st = lib().pirmcut_sweep_cut_static(int(n), ptrs[0], ptrs[1], ptrs[2], int(s), int(t),
                                         ptrs[3], ptrs[4], ptrs[5], _stream_ptr(stream))
     _check(None, st)
+
+
+def pirmcut_mlp_enable(h, mode: int, seed: int = 1):
+    _check(h, lib().pirmcut_mlp_enable(h, int(mode), int(seed) & (2**64 - 1)))
+
+
+def pirmcut_mlp_configure(h, iters_per_step: int = 8, learning_rate: float = 1e-3):
+    _check(h, lib().pirmcut_mlp_configure(h, int(iters_per_step), float(learning_rate)))
+
+
+def pirmcut_mlp_predict(h, features, delta=None):
+    """Raw model output for feature rows (numpy float32 [count, 6], or CUDA tensors)."""
+    if isinstance(features, np.ndarray):
+        f = np.ascontiguousarray(features, dtype=np.float32).reshape(-1, MLP_FEATURES)
+        if delta is None:
+            delta = np.empty(f.shape[0], dtype=np.float32)
+        pf, kind, keep = _ptr(f, np.float32)
+    else:
+        pf, kind, keep = _ptr(features, np.float32)
+        f = features
+    pd, kind2, keep2 = _ptr(delta, np.float32)
+    if kind != kind2:
+        raise TypeError("features and delta must be in the same kind of memory")
+    _check(h, lib().pirmcut_mlp_predict(h, pf, int(f.shape[0]), pd, kind))
+    return delta
+
+
+def pirmcut_mlp_weights(h, w=None):
+    """With ``w`` None: return the FP32 master weights (numpy float32[4673]).
+    Otherwise load ``w`` into the model (optimizer state reset)."""
+    if w is None:
+        out = np.empty(MLP_PARAMS, dtype=np.float32)
+        _check(h, lib().pirmcut_mlp_weights(h, out.ctypes.data, 0))
+        return out
+    a = np.ascontiguousarray(w, dtype=np.float32)
+    if a.size != MLP_PARAMS:
+        raise ValueError(f"expected {MLP_PARAMS} weights, got {a.size}")
+    _check(h, lib().pirmcut_mlp_weights(h, a.ctypes.data, 1))
+    return None
+
+
+def pirmcut_mlp_stats(h) -> MlpInfo:
+    info = MlpInfo()
+    _check(h, lib().pirmcut_mlp_stats(h, ctypes.byref(info)))
+    return info
+
+
+def pirmcut_mlp_features(h, nt: int):
+    out = np.empty((int(nt), MLP_FEATURES), dtype=np.float32)
+    _check(h, lib().pirmcut_mlp_features(h, out.ctypes.data))
+    return out
 
 
 def pirmcut_kernel_launches(h) -> int:
@@ -450,6 +524,24 @@ class Solver:
 
     def kernel_launches(self):
         return pirmcut_kernel_launches(self.h)
+
+    def mlp_enable(self, mode, seed=1):
+        pirmcut_mlp_enable(self.h, mode, seed)
+
+    def mlp_configure(self, iters_per_step=8, learning_rate=1e-3):
+        pirmcut_mlp_configure(self.h, iters_per_step, learning_rate)
+
+    def mlp_predict(self, features, delta=None):
+        return pirmcut_mlp_predict(self.h, features, delta)
+
+    def mlp_weights(self, w=None):
+        return pirmcut_mlp_weights(self.h, w)
+
+    def mlp_stats(self):
+        return pirmcut_mlp_stats(self.h)
+
+    def mlp_features(self):
+        return pirmcut_mlp_features(self.h, self.n - 2)
 
     def close(self):
         if self.h:

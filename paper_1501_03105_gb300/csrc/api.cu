@@ -49,6 +49,7 @@ void free_device(Ctx& c) {
     if (p) cudaFree(p);
   pirmcut::sweep_free(c);
   pirmcut::mixed_free(c);
+  pirmcut::mlp_free(c);
   if (c.g_init) cudaGraphExecDestroy(c.g_init);
   if (c.g_step) cudaGraphExecDestroy(c.g_step);
   if (c.g_cut) cudaGraphExecDestroy(c.g_cut);
@@ -103,12 +104,16 @@ pirmcut_status upload_problem(pirmcut_ctx* h) {
   Ctx& c = h->c;
   const pirmcut::HostGraph& g = c.hg;
   cudaStream_t st = c.stream;
+  // the conductances start as the capacities (W^(0) = C): a defined g^(l-1)
+  // for the first step even when x is set by the caller
   if (c.format == PIRMCUT_FORMAT_DIA) {
     CK(h, cudaMemcpyAsync(c.cdia, g.cdia.data(), sizeof(double) * g.cdia.size(), cudaMemcpyHostToDevice, st), "upload");
+    CK(h, cudaMemcpyAsync(c.gdia, c.cdia, sizeof(double) * g.cdia.size(), cudaMemcpyDeviceToDevice, st), "upload");
   } else {
     CK(h, cudaMemcpyAsync(c.rp, g.rp.data(), sizeof(int64_t) * g.rp.size(), cudaMemcpyHostToDevice, st), "upload");
     CK(h, cudaMemcpyAsync(c.col, g.col.data(), sizeof(int32_t) * g.col.size(), cudaMemcpyHostToDevice, st), "upload");
     CK(h, cudaMemcpyAsync(c.cval, g.cval.data(), sizeof(double) * g.cval.size(), cudaMemcpyHostToDevice, st), "upload");
+    CK(h, cudaMemcpyAsync(c.gval, c.cval, sizeof(double) * g.cval.size(), cudaMemcpyDeviceToDevice, st), "upload");
   }
   CK(h, cudaMemcpyAsync(c.cs, g.cs.data(), sizeof(double) * g.cs.size(), cudaMemcpyHostToDevice, st), "upload");
   CK(h, cudaMemcpyAsync(c.ct, g.ct.data(), sizeof(double) * g.ct.size(), cudaMemcpyHostToDevice, st), "upload");
@@ -571,6 +576,110 @@ pirmcut_status pirmcut_time_spmv(pirmcut_ctx* h, int reps, double* avg_ms, doubl
   CK(h, cudaMemcpyAsync(reinterpret_cast<char*>(c.S) + off_stop, &one, sizeof(int), cudaMemcpyHostToDevice, c.stream), "time");
   CK(h, cudaStreamSynchronize(c.stream), "time");
   *avg_ms = total / reps;
+  return PIRMCUT_OK;
+}
+
+pirmcut_status pirmcut_mlp_enable(pirmcut_ctx* h, int mode, uint64_t seed) {
+  if (!h) return fail(nullptr, PIRMCUT_EINVAL, "null context");
+  Ctx& c = h->c;
+  if (mode & ~(PIRMCUT_MLP_PREDICT | PIRMCUT_MLP_TRAIN))
+    return fail(h, PIRMCUT_EINVAL, "mode must be 0 or an OR of PIRMCUT_MLP_PREDICT and PIRMCUT_MLP_TRAIN");
+  if (mode && !c.mlp.master) {
+    CK(h, pirmcut::mlp_alloc(c), "model buffers");
+    CK(h, pirmcut::mlp_init(c, seed), "model initialisation");
+  }
+  if (mode != c.mlp_mode) {
+    // the step graphs bake the hooks in: rebuild
+    if (c.g_step) { cudaGraphExecDestroy(c.g_step); c.g_step = nullptr; }
+    c.mlp_mode = mode;
+  }
+  return PIRMCUT_OK;
+}
+
+pirmcut_status pirmcut_mlp_configure(pirmcut_ctx* h, int iters_per_step, float learning_rate) {
+  if (!h) return fail(nullptr, PIRMCUT_EINVAL, "null context");
+  Ctx& c = h->c;
+  if (iters_per_step < 0 || iters_per_step > 1024)
+    return fail(h, PIRMCUT_EINVAL, "iters_per_step must be in [0, 1024]");
+  if (!(learning_rate > 0.0f) || !std::isfinite(learning_rate))
+    return fail(h, PIRMCUT_EINVAL, "learning_rate must be positive and finite");
+  if (iters_per_step != c.mlp.iters_per_step || learning_rate != c.mlp.lr) {
+    if (c.g_step) { cudaGraphExecDestroy(c.g_step); c.g_step = nullptr; }
+  }
+  c.mlp.iters_per_step = iters_per_step;
+  c.mlp.lr = learning_rate;
+  return PIRMCUT_OK;
+}
+
+pirmcut_status pirmcut_mlp_predict(pirmcut_ctx* h, const float* features, int64_t count,
+                                   float* delta, int mem_kind) {
+  if (!h) return fail(nullptr, PIRMCUT_EINVAL, "null context");
+  Ctx& c = h->c;
+  if (!c.mlp.master) return fail(h, PIRMCUT_EINVAL, "no model: call pirmcut_mlp_enable first");
+  if (count < 0) return fail(h, PIRMCUT_EINVAL, "count must be >= 0");
+  if (count == 0) return PIRMCUT_OK;
+  if (!features || !delta) return fail(h, PIRMCUT_EINVAL, "null feature or output buffer");
+  if (mem_kind != PIRMCUT_MEM_HOST && mem_kind != PIRMCUT_MEM_DEVICE)
+    return fail(h, PIRMCUT_EINVAL, "mem_kind must be PIRMCUT_MEM_HOST or PIRMCUT_MEM_DEVICE");
+  const size_t fb = sizeof(float) * pirmcut::kMlpFeatures * size_t(count);
+  const size_t db = sizeof(float) * size_t(count);
+  if (mem_kind == PIRMCUT_MEM_DEVICE) {
+    CK(h, pirmcut::mlp_predict_delta(c, features, count, delta), "inference");
+    CK(h, cudaStreamSynchronize(c.stream), "inference");
+    return PIRMCUT_OK;
+  }
+  float* df = nullptr;
+  float* dd = nullptr;
+  cudaError_t e = cudaMalloc((void**)&df, fb);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dd, db);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(df, features, fb, cudaMemcpyHostToDevice, c.stream);
+  if (e == cudaSuccess) e = pirmcut::mlp_predict_delta(c, df, count, dd);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(delta, dd, db, cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (df) cudaFree(df);
+  if (dd) cudaFree(dd);
+  if (e != cudaSuccess) return cuda_fail(h, e, "inference");
+  return PIRMCUT_OK;
+}
+
+pirmcut_status pirmcut_mlp_weights(pirmcut_ctx* h, float* w, int direction) {
+  if (!h) return fail(nullptr, PIRMCUT_EINVAL, "null context");
+  Ctx& c = h->c;
+  if (!c.mlp.master) return fail(h, PIRMCUT_EINVAL, "no model: call pirmcut_mlp_enable first");
+  if (!w) return fail(h, PIRMCUT_EINVAL, "null weight buffer");
+  if (direction == 0) {
+    CK(h, pirmcut::mlp_get_weights(c, w), "reading the weights");
+  } else if (direction == 1) {
+    CK(h, pirmcut::mlp_set_weights(c, w), "loading the weights");
+  } else {
+    return fail(h, PIRMCUT_EINVAL, "direction must be 0 (read) or 1 (load)");
+  }
+  return PIRMCUT_OK;
+}
+
+pirmcut_status pirmcut_mlp_stats(pirmcut_ctx* h, pirmcut_mlp_info* info) {
+  if (!h) return fail(nullptr, PIRMCUT_EINVAL, "null context");
+  Ctx& c = h->c;
+  if (!info) return fail(h, PIRMCUT_EINVAL, "null info");
+  if (!c.mlp.master) return fail(h, PIRMCUT_EINVAL, "no model: call pirmcut_mlp_enable first");
+  pirmcut::MlpState m;
+  CK(h, pirmcut::mlp_get_state(c, &m), "reading the model state");
+  info->steps = m.steps;
+  info->used = m.used;
+  info->train_steps = m.train_steps;
+  info->loss = m.loss;
+  info->res_plain = std::sqrt(m.res_plain);
+  info->res_candidate = std::sqrt(m.res_cand);
+  info->mean_log_ratio = m.steps ? m.sum_log_ratio / m.steps : 0.0;
+  return PIRMCUT_OK;
+}
+
+pirmcut_status pirmcut_mlp_features(pirmcut_ctx* h, float* f) {
+  if (!h) return fail(nullptr, PIRMCUT_EINVAL, "null context");
+  Ctx& c = h->c;
+  if (!f) return fail(h, PIRMCUT_EINVAL, "null feature buffer");
+  if (!c.mlp.master) return fail(h, PIRMCUT_EINVAL, "no model: call pirmcut_mlp_enable first");
+  CK(h, pirmcut::mlp_get_features(c, f), "reading the features");
   return PIRMCUT_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -62,6 +63,39 @@ struct SweepBuf {
   double* result = nullptr;   // [value_prefix, value_exact, tau, k]
   int nblocks_sort = 0;
   int ntiles = 0;
+};
+
+// Learned warm start (per-node MLP, 6 -> 64 -> 64 -> 1).
+constexpr int kMlpFeatures = 6;
+constexpr int kMlpParams = 64 * kMlpFeatures + 64 + 64 * 64 + 64 + 64 + 1;
+
+struct MlpState {
+  double res_plain;      // ||b - L~ x^(l-1)||^2 at the last step
+  double res_cand;       // ||b - L~ x_cand||^2 at the last step
+  double sum_log_ratio;  // sum over steps of log(||r_cand|| / ||r_plain||)
+  float loss;            // mean squared error of the last minibatch
+  int sel;               // 1 when the last step started from the candidate
+  int steps;             // steps that evaluated a candidate
+  int used;              // steps that started from it
+  int train_steps;       // Adam steps taken
+  unsigned int counter;  // last-block counter of the residual reductions
+};
+
+struct MlpBuf {
+  float* master = nullptr;       // FP32 weights (kMlpParams)
+  __nv_bfloat16* w16 = nullptr;  // BF16 copy read by the inference/gradient kernels
+  float* m = nullptr;            // Adam moments
+  float* v = nullptr;
+  float* grad_part = nullptr;    // per-block gradient sums
+  float* loss_part = nullptr;
+  float* feat = nullptr;         // nt x kMlpFeatures
+  double* xcand = nullptr;       // candidate start
+  double* xprev = nullptr;       // x^(l-1): reweighting point and training baseline
+  double* gprev = nullptr;       // g^(l-1)
+  MlpState* state = nullptr;
+  uint64_t seed = 0;
+  int iters_per_step = 8;        // Adam steps after each IRLS step
+  float lr = 1e-3f;              // Adam learning rate
 };
 
 struct Ctx {
@@ -129,6 +163,8 @@ struct Ctx {
   int nodes_init = 0, nodes_step = 0, nodes_cut = 0;
 
   SweepBuf sw;
+  MlpBuf mlp;
+  int mlp_mode = 0;             // PIRMCUT_MLP_* bits
 
   bool x_set = false;
   int64_t launches = 0;
@@ -152,6 +188,20 @@ void mixed_free(Ctx& c);
 cudaError_t build_step_graph_mixed(Ctx& c, bool initial, cudaGraphExec_t* out, int* nodes);
 cudaError_t run_step_stream_mixed(Ctx& c, bool initial, int* flag_host, int64_t* kernels);
 cudaError_t launch_spmv32_once(Ctx& c);
+// mlp.cu
+bool mlp_active(const Ctx& c, bool initial);          // the step runs the MLP hooks
+const double* reweight_point(const Ctx& c, bool initial);  // x^(l-1) for gs/gt
+cudaError_t mlp_alloc(Ctx& c);
+void mlp_free(Ctx& c);
+cudaError_t mlp_init(Ctx& c, uint64_t seed);
+cudaError_t mlp_get_weights(Ctx& c, float* host);
+cudaError_t mlp_set_weights(Ctx& c, const float* host);
+cudaError_t mlp_get_state(Ctx& c, MlpState* host);
+cudaError_t mlp_get_features(Ctx& c, float* host);
+cudaError_t mlp_predict_delta(Ctx& c, const float* feat, int64_t count, float* delta);
+int enqueue_mlp_pre(Ctx& c, cudaStream_t st);    // before the reweighting
+int enqueue_mlp_post(Ctx& c, cudaStream_t st);   // after it: features, candidate, choice
+int enqueue_mlp_train(Ctx& c, cudaStream_t st);  // after the solve
 // sweep.cu
 cudaError_t sweep_alloc(Ctx& c);
 cudaError_t enqueue_sweep(Ctx& c, cudaStream_t st, bool record, int* nodes);

@@ -639,7 +639,7 @@ int enqueue_massemble(Ctx& c, cudaStream_t st, bool initial) {
   MAssemble a;
   a.cs = c.cs;
   a.ct = c.ct;
-  a.x = c.x;
+  a.x = reweight_point(c, initial);
   a.eps_list = c.eps_list;
   a.C = c.C;
   a.form = c.opt.reweight_form;
@@ -789,7 +789,10 @@ cudaError_t build_step_graph_mixed(Ctx& c, bool initial, cudaGraphExec_t* out, i
   e = cudaStreamGetCaptureInfo(st, &cst, nullptr, &graph, nullptr, nullptr, nullptr);
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&ho, graph, 1, cudaGraphCondAssignDefault);
   if (e == cudaSuccess) {
+    const bool mlp = mlp_active(c, initial);
+    if (mlp) n_nodes += enqueue_mlp_pre(c, st);
     n_nodes += enqueue_reweight(c, st, initial);
+    if (mlp) n_nodes += enqueue_mlp_post(c, st);
     n_nodes += enqueue_massemble(c, st, initial);
     if (initial || !c.opt.warm_start) cudaMemsetAsync(c.x, 0, sizeof(double) * c.nt, st);
     e = add_while(st, ho, &out_node, &out_body);
@@ -820,6 +823,7 @@ cudaError_t build_step_graph_mixed(Ctx& c, bool initial, cudaGraphExec_t* out, i
   if (bs) cudaStreamDestroy(bs);
   if (e == cudaSuccess)
     e = cudaStreamUpdateCaptureDependencies(st, &out_node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e == cudaSuccess && mlp_active(c, initial)) n_nodes += enqueue_mlp_train(c, st);
   if (e == cudaSuccess) n_nodes += enqueue_step_end(c, st, initial, c.O);
   cudaGraph_t captured = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(st, &captured);
@@ -840,7 +844,10 @@ cudaError_t launch_spmv32_once(Ctx& c) {
 cudaError_t run_step_stream_mixed(Ctx& c, bool initial, int* flag_host, int64_t* kernels) {
   cudaStream_t st = c.stream;
   cudaGraphConditionalHandle none{};
-  int64_t k = enqueue_reweight(c, st, initial);
+  const bool mlp = mlp_active(c, initial);
+  int64_t k = mlp ? enqueue_mlp_pre(c, st) : 0;
+  k += enqueue_reweight(c, st, initial);
+  if (mlp) k += enqueue_mlp_post(c, st);
   k += enqueue_massemble(c, st, initial);
   if (initial || !c.opt.warm_start) cudaMemsetAsync(c.x, 0, sizeof(double) * c.nt, st);
   cudaError_t e = cudaGetLastError();
@@ -863,6 +870,7 @@ cudaError_t run_step_stream_mixed(Ctx& c, bool initial, int* flag_host, int64_t*
     k += enqueue_xupdate(c, st);
   }
   if (e == cudaSuccess) {
+    if (mlp) k += enqueue_mlp_train(c, st);
     k += enqueue_step_end(c, st, initial, c.O);
     e = cudaGetLastError();
   }

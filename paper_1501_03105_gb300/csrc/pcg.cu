@@ -78,7 +78,8 @@ k_reweight_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __rest
 struct AssembleArgs {
   const double* cs;
   const double* ct;
-  const double* x;
+  const double* x;   // start vector of the PCG
+  const double* xw;  // reweighting point x^(l-1) (terminal conductances); x unless a learned start replaced it
   const double* eps_list;
   const StepCounters* C;
   int form;
@@ -133,8 +134,9 @@ k_assemble_dia(DiaDesc d, const double* __restrict__ g, AssembleArgs a) {
     const double xi = x[i];
     double gs = a.cs[i], gt = a.ct[i];
     if (!a.initial) {
-      gs = conductance(gs, 1.0 - xi, eps2, a.form);
-      gt = conductance(gt, xi, eps2, a.form);
+      const double wi = a.xw[i];
+      gs = conductance(gs, 1.0 - wi, eps2, a.form);
+      gt = conductance(gt, wi, eps2, a.form);
     }
     double sum = gs + gt, ax = 0.0;
 #pragma unroll
@@ -192,8 +194,9 @@ k_assemble_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __rest
       const double xi = x[i];
       double gs = a.cs[i], gt = a.ct[i];
       if (!a.initial) {
-        gs = conductance(gs, 1.0 - xi, eps2, a.form);
-        gt = conductance(gt, xi, eps2, a.form);
+        const double wi = a.xw[i];
+        gs = conductance(gs, 1.0 - wi, eps2, a.form);
+        gt = conductance(gt, wi, eps2, a.form);
       }
       sum += gs + gt;
       const double di = 1.0 / sum;
@@ -526,17 +529,22 @@ int enqueue_step_end(Ctx& c, cudaStream_t st, bool initial, const OuterState* O)
 
 namespace {
 
-// Kernels of a step before the PCG loop: [c -> g | reweight] -> assemble -> [x = 0].
+// Kernels of a step before the PCG loop:
+//   [keep x^(l-1), g^(l-1)] -> [c -> g | reweight] -> [features, learned start] -> assemble -> [x = 0].
 int enqueue_prologue(Ctx& c, cudaStream_t st, bool initial, cudaGraphConditionalHandle h,
                      int use_cond) {
   const int grid = row_grid(c);
   const bool zero_start = initial || !c.opt.warm_start;
+  const bool mlp = mlp_active(c, initial);
   double* g = c.format == PIRMCUT_FORMAT_DIA ? c.gdia : c.gval;
-  int kernels = enqueue_reweight(c, st, initial);
+  int kernels = mlp ? enqueue_mlp_pre(c, st) : 0;
+  kernels += enqueue_reweight(c, st, initial);
+  if (mlp) kernels += enqueue_mlp_post(c, st);
   AssembleArgs a;
   a.cs = c.cs;
   a.ct = c.ct;
   a.x = c.x;
+  a.xw = reweight_point(c, initial);
   a.eps_list = c.eps_list;
   a.C = c.C;
   a.form = c.opt.reweight_form;
@@ -626,6 +634,7 @@ cudaError_t build_step_graph(Ctx& c, bool initial, cudaGraphExec_t* out, int* no
   }
   if (e == cudaSuccess)
     e = cudaStreamUpdateCaptureDependencies(st, &cond_node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e == cudaSuccess && mlp_active(c, initial)) n_nodes += enqueue_mlp_train(c, st);
   if (e == cudaSuccess) n_nodes += enqueue_step_end(c, st, initial, nullptr);
   cudaGraph_t captured = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(st, &captured);
@@ -654,6 +663,7 @@ cudaError_t run_step_stream(Ctx& c, bool initial, int* stop_flag_host, int64_t* 
     if (guard > c.opt.pcg_max_iter / 8 + 2) break;  // the device caps iterations; belt and braces
   }
   if (e == cudaSuccess) {
+    if (mlp_active(c, initial)) k += enqueue_mlp_train(c, st);
     k += enqueue_step_end(c, st, initial, nullptr);
     e = cudaGetLastError();
   }

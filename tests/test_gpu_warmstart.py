@@ -1,0 +1,308 @@
+"""GPU parity of the learned warm start against ``oracle/warmstart.py``.
+
+Bars:
+* features: FP32 values computed in FP64 and rounded once (f0-f2, f4, f5:
+  within 2e-6 absolute), f3 from FP32 logarithms (within 1e-5 absolute);
+* inference: within the oracle's rigorous bound on an FP32 fused
+  multiply-add evaluation of the network;
+* candidate residuals: relative 1e-9 where the candidate is exact on both
+  sides (a constant delta), 1e-5 where it comes from the network;
+* the solve after a learned start: the same 1e-9 bar on x as every step;
+* training: after one Adam step from zero moments, each parameter whose oracle
+  gradient is clearly signed moved by -lr * sign(gradient).
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle as O
+import oracle.warmstart as W
+
+pytestmark = pytest.mark.gpu
+
+XTOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1501_03105_gb300 as pkg
+    from paper_1501_03105_gb300 import binding, build
+    import os
+    if not os.path.exists(binding.LIB_PATH):
+        build.build()
+    return pkg
+
+
+GRAPHS = [
+    ("grid16", lambda: gen.config_graph(1, scale=16)),
+    ("vol8", lambda: gen.config_graph(3, scale=8)),
+    ("random40", lambda: gen.random_graph(40, 0.1, 12)),
+    ("chunglu", lambda: gen.chung_lu_instance(600, 5)),
+]
+
+
+def reduced(prob, x):
+    return x[prob.nonterminals]
+
+
+def jacobi_weights(alpha):
+    """Weights whose output is alpha * (f1 - f0): one damped Jacobi step,
+    since f1 - f0 = (sum_u g x_u) / d_v - x_v = r_v / d_v."""
+    w = np.zeros(W.NPARAM, dtype=np.float32)
+    W1 = w[W.OFF_W1:W.OFF_B1].reshape(64, 6)
+    W1[0, 0], W1[0, 1] = -1.0, 1.0
+    w[W.OFF_B1] = 1.0                       # f1 - f0 + 1 >= 0: the ReLU passes it
+    w[W.OFF_W2] = 1.0                       # W2[0][0]
+    w[W.OFF_W3] = alpha
+    w[W.OFF_B3] = -alpha
+    return w
+
+
+@pytest.mark.parametrize("fmt", [0, 2])
+@pytest.mark.parametrize("name,make", GRAPHS)
+def test_features_match_oracle(P, name, make, fmt):
+    g = make()
+    prob = O.Problem.from_graph(g)
+    T = 3
+    eps = O.eps_schedule(T)
+    xs, _ = O.irls(prob, T, eps)
+    gprev = O.initial_conductance(prob)
+    with P.Solver(g, pcg_tol=1e-13, format=fmt) as s:
+        s.initial()
+        s.mlp_enable(P.binding.MLP_TRAIN, seed=3)
+        s.mlp_configure(0, 1e-3)
+        for l in range(1, T + 1):
+            s.set_x(xs[l - 1])
+            s.irls_step(eps[l - 1])
+            gl = O.reweight(prob, xs[l - 1], eps[l - 1])
+            ref = W.features(prob, xs[l - 1], gl, gprev, eps[l - 1])
+            got = s.mlp_features()
+            cols = [0, 1, 2, 4, 5]
+            np.testing.assert_allclose(got[:, cols], ref[:, cols], rtol=0, atol=2e-6, err_msg=f"step {l}")
+            np.testing.assert_allclose(got[:, 3], ref[:, 3], rtol=0, atol=1e-5, err_msg=f"step {l}")
+            assert np.max(np.abs(s.get_x() - xs[l])) <= XTOL
+            gprev = gl
+
+
+@pytest.mark.parametrize("count", [1, 257, 5000])
+def test_inference_within_the_fp32_bound(P, count):
+    g = gen.config_graph(1, scale=8)
+    rng = np.random.default_rng(count)
+    w = rng.normal(0, 0.2, W.NPARAM).astype(np.float32)
+    F = rng.normal(0, 1, (count, 6)).astype(np.float32)
+    with P.Solver(g) as s:
+        s.mlp_enable(P.binding.MLP_PREDICT, seed=1)
+        s.mlp_weights(w)
+        got = s.mlp_predict(F)
+        back = s.mlp_weights()
+    assert np.array_equal(back, w)
+    out, bound = W.mlp_forward(w, F)
+    assert np.all(np.abs(got.astype(np.float64) - out) <= bound)
+
+
+def test_inference_device_buffers(P):
+    import torch
+    g = gen.config_graph(1, scale=8)
+    rng = np.random.default_rng(9)
+    w = rng.normal(0, 0.2, W.NPARAM).astype(np.float32)
+    F = rng.normal(0, 1, (300, 6)).astype(np.float32)
+    with P.Solver(g) as s:
+        s.mlp_enable(P.binding.MLP_PREDICT, seed=1)
+        s.mlp_weights(w)
+        dF = torch.from_numpy(F).cuda()
+        dd = torch.empty(300, dtype=torch.float32, device="cuda")
+        s.mlp_predict(dF, dd)
+        got = dd.cpu().numpy()
+    out, bound = W.mlp_forward(w, F)
+    assert np.all(np.abs(got.astype(np.float64) - out) <= bound)
+
+
+@pytest.mark.parametrize("fmt", [0, 2])
+def test_untrained_model_is_bit_identical_to_the_plain_start(P, fmt):
+    """A fresh model has a zero output layer: the candidate equals x^(l-1),
+    is never strictly better, and every step is bit-identical to the plain
+    warm start."""
+    g = gen.config_graph(1)
+    T = 10
+    eps = O.eps_schedule(T)
+    with P.Solver(g, format=fmt) as a, P.Solver(g, format=fmt) as b:
+        ia = a.solve(T, eps)
+        b.mlp_enable(P.binding.MLP_PREDICT, seed=5)
+        ib = b.solve(T, eps)
+        assert np.array_equal(a.get_x(), b.get_x())
+        assert [i.pcg_iters for i in ia] == [i.pcg_iters for i in ib]
+        st = b.mlp_stats()
+        assert st.steps == T and st.used == 0
+
+
+@pytest.mark.parametrize("fmt", [0, 2])
+@pytest.mark.parametrize("delta", [-1 / 32, 1 / 64])
+def test_constant_candidate_residuals_and_choice(P, fmt, delta):
+    """delta = const (only b3 set): both candidate residuals are exact on both
+    sides; the choice and the solution follow the oracle."""
+    g = gen.config_graph(1, scale=24)
+    prob = O.Problem.from_graph(g)
+    T = 6
+    eps = O.eps_schedule(T)
+    xs, _ = O.irls(prob, T, eps)
+    w = np.zeros(W.NPARAM, dtype=np.float32)
+    w[W.OFF_B3] = delta
+    with P.Solver(g, pcg_tol=1e-13, format=fmt) as s:
+        s.initial()
+        s.mlp_enable(P.binding.MLP_PREDICT, seed=1)
+        s.mlp_weights(w)
+        used = 0
+        for l in range(1, T + 1):
+            s.set_x(xs[l - 1])
+            s.irls_step(eps[l - 1])
+            gl = O.reweight(prob, xs[l - 1], eps[l - 1])
+            v0 = reduced(prob, xs[l - 1])
+            rp = W.residual_norm(prob, gl, v0)
+            rc = W.residual_norm(prob, gl, W.candidate_start(v0, np.full(v0.shape, delta)))
+            st = s.mlp_stats()
+            assert st.res_plain == pytest.approx(rp, rel=1e-9)
+            assert st.res_candidate == pytest.approx(rc, rel=1e-9)
+            used += int(rc < rp)
+            assert st.used == used
+            assert np.max(np.abs(s.get_x() - xs[l])) <= XTOL, l
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("fmt", [0, 2])
+def test_jacobi_candidate_is_taken_and_the_solve_stays_exact(P, fmt, precision):
+    """Weights that output half a Jacobi step: the candidate usually has the
+    smaller residual; the GPU's residuals and choices follow the oracle's, and
+    every step still meets the 1e-9 bar on x (FP64 and mixed solvers)."""
+    g = gen.config_graph(1, scale=32)
+    prob = O.Problem.from_graph(g)
+    T = 8
+    eps = O.eps_schedule(T)
+    xs, _ = O.irls(prob, T, eps)
+    gprev = O.initial_conductance(prob)
+    w = jacobi_weights(0.5)
+    with P.Solver(g, pcg_tol=1e-13, format=fmt, precision=precision) as s:
+        s.initial()
+        s.mlp_enable(P.binding.MLP_PREDICT, seed=1)
+        s.mlp_weights(w)
+        used = 0
+        for l in range(1, T + 1):
+            s.set_x(xs[l - 1])
+            info = s.irls_step(eps[l - 1])
+            assert info.status == 0
+            gl = O.reweight(prob, xs[l - 1], eps[l - 1])
+            F = W.features(prob, xs[l - 1], gl, gprev, eps[l - 1])
+            out, bound = W.mlp_forward(w, F)
+            v0 = reduced(prob, xs[l - 1])
+            rp = W.residual_norm(prob, gl, v0)
+            rc = W.residual_norm(prob, gl, W.candidate_start(v0, out))
+            st = s.mlp_stats()
+            assert st.res_plain == pytest.approx(rp, rel=1e-9)
+            assert st.res_candidate == pytest.approx(rc, rel=1e-5)
+            if abs(rc - rp) > 1e-4 * rp:
+                used += int(rc < rp)
+                assert st.used == used, l
+            else:
+                used = st.used
+            assert np.max(np.abs(s.get_x() - xs[l])) <= XTOL, l
+            gprev = gl
+        assert used >= 1
+
+
+@pytest.mark.parametrize("fmt", [0, 2])
+def test_first_adam_step_follows_the_oracle_gradient(P, fmt):
+    """One Adam step from zero moments moves each parameter by -lr * sign(g):
+    the signs of the GPU's minibatch gradient (hand-written backward pass,
+    SplitMix64-drawn nodes) against the oracle's exact gradient."""
+    g = gen.config_graph(1, scale=32)
+    prob = O.Problem.from_graph(g)
+    xs, _ = O.irls(prob, 1, [0.1])
+    rng = np.random.default_rng(21)
+    w0 = rng.normal(0, 0.2, W.NPARAM).astype(np.float32)
+    seed = 77
+    lr = 1e-3
+    with P.Solver(g, pcg_tol=1e-13, format=fmt) as s:
+        s.initial()
+        s.mlp_enable(P.binding.MLP_TRAIN, seed=seed)
+        s.mlp_configure(1, lr)
+        s.mlp_weights(w0)
+        s.set_x(xs[0])
+        s.irls_step(0.1)
+        w1 = s.mlp_weights()
+        st = s.mlp_stats()
+        assert st.train_steps == 1
+    g1 = O.reweight(prob, xs[0], 0.1)
+    F = W.features(prob, xs[0], g1, O.initial_conductance(prob), 0.1)
+    nodes = W.sample_nodes(seed, 0, prob.nt)
+    target = (reduced(prob, xs[1]) - reduced(prob, xs[0]))[nodes].astype(np.float32)
+    grad, loss = W.mlp_gradient(w0, F[nodes], target)
+    assert st.loss == pytest.approx(loss, rel=1e-3)
+    clear = np.abs(grad) > 1e-3 * np.abs(grad).max()
+    assert clear.sum() > 0.3 * W.NPARAM
+    step = (w1.astype(np.float64) - w0.astype(np.float64))[clear]
+    np.testing.assert_allclose(step, -lr * np.sign(grad[clear]), rtol=0, atol=2e-6)
+    assert np.all(np.abs(w1 - w0) <= lr * (1 + 1e-5) + 1e-6)
+
+
+def test_training_is_deterministic_and_graph_equals_stream(P):
+    g = gen.config_graph(1)
+    T = 12
+    eps = O.eps_schedule(T)
+    runs = []
+    for launch in (1, 1, 0):
+        with P.Solver(g, graph_launch=launch) as s:
+            s.mlp_enable(P.binding.MLP_PREDICT | P.binding.MLP_TRAIN, seed=11)
+            infos = s.solve(T, eps)
+            runs.append((s.get_x(), s.mlp_weights(), [i.pcg_iters for i in infos],
+                         s.mlp_stats().as_dict()))
+    for r in runs[1:]:
+        assert np.array_equal(r[0], runs[0][0])
+        assert np.array_equal(r[1], runs[0][1])
+        assert r[2] == runs[0][2]
+        assert r[3] == runs[0][3]
+    assert runs[0][3]["train_steps"] == 8 * T
+
+
+def test_training_lowers_the_loss_on_a_repeated_sequence(P):
+    """Fit on the trajectory of one problem, then run it again: the second
+    pass's minibatch losses are below the first pass's."""
+    g = gen.config_graph(1, scale=48)
+    T = 12
+    eps = O.eps_schedule(T)
+    passes = []
+    with P.Solver(g) as s:
+        s.mlp_enable(P.binding.MLP_TRAIN, seed=2)
+        for _ in range(3):
+            s.initial()
+            losses = []
+            for l in range(T):
+                s.irls_step(eps[l])
+                losses.append(s.mlp_stats().loss)
+            passes.append(np.mean(losses))
+    assert passes[2] < passes[0]
+
+
+def test_mlp_call_errors(P):
+    B = P.binding
+    g = gen.config_graph(1, scale=8)
+    with P.Solver(g) as s:
+        for fn in (lambda: s.mlp_weights(), lambda: s.mlp_stats(), lambda: s.mlp_features(),
+                   lambda: s.mlp_predict(np.zeros((2, 6), np.float32))):
+            with pytest.raises(B.PirmcutError) as ei:
+                fn()
+            assert ei.value.status == B.EINVAL
+        with pytest.raises(B.PirmcutError):
+            s.mlp_enable(4)
+        with pytest.raises(B.PirmcutError):
+            s.mlp_configure(-1, 1e-3)
+        with pytest.raises(B.PirmcutError):
+            s.mlp_configure(1, 0.0)
+        s.mlp_enable(B.MLP_PREDICT)
+        assert s.mlp_predict(np.zeros((0, 6), np.float32)).shape == (0,)
+        with pytest.raises(ValueError):
+            s.mlp_weights(np.zeros(5, np.float32))
+        s.mlp_enable(0)
+        s.solve(3, O.eps_schedule(3))
+        assert s.mlp_stats().steps == 0
