@@ -313,6 +313,132 @@ def run_batch(args):
     return 0
 
 
+def run_sequence(args):
+    """A sequence of related 128^3 volume problems (each one's capacities are
+    the previous one's times exp(N(0, 0.01)) per edge).  The learned warm start
+    trains on the IRLS trajectories of the first half and is then frozen; on
+    the second half four arms solve every problem (x^(0) + T steps + sweep
+    cut): plain FP64 (each PCG starts from x^(l-1)), learned FP64, plain mixed
+    and learned mixed."""
+    import gen
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_1501_03105_gb300 import binding as B
+    from paper_1501_03105_gb300 import build as _build
+    if not os.path.exists(B.LIB_PATH):
+        _build.build()
+    W_side = args.seq_scale
+    base = gen.config_graph(5, W_side if W_side != 128 else None)
+    P = args.problems
+    P_train = P // 2
+    T = 30
+    eps = eps_list(T)
+    stream = torch.cuda.current_stream()
+    side_dev = torch.empty(base.n, dtype=torch.uint8, device="cuda")
+    arms = {
+        "plain_fp64": (B.PREC_FP64, 0),
+        "learned_fp64": (B.PREC_FP64, B.MLP_PREDICT),
+        "plain_mixed": (B.PREC_MIXED, 0),
+        "learned_mixed": (B.PREC_MIXED, B.MLP_PREDICT),
+    }
+    solvers = {}
+    for name, (prec, mode) in arms.items():
+        opt = B.pirmcut_default_options(pcg_tol=PCG_TOL, precision=prec, track_cut=1,
+                                        inner_tol=args.inner_tol)
+        solvers[name] = B.Solver(base, opt, stream=stream)
+    trainer = solvers["learned_fp64"]
+    trainer.mlp_enable(B.MLP_PREDICT | B.MLP_TRAIN, seed=5)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def run(s):
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        infos = s.solve(T, eps)
+        _, value, _ = s.cut(side=side_dev)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return infos, value, ev0.elapsed_time(ev1)
+
+    train_iters = []
+    stats = {k: {"iters": [], "iters0": [], "ms": [], "ttc": [], "cut": [], "alpha": [], "dE": []}
+             for k in arms}
+    log_ratio = {}
+    t_start = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for k, c in enumerate(gen.capacity_sequence(base, P, seed=5, sigma=0.01)):
+            if k < P_train:
+                trainer.update_weights(c)
+                infos, _, _ = run(trainer)
+                train_iters.append(sum(i.pcg_iters for i in infos))
+                continue
+            if k == P_train:
+                trainer.mlp_enable(B.MLP_PREDICT)   # frozen from here on
+                w = trainer.mlp_weights()
+                s = solvers["learned_mixed"]
+                s.mlp_enable(B.MLP_PREDICT, seed=5)
+                s.mlp_weights(w)
+                st0 = {n: (solvers[n].mlp_stats().steps, solvers[n].mlp_stats().used)
+                       for n in ("learned_fp64", "learned_mixed")}
+            for name, s in solvers.items():
+                s.update_weights(c)
+                infos, value, ms = run(s)
+                st = stats[name]
+                st["iters"].append(sum(i.pcg_iters for i in infos))
+                st["iters0"].append(infos[0].pcg_iters)
+                st["ms"].append(ms)
+                st["cut"].append(value)
+                st["track"] = [(i.cut_value, i.ms) for i in infos]
+            ref = stats["plain_fp64"]["cut"][-1]
+            for name in arms:
+                acc, ttc = 0.0, None
+                for cv, ms_l in stats[name].pop("track"):
+                    acc += ms_l
+                    if ttc is None and abs(cv - ref) <= 1e-6 * ref:
+                        ttc = acc
+                stats[name]["ttc"].append(ttc if ttc is not None else float("nan"))
+    wall = time.perf_counter() - t_start
+    for n in ("learned_fp64", "learned_mixed"):
+        st = solvers[n].mlp_stats()
+        log_ratio[n] = {"steps": st.steps - st0[n][0], "moved": st.used - st0[n][1],
+                        "mean_alpha_all_steps": st.mean_alpha, "last_alpha": st.alpha,
+                        "last_energy_change": st.energy_change, "last_res_plain": st.res_plain}
+    tstats = trainer.mlp_stats()
+    for s in solvers.values():
+        s.close()
+    summary = {}
+    for name in arms:
+        st = stats[name]
+        summary[name] = {"pcg_iters_per_problem": float(np.mean(st["iters"])),
+                         "pcg_iters_x0_per_problem": float(np.mean(st["iters0"])),
+                         "ms_per_problem": float(np.mean(st["ms"])),
+                         "time_to_cut_1e-6_ms": float(np.nanmean(st["ttc"])),
+                         "cut_max_rel_diff_vs_plain_fp64": float(max(
+                             abs(a - b) / b for a, b in zip(st["cut"], stats["plain_fp64"]["cut"])))}
+    base_ms = summary["plain_fp64"]["ms_per_problem"]
+    for name in arms:
+        summary[name]["speedup_vs_plain_fp64"] = base_ms / summary[name]["ms_per_problem"]
+        summary[name]["iters_ratio_vs_plain_fp64"] = (summary[name]["pcg_iters_per_problem"] /
+                                                      summary["plain_fp64"]["pcg_iters_per_problem"])
+    line = {
+        "metric": "time-to-cut per problem", "value": summary["learned_fp64"]["ms_per_problem"],
+        "unit": "ms", "n_gpus": 1, "higher_is_better": False, "dtype": "f64 (+ bf16 MLP)",
+        "data": "synthetic",
+        "config": {"workload": f"seq{W_side}: sequence of {P} {W_side}^3 6-connected volume problems, "
+                               f"capacities x exp(N(0,0.01)) per edge per problem, seed 5",
+                   "train_problems": P_train, "eval_problems": P - P_train, "T": T,
+                   "pcg_tol": PCG_TOL, "step": "x0 + 30 IRLS steps + sweep cut per problem"},
+        "arms": summary,
+        "learned_start_use": log_ratio,
+        "training": {"problems": P_train, "adam_steps": tstats.train_steps,
+                     "last_minibatch_loss": tstats.loss,
+                     "pcg_iters_first_5": train_iters[:5], "pcg_iters_last_5": train_iters[-5:]},
+        "wall_s": wall, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -322,7 +448,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=15.0)
-    ap.add_argument("--workload", default="grid2048", choices=list(WORKLOADS) + ["chunglu64"])
+    ap.add_argument("--workload", default="grid2048", choices=list(WORKLOADS) + ["chunglu64", "seq128"])
+    ap.add_argument("--problems", type=int, default=200, help="seq128: problems in the sequence")
+    ap.add_argument("--seq-scale", type=int, default=128, help="seq128: side of the volume")
     ap.add_argument("--inner-tol", type=float, default=1e-5,
                     help="mixed path: relative reduction of each FP32 inner solve")
     ap.add_argument("--only", default=None, choices=["fp64", "mixed"],
@@ -335,6 +463,8 @@ def main():
         return run_reference(args)
     if args.workload == "chunglu64":
         return run_batch(args)
+    if args.workload == "seq128":
+        return run_sequence(args)
 
     import torch
     ws, rank, local = dist_env()

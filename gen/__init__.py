@@ -15,6 +15,7 @@ from .graphs import (  # noqa: F401
     chung_lu_batch,
     config_graph,
     perturb_capacities,
+    capacity_sequence,
     permute_graph,
     CONFIGS,
 )

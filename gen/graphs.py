@@ -283,6 +283,24 @@ def perturb_capacities(g: Graph, seed: int, sigma: float = 0.01) -> Graph:
     return Graph(g.n, g.row_ptr.copy(), g.col.copy(), g.c * f[inv], g.s, g.t, g.name + "+p")
 
 
+def capacity_sequence(g: Graph, count: int, seed: int, sigma: float = 0.01):
+    """Capacity arrays of a sequence of ``count`` related problems on the
+    structure of ``g``: problem 0 has g's capacities and problem k+1
+    multiplies every undirected capacity of problem k by exp(N(0, sigma))
+    (both stored directions by the same factor).  Yields float64 arrays in
+    g's CSR order; the edge pairing is computed once."""
+    rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.row_ptr))
+    lo = np.minimum(rows, g.col.astype(np.int64))
+    hi = np.maximum(rows, g.col.astype(np.int64))
+    uk, inv = np.unique(lo * g.n + hi, return_inverse=True)
+    rng = np.random.default_rng(seed)
+    c = g.c.astype(np.float64).copy()
+    for k in range(count):
+        if k > 0:
+            c = c * np.exp(rng.normal(0.0, sigma, uk.shape[0]))[inv]
+        yield c
+
+
 def permute_graph(g: Graph, perm: np.ndarray) -> Graph:
     """Relabel vertex v as perm[v]; returns a new sorted CSR."""
     rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.row_ptr))

@@ -244,9 +244,16 @@ pirmcut_status pirmcut_cut_two_level(pirmcut_ctx* ctx, uint8_t* side, double* va
  * Learned warm start.  The paper starts the PCG of step l from x^(l-1)
  * (Section 3.1) and aims at sequences of related problems (Section 6).  With
  * PIRMCUT_MLP_PREDICT on, each IRLS step after x^(0) (with warm_start = 1)
- * also forms a candidate start x^(l-1) + delta, clipped to [0, 1], where delta
- * comes from a per-node MLP (6 features -> 64 -> 64 -> 1, ReLU; BF16 weights,
- * FP32 arithmetic).  The features of node v, all of step l:
+ * starts instead from x^(l-1) + alpha * d, where d is a per-node direction
+ * predicted by an MLP (6 features -> 64 -> 64 -> 1, ReLU; BF16 weights, FP32
+ * arithmetic) and alpha comes from an exact line search (FP64) on the
+ * quadratic energy E(v) = v^T L~ v - 2 b^T v = ||v - v*||^2_{L~} - const:
+ *   alpha = d^T r / d^T L~ d,  r = b - L~ x^(l-1)   (alpha = 0 if d^T L~ d <= 0).
+ * E is the error norm that CG minimises, so the learned start is never
+ * worse than x^(l-1) in that norm: the plain warm start is the fallback and
+ * the judge.  The conductances always come from x^(l-1), so the solved system
+ * is unchanged and every result keeps the solver's tolerance.
+ * The features of node v, all of step l:
  *   f0 x^(l-1)_v;
  *   f1, f2 mean and standard deviation of the neighbours' x^(l-1), weighted by
  *          the new conductances, s and t included (x_s = 1, x_t = 0);
@@ -255,38 +262,36 @@ pirmcut_status pirmcut_cut_two_level(pirmcut_ctx* ctx, uint8_t* side, double* va
  *      of the last step this context ran (the capacities after creation);
  *   f4 log of the weighted degree of v in L~ (its diagonal entry), / 8;
  *   f5 log(eps_l) / 8.
- * The candidate replaces x^(l-1) as the start only when its FP64 residual
- * ||b - L~ v||_2 is strictly smaller; the conductances always come from
- * x^(l-1), so the solved system is unchanged and every result keeps the
- * solver's tolerance.  With PIRMCUT_MLP_TRAIN on, each such step ends with 8
- * Adam steps (by default; learning rate 1e-3) on minibatches of 2048 nodes
- * drawn by a counter-based hash (SplitMix64), fitting delta to
- * x^(l) - x^(l-1) (mean squared error).
- * Everything runs on the GPU inside the step; results are reproducible.
+ * With PIRMCUT_MLP_TRAIN on, each such step ends with 8 Adam steps (by
+ * default; learning rate 1e-3) on minibatches of 2048 nodes drawn by a
+ * counter-based hash (SplitMix64), fitting d to x^(l) - x^(l-1) (mean squared
+ * error).  Everything runs on the GPU inside the step; results are
+ * reproducible.
  *
  * Weight layout (PIRMCUT_MLP_PARAMS floats, row-major, out x in):
  *   W1[64][6] b1[64] W2[64][64] b2[64] w3[64] b3.
  *
  * pirmcut_mlp_enable: mode = 0 or an OR of the two flags.  The first call
  *   with mode != 0 allocates the model and its buffers (two doubles and six
- *   floats per non-terminal plus one copy of the conductances) and initialises it from
- *   seed: Glorot-uniform W1, W2, zero biases and output layer, so an untrained
- *   model proposes no change.  Later calls change the mode only (weights and
- *   statistics are kept, e.g. across pirmcut_update_weights).  The step graphs
- *   are rebuilt on the next solve.  Errors: EINVAL (mode), ENOMEM, ECUDA.
+ *   floats per non-terminal plus one copy of the conductances) and
+ *   initialises it from seed: Glorot-uniform W1, W2, zero biases and output
+ *   layer, so an untrained model proposes d = 0 (alpha = 0).  Later calls
+ *   change the mode only (weights and statistics are kept, e.g. across
+ *   pirmcut_update_weights).  The step graphs are rebuilt on the next solve.
+ *   Errors: EINVAL (mode), ENOMEM, ECUDA.
  * pirmcut_mlp_configure: iters_per_step Adam steps (0..1024, default 8) with
  *   learning rate learning_rate (> 0, default 1e-3) after each step when
  *   training.  Errors: EINVAL.
- * pirmcut_mlp_predict: the model's raw output delta (no clipping) for count
- *   feature rows (float[count * 6], row-major) into float[count]; both arrays
- *   in mem_kind memory.  Errors: EINVAL (no model, sizes), ENOMEM, ECUDA.
+ * pirmcut_mlp_predict: the model's output d for count feature rows
+ *   (float[count * 6], row-major) into float[count]; both arrays in mem_kind
+ *   memory.  Errors: EINVAL (no model, sizes), ENOMEM, ECUDA.
  * pirmcut_mlp_weights: direction 0 copies the FP32 master weights to w
  *   (host, PIRMCUT_MLP_PARAMS floats); direction 1 loads them from w and
  *   resets the optimizer state.  Errors: EINVAL (no model, NULL w), ECUDA.
- * pirmcut_mlp_stats: steps that evaluated a candidate, steps that used it,
- *   Adam steps taken, the last minibatch loss, and for the last step the two
- *   residual norms ||r(x^(l-1))||, ||r(candidate)||; mean_log_ratio is the
- *   mean over steps of log(||r(candidate)|| / ||r(x^(l-1))||).
+ * pirmcut_mlp_stats: steps that ran the line search, steps that moved
+ *   (alpha != 0), Adam steps taken, the last minibatch loss; for the last
+ *   step alpha, the energy change E(start) - E(x^(l-1)) (<= 0) and
+ *   ||b - L~ x^(l-1)||_2; the mean of alpha over steps.
  * pirmcut_mlp_features: the features of the last step, float[n~ * 6] in host
  *   memory, in reduced numbering (the caller's order with s and t removed).
  */
@@ -299,9 +304,10 @@ typedef struct {
   int used;
   int train_steps;
   float loss;
+  double alpha;
+  double energy_change;
   double res_plain;
-  double res_candidate;
-  double mean_log_ratio;
+  double mean_alpha;
 } pirmcut_mlp_info;
 pirmcut_status pirmcut_mlp_enable(pirmcut_ctx* ctx, int mode, uint64_t seed);
 pirmcut_status pirmcut_mlp_configure(pirmcut_ctx* ctx, int iters_per_step, float learning_rate);

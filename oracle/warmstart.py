@@ -5,9 +5,10 @@ path.  It shares no code with the CUDA library.
 
 The paper starts the PCG of IRLS step l from the previous iterate v^(l-1)
 (Section 3.1) and aims at sequences and batches of related problems
-(Section 6).  The library can also propose a learned start: a per-node MLP
-predicts x^(l) - x^(l-1) from six features of step l, and the proposal is
-used only when its residual is smaller than that of x^(l-1).  This module
+(Section 6).  The library can also move the start along a learned direction: a per-node
+MLP predicts x^(l) - x^(l-1) from six features of step l, and an exact line
+search on the energy that CG minimises sets the step length, so the start is
+never worse than x^(l-1) in that norm.  This module
 writes every piece of that out plainly:
 
 * ``features``        the six per-node features, from their definitions;
@@ -19,11 +20,14 @@ writes every piece of that out plainly:
 * ``splitmix64``      the SplitMix64 generator (Steele, Lea & Flood, 2014),
                       ``sample_nodes`` the minibatch it draws;
 * ``adam_step``       one Adam update (Kingma & Ba, 2015) in FP32;
-* ``residual_norm``   ||b - L~ v||_2 of a start v, conductances from x^(l-1).
+* ``residual_norm``   ||b - L~ v||_2 of a start v, conductances from x^(l-1);
+* ``energy``, ``line_search``  the quadratic energy E(v) = v^T L~ v - 2 b^T v
+                      and the exact minimiser of E along the learned direction.
 
 Parity status: pinned by hand-computed features on a small graph, by finite
 differences of the gradient, by SplitMix64's published output, by BF16
-rounding cases and by the Adam first-step identity (see
+rounding cases, by the Adam first-step identity and by the energy identity
+E(v) - E(v*) = ||v - v*||^2 (see
 ``tests/test_oracle_warmstart.py``).
 """
 from __future__ import annotations
@@ -216,6 +220,22 @@ def residual_norm(prob: Problem, g: np.ndarray, v: np.ndarray) -> float:
     return float(np.linalg.norm(b - Lt @ v))
 
 
-def candidate_start(x_prev_reduced: np.ndarray, delta: np.ndarray) -> np.ndarray:
-    """clip(x^(l-1) + delta, 0, 1), the proposed start."""
-    return np.clip(x_prev_reduced + np.asarray(delta, dtype=np.float64), 0.0, 1.0)
+def energy(prob: Problem, g: np.ndarray, v: np.ndarray) -> float:
+    """E(v) = v^T L~ v - 2 b^T v, which equals ||v - v*||^2_{L~} - v*^T b for
+    the solution v* of L~ v* = b."""
+    Lt, b = reduced_system(prob, laplacian(prob, g))
+    return float(v @ (Lt @ v) - 2.0 * (b @ v))
+
+
+def line_search(prob: Problem, g: np.ndarray, v0: np.ndarray, d: np.ndarray):
+    """Exact minimiser of E(v0 + alpha d) over alpha: alpha = d^T r / d^T L~ d
+    with r = b - L~ v0 (alpha = 0 when d^T L~ d <= 0).  Returns (alpha, the
+    energy change E(v0 + alpha d) - E(v0) = -(d^T r) alpha)."""
+    Lt, b = reduced_system(prob, laplacian(prob, g))
+    d = np.asarray(d, dtype=np.float64)
+    r = b - Lt @ v0
+    dad = float(d @ (Lt @ d))
+    if not dad > 0.0:
+        return 0.0, 0.0
+    alpha = float(d @ r) / dad
+    return alpha, -float(d @ r) * alpha

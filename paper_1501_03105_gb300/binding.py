@@ -49,8 +49,9 @@ class StepInfo(ctypes.Structure):
 
 class MlpInfo(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("used", ctypes.c_int), ("train_steps", ctypes.c_int),
-                ("loss", ctypes.c_float), ("res_plain", ctypes.c_double),
-                ("res_candidate", ctypes.c_double), ("mean_log_ratio", ctypes.c_double)]
+                ("loss", ctypes.c_float), ("alpha", ctypes.c_double),
+                ("energy_change", ctypes.c_double), ("res_plain", ctypes.c_double),
+                ("mean_alpha", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

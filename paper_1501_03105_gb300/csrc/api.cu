@@ -668,9 +668,10 @@ pirmcut_status pirmcut_mlp_stats(pirmcut_ctx* h, pirmcut_mlp_info* info) {
   info->used = m.used;
   info->train_steps = m.train_steps;
   info->loss = m.loss;
+  info->alpha = m.alpha;
+  info->energy_change = m.energy_change;
   info->res_plain = std::sqrt(m.res_plain);
-  info->res_candidate = std::sqrt(m.res_cand);
-  info->mean_log_ratio = m.steps ? m.sum_log_ratio / m.steps : 0.0;
+  info->mean_alpha = m.steps ? m.sum_alpha / m.steps : 0.0;
   return PIRMCUT_OK;
 }
 

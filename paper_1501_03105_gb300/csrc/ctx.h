@@ -70,9 +70,10 @@ constexpr int kMlpFeatures = 6;
 constexpr int kMlpParams = 64 * kMlpFeatures + 64 + 64 * 64 + 64 + 64 + 1;
 
 struct MlpState {
-  double res_plain;      // ||b - L~ x^(l-1)||^2 at the last step
-  double res_cand;       // ||b - L~ x_cand||^2 at the last step
-  double sum_log_ratio;  // sum over steps of log(||r_cand|| / ||r_plain||)
+  double alpha;          // step length along the learned direction, last step
+  double energy_change;  // E(x^(l-1) + alpha d) - E(x^(l-1)) <= 0, last step
+  double res_plain;      // ||b - L~ x^(l-1)||^2, last step
+  double sum_alpha;      // sum of alpha over steps
   float loss;            // mean squared error of the last minibatch
   int sel;               // 1 when the last step started from the candidate
   int steps;             // steps that evaluated a candidate
@@ -89,7 +90,7 @@ struct MlpBuf {
   float* grad_part = nullptr;    // per-block gradient sums
   float* loss_part = nullptr;
   float* feat = nullptr;         // nt x kMlpFeatures
-  double* xcand = nullptr;       // candidate start
+  double* dir = nullptr;         // learned direction d (FP64)
   double* xprev = nullptr;       // x^(l-1): reweighting point and training baseline
   double* gprev = nullptr;       // g^(l-1)
   MlpState* state = nullptr;

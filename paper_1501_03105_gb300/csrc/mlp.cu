@@ -11,10 +11,12 @@
 //   f3  mean over the incident non-terminal edges of log(g^(l) / g^(l-1)), / 8
 //   f4  log of the weighted degree (the diagonal of L~), / 8
 //   f5  log(eps_l) / 8
-// The candidate start clip(x^(l-1) + delta, 0, 1) is used only when its FP64
-// residual ||b - L~ v||_2 is below that of x^(l-1): the plain warm start is
-// both the fallback and the judge, so a badly trained model never makes the
-// start worse.  The reweighting point stays x^(l-1) (kept in xprev).
+// The start is x^(l-1) + alpha * delta with alpha from an exact line search
+// on the quadratic energy E(v) = v^T L~ v - 2 b^T v = ||v - v*||_{L~}^2 - const
+// (FP64): alpha = delta^T r / delta^T L~ delta with r = b - L~ x^(l-1).  E is
+// the error norm CG minimises, so the learned start is never worse than the
+// plain warm start (alpha = 0 is always available): x^(l-1) is both the
+// fallback and the judge.  The reweighting point stays x^(l-1) (in xprev).
 // Training runs on the trajectory the solver itself produces: after a step,
 // minibatches of nodes drawn by a counter-based hash go through hand-written
 // forward/backward kernels; each block accumulates its samples' gradients in
@@ -160,15 +162,15 @@ k_features_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __rest
   }
 }
 
-// xcand = clip(x + MLP(f), 0, 1), one node per thread.  The BF16 weights are
+// delta = MLP(f), one node per thread.  The BF16 weights are
 // widened to FP32 in shared memory with W2 transposed, so that the 64 layer-2
 // accumulators of a thread take one hidden unit k at a time from consecutive
 // (vectorisable, broadcast) shared-memory words; FP32 accumulation.
-// kDelta: write the raw output delta (FP32) instead of the clipped start.
-template <bool kDelta>
+// delta -> dir (FP64, the search direction) or out32 (FP32, inference API)
+template <bool kF32>
 __global__ void __launch_bounds__(kThreads)
 k_mlp_predict(int64_t nt, const float* __restrict__ f, const __nv_bfloat16* __restrict__ w16,
-              const double* __restrict__ x, double* __restrict__ xcand, float* __restrict__ delta) {
+              double* __restrict__ dir, float* __restrict__ out32) {
   extern __shared__ __align__(16) float sw[];
   for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) {
     int dst = i;
@@ -200,91 +202,109 @@ k_mlp_predict(int64_t nt, const float* __restrict__ f, const __nv_bfloat16* __re
     float out = sw[OFF_B3];
 #pragma unroll
     for (int j = 0; j < H; ++j) out = fmaf(sw[OFF_W3 + j], fmaxf(z[j], 0.0f), out);
-    if (kDelta) delta[i] = out;
-    else xcand[i] = fmin(fmax(x[i] + double(out), 0.0), 1.0);
+    if (kF32) out32[i] = out;
+    else dir[i] = double(out);
   }
 }
 
-// ||b - L~ v||^2 for a start v: conductances g of this step, terminal
-// conductances from the reweighting point xw; total -> *out
+// Line search along the learned direction d from x = x^(l-1): with
+// r = b - L~ x, the last block forms alpha = (d, r) / (d, L~ d) (0 when the
+// denominator is not positive and finite) and the energy change
+// -(d, r)^2 / (d, L~ d).
+__device__ __forceinline__ void linesearch_finish(double dr, double dad, double rr, double* partials,
+                                                  MlpState* M) {
+  double v[3] = {dr, dad, rr}, tot[3];
+  if (grid_sum<3>(v, partials, &M->counter, tot) && threadIdx.x == 0) {
+    const double a = tot[1] > 0.0 ? tot[0] / tot[1] : 0.0;
+    const bool ok = isfinite(a) && a != 0.0;
+    M->alpha = ok ? a : 0.0;
+    M->energy_change = ok ? -tot[0] * a : 0.0;
+    M->res_plain = tot[2];
+  }
+}
+
 template <int K>
 __global__ void __launch_bounds__(kThreads)
-k_resnorm_dia(DiaDesc d, const double* __restrict__ g, const double* __restrict__ cs,
-              const double* __restrict__ ct, const double* __restrict__ xw,
-              const double* __restrict__ v, const double* __restrict__ eps_list,
-              const StepCounters* __restrict__ C, int form, double* partials,
-              unsigned int* counter, double* out) {
+k_linesearch_dia(DiaDesc d, const double* __restrict__ g, const double* __restrict__ cs,
+                 const double* __restrict__ ct, const double* __restrict__ x,
+                 const double* __restrict__ dir, const double* __restrict__ eps_list,
+                 const StepCounters* __restrict__ C, int form, double* partials, MlpState* M) {
   const int64_t nt = d.nt;
   const double eps = eps_list[C->eps_idx];
   const double eps2 = eps * eps;
-  double rr = 0.0;
+  double dr = 0.0, dad = 0.0, rr = 0.0;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nt;
        i += int64_t(gridDim.x) * blockDim.x) {
-    const double xi = xw[i];
+    const double xi = x[i], di = dir[i];
     const double gs = conductance(cs[i], 1.0 - xi, eps2, form);
     const double gt = conductance(ct[i], xi, eps2, form);
-    double sum = gs + gt, ax = 0.0;
+    double sum = gs + gt, ax = 0.0, ad = 0.0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int64_t o = d.off[k];
       if (i + o < nt) {
-        sum += g[k * nt + i];
-        ax = fma(g[k * nt + i], v[i + o], ax);
+        const double w = g[k * nt + i];
+        sum += w;
+        ax = fma(w, x[i + o], ax);
+        ad = fma(w, dir[i + o], ad);
       }
       if (i >= o) {
-        sum += g[k * nt + i - o];
-        ax = fma(g[k * nt + i - o], v[i - o], ax);
+        const double w = g[k * nt + i - o];
+        sum += w;
+        ax = fma(w, x[i - o], ax);
+        ad = fma(w, dir[i - o], ad);
       }
     }
-    const double r = gs - fma(sum, v[i], -ax);
+    const double r = gs - fma(sum, xi, -ax);
+    dr = fma(di, r, dr);
+    dad = fma(di, fma(sum, di, -ad), dad);
     rr = fma(r, r, rr);
   }
-  double a[1] = {rr}, tot[1];
-  if (grid_sum<1>(a, partials, counter, tot) && threadIdx.x == 0) *out = tot[0];
+  linesearch_finish(dr, dad, rr, partials, M);
 }
 
 __global__ void __launch_bounds__(kThreads)
-k_resnorm_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-              const double* __restrict__ g, const double* __restrict__ cs,
-              const double* __restrict__ ct, const double* __restrict__ xw,
-              const double* __restrict__ v, const double* __restrict__ eps_list,
-              const StepCounters* __restrict__ C, int form, double* partials,
-              unsigned int* counter, double* out) {
+k_linesearch_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                 const double* __restrict__ g, const double* __restrict__ cs,
+                 const double* __restrict__ ct, const double* __restrict__ x,
+                 const double* __restrict__ dir, const double* __restrict__ eps_list,
+                 const StepCounters* __restrict__ C, int form, double* partials, MlpState* M) {
   const double eps = eps_list[C->eps_idx];
   const double eps2 = eps * eps;
-  double rr = 0.0;
+  double dr = 0.0, dad = 0.0, rr = 0.0;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nt;
        i += int64_t(gridDim.x) * blockDim.x) {
-    const double xi = xw[i];
+    const double xi = x[i], di = dir[i];
     const double gs = conductance(cs[i], 1.0 - xi, eps2, form);
     const double gt = conductance(ct[i], xi, eps2, form);
-    double sum = gs + gt, ax = 0.0;
+    double sum = gs + gt, ax = 0.0, ad = 0.0;
     for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
-      sum += g[e];
-      ax = fma(g[e], v[col[e]], ax);
+      const double w = g[e];
+      sum += w;
+      ax = fma(w, x[col[e]], ax);
+      ad = fma(w, dir[col[e]], ad);
     }
-    const double r = gs - fma(sum, v[i], -ax);
+    const double r = gs - fma(sum, xi, -ax);
+    dr = fma(di, r, dr);
+    dad = fma(di, fma(sum, di, -ad), dad);
     rr = fma(r, r, rr);
   }
-  double a[1] = {rr}, tot[1];
-  if (grid_sum<1>(a, partials, counter, tot) && threadIdx.x == 0) *out = tot[0];
+  linesearch_finish(dr, dad, rr, partials, M);
 }
 
-// x := xcand when the candidate's residual is strictly smaller
+// x += alpha * d
 __global__ void __launch_bounds__(kThreads)
-k_mlp_commit(int64_t nt, MlpState* M, const double* __restrict__ xcand, double* __restrict__ x) {
-  const double rc = M->res_cand, rp = M->res_plain;
-  const int use = rc < rp ? 1 : 0;
-  if (use) {
+k_mlp_commit(int64_t nt, MlpState* M, const double* __restrict__ dir, double* __restrict__ x) {
+  const double a = M->alpha;
+  if (a != 0.0) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nt;
          i += int64_t(gridDim.x) * blockDim.x)
-      x[i] = xcand[i];
+      x[i] = fma(a, dir[i], x[i]);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    M->sel = use;
     M->steps += 1;
-    M->used += use;
-    if (rc > 0.0 && rp > 0.0) M->sum_log_ratio += 0.5 * log(rc / rp);
+    M->used += a != 0.0 ? 1 : 0;
+    M->sum_alpha += a;
   }
 }
 
@@ -419,7 +439,7 @@ cudaError_t mlp_alloc(Ctx& c) {
   A((void**)&b.grad_part, sizeof(float) * NPARAM * TRAIN_BLOCKS);
   A((void**)&b.loss_part, sizeof(float) * TRAIN_BLOCKS);
   A((void**)&b.feat, sizeof(float) * NF * size_t(c.nt));
-  A((void**)&b.xcand, sizeof(double) * size_t(c.nt));
+  A((void**)&b.dir, sizeof(double) * size_t(c.nt));
   A((void**)&b.xprev, sizeof(double) * size_t(c.nt));
   A((void**)&b.gprev, sizeof(double) * ng);
   A((void**)&b.state, sizeof(MlpState));
@@ -431,7 +451,7 @@ cudaError_t mlp_alloc(Ctx& c) {
 
 void mlp_free(Ctx& c) {
   MlpBuf& b = c.mlp;
-  void* ps[] = {b.master, b.w16, b.m, b.v, b.grad_part, b.loss_part, b.feat, b.xcand,
+  void* ps[] = {b.master, b.w16, b.m, b.v, b.grad_part, b.loss_part, b.feat, b.dir,
                 b.xprev, b.gprev, b.state};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -492,8 +512,8 @@ int enqueue_mlp_pre(Ctx& c, cudaStream_t st) {
   return 0;
 }
 
-// After the reweighting: features; with prediction on, the candidate, the
-// residual norms of both starts and the choice (x := candidate if better).
+// After the reweighting: features; with prediction on, the learned
+// direction, the line search along it and the move x += alpha d.
 // Returns the kernels enqueued.
 int enqueue_mlp_post(Ctx& c, cudaStream_t st) {
   MlpBuf& b = c.mlp;
@@ -507,23 +527,18 @@ int enqueue_mlp_post(Ctx& c, cudaStream_t st) {
                                               c.eps_list, c.C, form, b.feat);
   }
   if (!(c.mlp_mode & PIRMCUT_MLP_PREDICT)) return 1;
-  k_mlp_predict<false><<<grid, kThreads, sizeof(float) * NPARAM, st>>>(c.nt, b.feat, b.w16, c.x,
-                                                                       b.xcand, nullptr);
-  unsigned int* counter = &b.state->counter;
-  for (int which = 0; which < 2; ++which) {
-    const double* v = which == 0 ? c.x : b.xcand;
-    double* out = which == 0 ? &b.state->res_plain : &b.state->res_cand;
-    if (c.format == PIRMCUT_FORMAT_DIA) {
-      PIRMCUT_DISPATCH_K(c.K, (k_resnorm_dia<KK><<<grid, kThreads, 0, st>>>(
-                                  c.dd, c.gdia, c.cs, c.ct, c.x, v, c.eps_list, c.C, form,
-                                  c.partials, counter, out)));
-    } else {
-      k_resnorm_csr<<<grid, kThreads, 0, st>>>(c.nt, c.rp, c.col, c.gval, c.cs, c.ct, c.x, v,
-                                               c.eps_list, c.C, form, c.partials, counter, out);
-    }
+  k_mlp_predict<false><<<grid, kThreads, sizeof(float) * NPARAM, st>>>(c.nt, b.feat, b.w16, b.dir,
+                                                                       nullptr);
+  if (c.format == PIRMCUT_FORMAT_DIA) {
+    PIRMCUT_DISPATCH_K(c.K, (k_linesearch_dia<KK><<<grid, kThreads, 0, st>>>(
+                                c.dd, c.gdia, c.cs, c.ct, c.x, b.dir, c.eps_list, c.C, form,
+                                c.partials, b.state)));
+  } else {
+    k_linesearch_csr<<<grid, kThreads, 0, st>>>(c.nt, c.rp, c.col, c.gval, c.cs, c.ct, c.x, b.dir,
+                                                c.eps_list, c.C, form, c.partials, b.state);
   }
-  k_mlp_commit<<<grid, kThreads, 0, st>>>(c.nt, b.state, b.xcand, c.x);
-  return 5;
+  k_mlp_commit<<<grid, kThreads, 0, st>>>(c.nt, b.state, b.dir, c.x);
+  return 4;
 }
 
 // After the solve of a step, with training on: iters_per_step Adam steps on
@@ -543,7 +558,7 @@ int enqueue_mlp_train(Ctx& c, cudaStream_t st) {
 // Inference on caller-supplied features (count x kMlpFeatures, device) -> delta (device).
 cudaError_t mlp_predict_delta(Ctx& c, const float* feat, int64_t count, float* delta) {
   k_mlp_predict<true><<<grid_for(count), kThreads, sizeof(float) * NPARAM, c.stream>>>(
-      count, feat, c.mlp.w16, nullptr, nullptr, delta);
+      count, feat, c.mlp.w16, nullptr, delta);
   c.launches += 1;
   return cudaGetLastError();
 }

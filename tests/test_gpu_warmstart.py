@@ -5,8 +5,9 @@ Bars:
   within 2e-6 absolute), f3 from FP32 logarithms (within 1e-5 absolute);
 * inference: within the oracle's rigorous bound on an FP32 fused
   multiply-add evaluation of the network;
-* candidate residuals: relative 1e-9 where the candidate is exact on both
-  sides (a constant delta), 1e-5 where it comes from the network;
+* line search: alpha and the energy change to relative 1e-9 (1e-7 for the
+  change, a quotient of FP64 sums) where the direction is exact on both sides
+  (a constant), to relative 1e-5 where it comes from the FP32 network;
 * the solve after a learned start: the same 1e-9 bar on x as every step;
 * training: after one Adam step from zero moments, each parameter whose oracle
   gradient is clearly signed moved by -lr * sign(gradient).
@@ -122,9 +123,8 @@ def test_inference_device_buffers(P):
 
 @pytest.mark.parametrize("fmt", [0, 2])
 def test_untrained_model_is_bit_identical_to_the_plain_start(P, fmt):
-    """A fresh model has a zero output layer: the candidate equals x^(l-1),
-    is never strictly better, and every step is bit-identical to the plain
-    warm start."""
+    """A fresh model has a zero output layer: d = 0, alpha = 0, and every step
+    is bit-identical to the plain warm start."""
     g = gen.config_graph(1)
     T = 10
     eps = O.eps_schedule(T)
@@ -135,14 +135,14 @@ def test_untrained_model_is_bit_identical_to_the_plain_start(P, fmt):
         assert np.array_equal(a.get_x(), b.get_x())
         assert [i.pcg_iters for i in ia] == [i.pcg_iters for i in ib]
         st = b.mlp_stats()
-        assert st.steps == T and st.used == 0
+        assert st.steps == T and st.used == 0 and st.alpha == 0.0
 
 
 @pytest.mark.parametrize("fmt", [0, 2])
 @pytest.mark.parametrize("delta", [-1 / 32, 1 / 64])
-def test_constant_candidate_residuals_and_choice(P, fmt, delta):
-    """delta = const (only b3 set): both candidate residuals are exact on both
-    sides; the choice and the solution follow the oracle."""
+def test_constant_direction_line_search(P, fmt, delta):
+    """d = const (only b3 set): the line search is exact on both sides; alpha,
+    the energy change, the plain residual and the solution follow the oracle."""
     g = gen.config_graph(1, scale=24)
     prob = O.Problem.from_graph(g)
     T = 6
@@ -154,27 +154,26 @@ def test_constant_candidate_residuals_and_choice(P, fmt, delta):
         s.initial()
         s.mlp_enable(P.binding.MLP_PREDICT, seed=1)
         s.mlp_weights(w)
-        used = 0
         for l in range(1, T + 1):
             s.set_x(xs[l - 1])
             s.irls_step(eps[l - 1])
             gl = O.reweight(prob, xs[l - 1], eps[l - 1])
             v0 = reduced(prob, xs[l - 1])
-            rp = W.residual_norm(prob, gl, v0)
-            rc = W.residual_norm(prob, gl, W.candidate_start(v0, np.full(v0.shape, delta)))
+            alpha, dE = W.line_search(prob, gl, v0, np.full(v0.shape, delta))
             st = s.mlp_stats()
-            assert st.res_plain == pytest.approx(rp, rel=1e-9)
-            assert st.res_candidate == pytest.approx(rc, rel=1e-9)
-            used += int(rc < rp)
-            assert st.used == used
+            assert st.alpha == pytest.approx(alpha, rel=1e-9)
+            assert st.energy_change == pytest.approx(dE, rel=1e-7)
+            assert st.energy_change <= 0.0
+            assert st.res_plain == pytest.approx(W.residual_norm(prob, gl, v0), rel=1e-9)
+            assert st.used == l
             assert np.max(np.abs(s.get_x() - xs[l])) <= XTOL, l
 
 
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("fmt", [0, 2])
-def test_jacobi_candidate_is_taken_and_the_solve_stays_exact(P, fmt, precision):
-    """Weights that output half a Jacobi step: the candidate usually has the
-    smaller residual; the GPU's residuals and choices follow the oracle's, and
+def test_jacobi_direction_and_the_solve_stays_exact(P, fmt, precision):
+    """Weights that output half a Jacobi correction: the GPU's line search
+    follows the oracle's on the network's output, the energy decreases, and
     every step still meets the 1e-9 bar on x (FP64 and mixed solvers)."""
     g = gen.config_graph(1, scale=32)
     prob = O.Problem.from_graph(g)
@@ -187,7 +186,6 @@ def test_jacobi_candidate_is_taken_and_the_solve_stays_exact(P, fmt, precision):
         s.initial()
         s.mlp_enable(P.binding.MLP_PREDICT, seed=1)
         s.mlp_weights(w)
-        used = 0
         for l in range(1, T + 1):
             s.set_x(xs[l - 1])
             info = s.irls_step(eps[l - 1])
@@ -196,19 +194,13 @@ def test_jacobi_candidate_is_taken_and_the_solve_stays_exact(P, fmt, precision):
             F = W.features(prob, xs[l - 1], gl, gprev, eps[l - 1])
             out, bound = W.mlp_forward(w, F)
             v0 = reduced(prob, xs[l - 1])
-            rp = W.residual_norm(prob, gl, v0)
-            rc = W.residual_norm(prob, gl, W.candidate_start(v0, out))
+            alpha, dE = W.line_search(prob, gl, v0, out)
             st = s.mlp_stats()
-            assert st.res_plain == pytest.approx(rp, rel=1e-9)
-            assert st.res_candidate == pytest.approx(rc, rel=1e-5)
-            if abs(rc - rp) > 1e-4 * rp:
-                used += int(rc < rp)
-                assert st.used == used, l
-            else:
-                used = st.used
+            assert st.alpha == pytest.approx(alpha, rel=1e-5)
+            assert st.energy_change == pytest.approx(dE, rel=1e-4)
+            assert st.energy_change < 0.0
             assert np.max(np.abs(s.get_x() - xs[l])) <= XTOL, l
             gprev = gl
-        assert used >= 1
 
 
 @pytest.mark.parametrize("fmt", [0, 2])

@@ -220,9 +220,32 @@ def test_residual_norm_at_zero_and_at_the_solution():
     assert W.residual_norm(prob, g, v) <= 1e-12 * np.linalg.norm(b)
 
 
-def test_candidate_is_clipped():
-    c = W.candidate_start(np.array([0.1, 0.9, 0.5]), np.array([-0.3, 0.3, 0.25]))
-    assert np.array_equal(c, [0.0, 1.0, 0.75])
+def test_energy_identity_and_line_search_optimality():
+    """E(v) - E(v*) = ||v - v*||^2_{L~}; the line search's alpha minimises E
+    along d and its energy change is E(v0 + alpha d) - E(v0)."""
+    g0 = gen.config_graph(1, scale=10)
+    prob = O.Problem.from_graph(g0)
+    rng = np.random.default_rng(3)
+    x = np.clip(O.wls_step(prob, O.initial_conductance(prob))[0] + rng.normal(0, 0.05, prob.n), 0, 1)
+    x[prob.s], x[prob.t] = 1.0, 0.0
+    g = O.reweight(prob, x, 0.05)
+    Lt, b = O.reduced_system(prob, O.laplacian(prob, g))
+    vs = O.solve_direct(Lt, b)
+    v = x[prob.nonterminals]
+    e = v - vs
+    assert W.energy(prob, g, v) - W.energy(prob, g, vs) == pytest.approx(e @ (Lt @ e), rel=1e-9)
+    d = rng.normal(0, 1, prob.nt)
+    alpha, dE = W.line_search(prob, g, v, d)
+    E0 = W.energy(prob, g, v)
+    assert W.energy(prob, g, v + alpha * d) - E0 == pytest.approx(dE, rel=1e-6)
+    assert dE < 0
+    for h in (1e-3, -1e-3):
+        assert W.energy(prob, g, v + (alpha + h) * d) > E0 + dE
+    # the exact error direction: alpha = 1 and the solution is reached
+    alpha, dE = W.line_search(prob, g, v, vs - v)
+    assert alpha == pytest.approx(1.0, rel=1e-9)
+    assert dE == pytest.approx(-(e @ (Lt @ e)), rel=1e-9)
+    assert W.line_search(prob, g, v, np.zeros(prob.nt)) == (0.0, 0.0)
 
 
 # --- mutants ------------------------------------------------------------------
@@ -230,7 +253,7 @@ def test_candidate_is_clipped():
 PINS = [test_features_hand_example, test_features_constant_field_and_unchanged_conductances,
         test_gradient_matches_finite_differences, test_forward_error_bound_covers_float32_fma_evaluation,
         test_adam_moves_by_lr_times_sign_for_a_constant_gradient, test_bf16_round_cases,
-        test_splitmix64_published_sequence]
+        test_splitmix64_published_sequence, test_energy_identity_and_line_search_optimality]
 
 
 def _features_no_terminals(prob, x, g, g_prev, eps):
@@ -280,6 +303,16 @@ def _bf16_truncate(a):
     return (u & 0xFFFF0000).astype(np.uint32).view(np.float32)
 
 
+def _line_search_sign(prob, g, v0, d):
+    alpha, dE = _ORIG["line_search"](prob, g, v0, d)
+    return -alpha, dE
+
+
+def _energy_without_factor_two(prob, g, v):
+    Lt, b = O.reduced_system(prob, O.laplacian(prob, g))
+    return float(v @ (Lt @ v) - b @ v)
+
+
 def _splitmix_wrong_shift(z):
     z = (z + 0x9E3779B97F4A7C15) & W.MASK64
     z = ((z ^ (z >> 31)) * 0xBF58476D1CE4E5B9) & W.MASK64
@@ -287,7 +320,8 @@ def _splitmix_wrong_shift(z):
     return z ^ (z >> 31)
 
 
-_ORIG = {k: getattr(W, k) for k in ("features", "mlp_gradient", "adam_step", "bf16_round", "splitmix64")}
+_ORIG = {k: getattr(W, k) for k in ("features", "mlp_gradient", "adam_step", "bf16_round", "splitmix64",
+                                    "line_search", "energy")}
 
 MUTANTS = [
     ("features", _features_no_terminals),
@@ -297,6 +331,8 @@ MUTANTS = [
     ("adam_step", _adam_no_bias_correction),
     ("bf16_round", _bf16_truncate),
     ("splitmix64", _splitmix_wrong_shift),
+    ("line_search", _line_search_sign),
+    ("energy", _energy_without_factor_two),
 ]
 
 
