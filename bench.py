@@ -344,8 +344,9 @@ def run_sequence(args):
     }
     solvers = {}
     for name, (prec, mode) in arms.items():
-        opt = B.pirmcut_default_options(pcg_tol=PCG_TOL, precision=prec, track_cut=1,
-                                        inner_tol=args.inner_tol)
+        opt = B.pirmcut_default_options(pcg_tol=args.seq_tol, precision=prec, track_cut=1,
+                                        inner_tol=min(args.inner_tol, args.seq_tol),
+                                        graph_launch=int(args.launch == "graph"))
         solvers[name] = B.Solver(base, opt, stream=stream)
     trainer = solvers["learned_fp64"]
     trainer.mlp_enable(B.MLP_PREDICT | B.MLP_TRAIN, seed=5)
@@ -427,7 +428,9 @@ def run_sequence(args):
         "config": {"workload": f"seq{W_side}: sequence of {P} {W_side}^3 6-connected volume problems, "
                                f"capacities x exp(N(0,0.01)) per edge per problem, seed 5",
                    "train_problems": P_train, "eval_problems": P - P_train, "T": T,
-                   "pcg_tol": PCG_TOL, "step": "x0 + 30 IRLS steps + sweep cut per problem"},
+                   "pcg_tol": args.seq_tol, "step": "x0 + 30 IRLS steps + sweep cut per problem",
+                   "time_to_cut": "device time until the step whose sweep cut is within 1e-6 "
+                                  "of the plain FP64 arm's final cut"},
         "arms": summary,
         "learned_start_use": log_ratio,
         "training": {"problems": P_train, "adam_steps": tstats.train_steps,
@@ -451,6 +454,7 @@ def main():
     ap.add_argument("--workload", default="grid2048", choices=list(WORKLOADS) + ["chunglu64", "seq128"])
     ap.add_argument("--problems", type=int, default=200, help="seq128: problems in the sequence")
     ap.add_argument("--seq-scale", type=int, default=128, help="seq128: side of the volume")
+    ap.add_argument("--seq-tol", type=float, default=PCG_TOL, help="seq128: PCG tolerance")
     ap.add_argument("--inner-tol", type=float, default=1e-5,
                     help="mixed path: relative reduction of each FP32 inner solve")
     ap.add_argument("--only", default=None, choices=["fp64", "mixed"],

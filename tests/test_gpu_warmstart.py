@@ -49,6 +49,26 @@ def reduced(prob, x):
     return x[prob.nonterminals]
 
 
+def line_search_tolerance(prob, g, v0, d, e):
+    """First-order bound on how far alpha and the energy change can move when
+    every entry of d may be off by at most e (e >= 0, per node)."""
+    Lt, b = O.reduced_system(prob, O.laplacian(prob, g))
+    r = b - Lt @ v0
+    Ad = Lt @ d
+    dr, dad = float(d @ r), float(d @ Ad)
+    er, ead = float(e @ np.abs(r)), float(e @ np.abs(Ad))
+    ta = (er + 2 * abs(dr / dad) * ead) / dad
+    tE = 2 * abs(dr) * er / dad + 2 * dr * dr * ead / dad ** 2
+    return ta, tE
+
+
+def feature_ulps(F):
+    """One unit in the last place of each FP32 feature (both sides round
+    their FP64 values once, so they may differ by that much)."""
+    F = np.asarray(F, dtype=np.float32)
+    return np.abs(np.spacing(F)).astype(np.float64)
+
+
 def jacobi_weights(alpha):
     """Weights whose output is alpha * (f1 - f0): one damped Jacobi step,
     since f1 - f0 = (sum_u g x_u) / d_v - x_v = r_v / d_v."""
@@ -195,9 +215,15 @@ def test_jacobi_direction_and_the_solve_stays_exact(P, fmt, precision):
             out, bound = W.mlp_forward(w, F)
             v0 = reduced(prob, xs[l - 1])
             alpha, dE = W.line_search(prob, gl, v0, out)
+            # d = 0.5 (f1 - f0): the network's own bound plus one ulp of each
+            # input feature on either side
+            ul = feature_ulps(F)
+            e = bound + 0.5 * 2 * (ul[:, 0] + ul[:, 1])
+            ta, tE = line_search_tolerance(prob, gl, v0, out, e)
             st = s.mlp_stats()
-            assert st.alpha == pytest.approx(alpha, rel=1e-5)
-            assert st.energy_change == pytest.approx(dE, rel=1e-4)
+            assert abs(st.alpha - alpha) <= 2 * ta + 1e-12 * abs(alpha), (st.alpha, alpha, ta)
+            assert abs(st.energy_change - dE) <= 2 * tE + 1e-9 * abs(dE), (st.energy_change, dE, tE)
+            assert abs(st.alpha - alpha) <= 1e-3 * abs(alpha)
             assert st.energy_change < 0.0
             assert np.max(np.abs(s.get_x() - xs[l])) <= XTOL, l
             gprev = gl
