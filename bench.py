@@ -60,6 +60,21 @@ def dist_env():
     return ws, rank, local
 
 
+def job_totals(units, seconds, dist=None, device="cpu"):
+    """Whole-job (units, seconds) over the ranks of a process group: units
+    summed (every rank's own work), seconds the slowest rank's.  Without a
+    group, the local values."""
+    if dist is None:
+        return float(units), float(seconds)
+    import torch
+    t = torch.tensor([float(units), float(seconds)], dtype=torch.float64, device=device)
+    u = t[:1].clone()
+    m = t[1:].clone()
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(m.item())
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -528,10 +543,9 @@ def main():
             clk.__exit__(None, None, None)
         ms = ev0.elapsed_time(ev1)
         launches = solver.kernel_launches() - launches0
+        nt_, ne_, _ = solver.problem_size()
+        job_units, ms = job_totals(ne_ * iters, ms, dist, "cuda")
         if dist:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
             dist.barrier()
         x_final = solver.get_x()
         spmv_ms, spmv_bytes, spmv_flops = solver.time_spmv(reps=30)
@@ -541,7 +555,8 @@ def main():
         opt.track_cut = 1
         with B.Solver(g, opt, stream=stream) as s2:
             infos = s2.solve(T_STEPS, eps)
-        return dict(ms=ms, iters=iters, refine=refine, cut=cut_value, launches=launches,
+        return dict(ms=ms, iters=iters, job_units=job_units, refine=refine, cut=cut_value,
+                    launches=launches,
                     x=x_final, spmv=(spmv_ms, spmv_bytes, spmv_flops), nt=nt, ne=ne, fmt=fmt,
                     track=[(i.cut_value, i.ms) for i in infos],
                     clocks=clk.summary() if clk else None)
@@ -555,7 +570,7 @@ def main():
     nt, ne, fmt = r64["nt"], r64["ne"], r64["fmt"]
     iters, ms, launches, cut_value = r64["iters"], r64["ms"], r64["launches"], r64["cut"]
     ms_step = ms / args.steps
-    value = ws * ne * iters / (ms / 1e3)
+    value = r64["job_units"] / (ms / 1e3)
     mu_ref = cut_value
 
     def time_to_cut(track):
@@ -584,7 +599,7 @@ def main():
     m_ms, m_bytes, m_flops = rmx["spmv"]
     m_gbs = m_bytes / (m_ms * 1e-3) / 1e9
     mixed = {
-        "value": ws * ne * rmx["iters"] / (rmx["ms"] / 1e3), "unit": UNIT,
+        "value": rmx["job_units"] / (rmx["ms"] / 1e3), "unit": UNIT,
         "ms_per_step": rmx["ms"] / args.steps,
         "speedup_vs_fp64_per_step": ms_step / (rmx["ms"] / args.steps),
         "pcg_iters_per_step": rmx["iters"] / args.steps,
@@ -623,11 +638,8 @@ def main():
             e_iters += sum(i.pcg_iters for i in infos)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": ws * ne * e_iters / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e_units, dt = job_totals(ne * e_iters, dt, dist, "cuda")
+        e2e = {"value": e_units / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * dt / reps,
                "includes": "create (host CSR upload + packing), solve, sweep cut, side D2H, destroy"}
 

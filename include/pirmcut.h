@@ -210,10 +210,12 @@ int64_t pirmcut_kernel_launches(const pirmcut_ctx* ctx);
 
 /*
  * Diagnostics for roofline reports: time the PCG matrix-vector kernel
- * (q = L~ p with the fused (p, q) reduction, Section 3.1; the FP32 inner one
- * for MIXED contexts) on the current matrix and search direction, `reps` launches bracketed one by one with CUDA
- * events on the context's stream.  Needs a completed step (EINVAL otherwise);
- * leaves x untouched.  avg_ms receives the mean launch time; bytes and flops
+ * (q = L~ p with the fused (p, q) reduction, Section 3.1; for MIXED contexts
+ * the FP32 inner one, which on DIA grids whose width is a multiple of 4 also
+ * forms the new search direction and applies the previous d update) on the
+ * current matrix and search direction, `reps` launches bracketed one by one
+ * with CUDA events on the context's stream.  Needs a completed step (EINVAL
+ * otherwise); leaves x untouched (the FP32 scratch vectors are overwritten).  avg_ms receives the mean launch time; bytes and flops
  * (either may be NULL) the algorithmic bytes moved and floating-point
  * operations of one launch (every stored value, matrix index and vector entry
  * read or written once; an FMA counts 2).

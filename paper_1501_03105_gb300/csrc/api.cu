@@ -246,8 +246,16 @@ pirmcut_status run_steps(pirmcut_ctx* h, bool with_initial, int T, int first_ste
     cudaEventElapsedTime(&ms, h->events[k], h->events[k + 1]);
     pirmcut_step_info info;
     fill_info(c, c.h_recs[k], ms, &info);
-    if (graphs)
-      c.launches += 3LL * info.pcg_iters + 2LL * info.refinements;
+    if (graphs) {
+      // kernels inside the graphs' loops: three per CG iteration, two with the
+      // fused recurrence (whose loop body holds two iterations, so a solve with
+      // an odd count also runs one pair of no-op kernels), plus the residual
+      // and the x update per refinement
+      if (c.fused_inner && c.opt.precision == PIRMCUT_PREC_MIXED)
+        c.launches += 2LL * info.pcg_iters + 3LL * info.refinements;
+      else
+        c.launches += 3LL * info.pcg_iters + 2LL * info.refinements;
+    }
     if (infos) infos[k] = info;
     if (info.status == PIRMCUT_ENUMERIC) worst = PIRMCUT_ENUMERIC;
     else if (info.status == PIRMCUT_ENOCONV && worst == PIRMCUT_OK) worst = PIRMCUT_ENOCONV;
@@ -547,8 +555,9 @@ pirmcut_status pirmcut_time_spmv(pirmcut_ctx* h, int reps, double* avg_ms, doubl
   const bool mx = c.opt.precision == PIRMCUT_PREC_MIXED;
   const double V = mx ? 4.0 : 8.0;
   // vectors read/written once per row: diag, p, q (the FP32 inner system is
-  // scaled to unit diagonal: p and q only)
-  const double nvec = mx ? 2.0 : 3.0;
+  // scaled to unit diagonal: p and q only; the fused FP32 kernel also reads
+  // r and d and writes the new p and d)
+  const double nvec = mx ? (c.fused_inner ? 6.0 : 2.0) : 3.0;
   if (bytes) {
     *bytes = c.format == PIRMCUT_FORMAT_DIA ? nt * (V * c.K + V * nvec)
                                             : nnz * (V + 4.0) + nt * (V * nvec + 8.0);

@@ -141,10 +141,13 @@ struct Ctx {
   float* s32 = nullptr;
   float* r32 = nullptr;         // scaled inner residual
   float* p32 = nullptr;
+  float* p32b = nullptr;        // second direction buffer of the fused recurrence
   float* q32 = nullptr;
   float* d32 = nullptr;         // scaled correction
   double* b64 = nullptr;        // right-hand side (FP64)
   OuterState* O = nullptr;
+  bool fused_inner = false;     // two-kernel inner CG iteration (vectorised DIA)
+  int fused_grid = 1;
   StepCounters* C = nullptr;
   double* eps_list = nullptr;   // capacity eps_cap
   int eps_cap = 0;

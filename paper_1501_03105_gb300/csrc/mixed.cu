@@ -42,6 +42,14 @@
 #ifndef PIRMCUT_SPMV_UNROLL
 #define PIRMCUT_SPMV_UNROLL 1
 #endif
+// Two-kernel CG iteration on vectorised DIA grids (1) or the three-kernel one (0).
+#ifndef PIRMCUT_FUSED_INNER
+#define PIRMCUT_FUSED_INNER 1
+#endif
+// Minimum resident blocks per SM for the fused SpMV (caps its registers).
+#ifndef PIRMCUT_FUSED_MINB
+#define PIRMCUT_FUSED_MINB 4
+#endif
 
 namespace pirmcut {
 
@@ -508,6 +516,80 @@ k_spmv32v_dia(DiaDesc d, const float* __restrict__ g, const float* __restrict__ 
   spmv32_finish(pq, partials, S);
 }
 
+// The vectorised SpMV with the previous iteration's vector updates folded in
+// (two kernels per CG iteration instead of three): with beta and the pending
+// alpha of the previous iteration,
+//   p_new = r + beta p_old     (own rows, and recomputed for the neighbours)
+//   d    += alpha p_old        (the update the previous iteration left pending)
+//   q     = A^ p_new,  (p_new, q)
+// p_old and p_new are two buffers used in turn.  Every value is formed by the
+// same FMAs as in the three-kernel recurrence, so the iterates are identical.
+// The update of d left pending by the last iteration is applied by k_xupdate.
+template <int K>
+__global__ void __launch_bounds__(kThreads, PIRMCUT_FUSED_MINB)
+k_spmv32v_fused_dia(DiaDesc d, const float* __restrict__ g, const float* __restrict__ r,
+                    const float* __restrict__ pold, float* __restrict__ pnew, float* __restrict__ dv,
+                    float* __restrict__ q, double* partials, PcgState* S) {
+  if (S->stop_req) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) S->stopped = 1;
+    return;
+  }
+  const float alpha = float(S->alpha), beta = float(S->beta);
+  const int64_t nt = d.nt, n4 = nt >> 2;
+  FF pq{0.f, 0.f};
+  for (int64_t t = gtid(); t < n4; t += gstride()) {
+    const int64_t i0 = t << 2;
+    const float4 po = ld4(pold + i0), r4 = ld4(r + i0), d4 = ld4(dv + i0);
+    const float4 p4 = make_float4(fmaf(beta, po.x, r4.x), fmaf(beta, po.y, r4.y),
+                                  fmaf(beta, po.z, r4.z), fmaf(beta, po.w, r4.w));
+    st4(pnew + i0, p4);
+    st4(dv + i0, make_float4(fmaf(alpha, po.x, d4.x), fmaf(alpha, po.y, d4.y),
+                             fmaf(alpha, po.z, d4.z), fmaf(alpha, po.w, d4.w)));
+    float a0 = p4.x, a1 = p4.y, a2 = p4.z, a3 = p4.w;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int64_t o = d.off[k];
+      const float* gk = g + k * nt;
+      const float4 gu = ld4(gk + i0);
+      if (o == 1) {
+        const float pn = (i0 + 4 < nt) ? fmaf(beta, pold[i0 + 4], r[i0 + 4]) : 0.f;
+        const float gl = (i0 >= 1) ? gk[i0 - 1] : 0.f;
+        const float pl = (i0 >= 1) ? fmaf(beta, pold[i0 - 1], r[i0 - 1]) : 0.f;
+        a0 = fmaf(-gu.x, p4.y, a0);
+        a1 = fmaf(-gu.y, p4.z, a1);
+        a2 = fmaf(-gu.z, p4.w, a2);
+        a3 = fmaf(-gu.w, pn, a3);
+        a0 = fmaf(-gl, pl, a0);
+        a1 = fmaf(-gu.x, p4.x, a1);
+        a2 = fmaf(-gu.y, p4.y, a2);
+        a3 = fmaf(-gu.z, p4.z, a3);
+      } else {
+        if (i0 + o < nt) {
+          const float4 ou = ld4(pold + i0 + o), ru = ld4(r + i0 + o);
+          a0 = fmaf(-gu.x, fmaf(beta, ou.x, ru.x), a0);
+          a1 = fmaf(-gu.y, fmaf(beta, ou.y, ru.y), a1);
+          a2 = fmaf(-gu.z, fmaf(beta, ou.z, ru.z), a2);
+          a3 = fmaf(-gu.w, fmaf(beta, ou.w, ru.w), a3);
+        }
+        if (i0 >= o) {
+          const float4 gl = ld4(gk + i0 - o);
+          const float4 ol = ld4(pold + i0 - o), rl = ld4(r + i0 - o);
+          a0 = fmaf(-gl.x, fmaf(beta, ol.x, rl.x), a0);
+          a1 = fmaf(-gl.y, fmaf(beta, ol.y, rl.y), a1);
+          a2 = fmaf(-gl.z, fmaf(beta, ol.z, rl.z), a2);
+          a3 = fmaf(-gl.w, fmaf(beta, ol.w, rl.w), a3);
+        }
+      }
+    }
+    st4(q + i0, make_float4(a0, a1, a2, a3));
+    ff_fma(pq, p4.x, a0);
+    ff_fma(pq, p4.y, a1);
+    ff_fma(pq, p4.z, a2);
+    ff_fma(pq, p4.w, a3);
+  }
+  spmv32_finish(pq, partials, S);
+}
+
 template <int G>
 __global__ void __launch_bounds__(kThreads)
 k_spmv32_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
@@ -536,7 +618,8 @@ k_spmv32_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restri
   spmv32_finish(pq, partials, S);
 }
 
-__device__ __forceinline__ void update32_finish(FF rr, double* partials, PcgState* S) {
+__device__ __forceinline__ void update32_finish(FF rr, double* partials, PcgState* S,
+                                                cudaGraphConditionalHandle h, int end_loop) {
   FF v[1] = {rr};
   double tot[1];
   if (grid_sum_ff<1>(v, partials, &S->counter[2], tot) && threadIdx.x == 0) {
@@ -553,15 +636,21 @@ __device__ __forceinline__ void update32_finish(FF rr, double* partials, PcgStat
       S->beta = 0.0;
     }
     S->stop_req = stop;
+    if (end_loop && stop) cudaGraphSetConditional(h, 0u);
   }
 }
 
 // r -= alpha q; ||r||^2 -> beta and the stop test.  vec selects the float4
-// loop (n~ % 4 == 0).
+// loop (n~ % 4 == 0).  end_loop: this kernel ends the WHILE loop when it
+// requests the stop (fused recurrence; otherwise k_update32_xp does).
 __global__ void __launch_bounds__(kThreads, PIRMCUT_INNER_MINB)
 k_update32_r(int64_t nt, int vec, const float* __restrict__ q, float* __restrict__ r,
-             double* partials, PcgState* S) {
-  if (S->stop_req) return;
+             double* partials, PcgState* S, cudaGraphConditionalHandle h, int end_loop) {
+  if (S->stop_req) {
+    // an earlier kernel of this loop body stopped the recurrence
+    if (end_loop && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+    return;
+  }
   const float alpha = float(S->alpha);
   FF rr{0.f, 0.f};
   if (vec) {
@@ -583,7 +672,7 @@ k_update32_r(int64_t nt, int vec, const float* __restrict__ q, float* __restrict
       ff_fma(rr, ri, ri);
     }
   }
-  update32_finish(rr, partials, S);
+  update32_finish(rr, partials, S, h, end_loop);
 }
 
 // d += alpha p; p = r + beta p.  Ends the inner loop once a stop was requested.
@@ -612,11 +701,21 @@ k_update32_xp(int64_t nt, int vec, float* __restrict__ d, float* __restrict__ p,
   if (use_cond && blockIdx.x == 0 && threadIdx.x == 0 && S->stop_req) cudaGraphSetConditional(h, 0u);
 }
 
-// x += D^-1/2 d^ (FP64), skipped once the refinement loop has stopped
+// x += D^-1/2 d^ (FP64), skipped once the refinement loop has stopped.  With
+// the fused recurrence the last iteration's d += alpha p is still pending:
+// p_last is pa after an even number of iterations, pb after an odd one.
 __global__ void __launch_bounds__(kThreads)
 k_xupdate(int64_t nt, double* __restrict__ x, const float* __restrict__ d,
-          const double* __restrict__ s64, const OuterState* O) {
+          const double* __restrict__ s64, const OuterState* O, const PcgState* S,
+          const float* __restrict__ pa, const float* __restrict__ pb, int fused) {
   if (O->outer_stop) return;
+  if (fused) {
+    const float alpha = float(S->alpha);
+    const float* __restrict__ p = (S->iters & 1) ? pb : pa;
+    for (int64_t i = gtid(); i < nt; i += gstride())
+      x[i] = fma(s64[i], double(fmaf(alpha, p[i], d[i])), x[i]);
+    return;
+  }
   for (int64_t i = gtid(); i < nt; i += gstride()) x[i] = fma(s64[i], double(d[i]), x[i]);
 }
 
@@ -705,17 +804,39 @@ int enqueue_spmv32(Ctx& c, cudaStream_t st) {
   return 1;
 }
 
+// One launch of the fused SpMV: p_old = (odd ? pb : pa), p_new the other.
+int enqueue_fused_spmv32(Ctx& c, cudaStream_t st, bool odd) {
+  const float* pold = odd ? c.p32b : c.p32;
+  float* pnew = odd ? c.p32 : c.p32b;
+  PIRMCUT_DISPATCH_K(c.K, (k_spmv32v_fused_dia<KK><<<c.fused_grid, kThreads, 0, st>>>(
+                              c.dd, c.g32, c.r32, pold, pnew, c.d32, c.q32, c.partials, c.S)));
+  return 1;
+}
+
+// The kernels of CG iterations.  Three-kernel recurrence: one iteration
+// (spmv, update_r, update_xp).  Fused recurrence (vectorised DIA): two
+// iterations (spmv_fused(pa -> pb), update_r, spmv_fused(pb -> pa), update_r),
+// so that the body of a graph loop leaves p in its starting buffer; a stop
+// requested by the first update_r turns the second pair into no-ops.
 int enqueue_inner_iteration(Ctx& c, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
-  enqueue_spmv32(c, st);
   const int vec = vector_rows(c) ? 1 : 0;
   const int g = vec ? grid_for(c.nt / 4) : grid_for(c.nt);
-  k_update32_r<<<g, kThreads, 0, st>>>(c.nt, vec, c.q32, c.r32, c.partials, c.S);
+  if (c.fused_inner) {
+    for (int half = 0; half < 2; ++half) {
+      enqueue_fused_spmv32(c, st, half == 1);
+      k_update32_r<<<g, kThreads, 0, st>>>(c.nt, vec, c.q32, c.r32, c.partials, c.S, h, use_cond);
+    }
+    return 4;
+  }
+  enqueue_spmv32(c, st);
+  k_update32_r<<<g, kThreads, 0, st>>>(c.nt, vec, c.q32, c.r32, c.partials, c.S, h, 0);
   k_update32_xp<<<g, kThreads, 0, st>>>(c.nt, vec, c.d32, c.p32, c.r32, c.S, h, use_cond);
   return 3;
 }
 
 int enqueue_xupdate(Ctx& c, cudaStream_t st) {
-  k_xupdate<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.x, c.d32, c.s64, c.O);
+  k_xupdate<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.x, c.d32, c.s64, c.O, c.S, c.p32, c.p32b,
+                                                 c.fused_inner ? 1 : 0);
   return 1;
 }
 
@@ -755,20 +876,37 @@ cudaError_t mixed_alloc(Ctx& c) {
   A((void**)&c.s32, sizeof(float) * nt);
   A((void**)&c.r32, sizeof(float) * nt);
   A((void**)&c.p32, sizeof(float) * nt);
+  c.fused_inner = PIRMCUT_FUSED_INNER && vector_dia(c);
+  if (c.fused_inner) A((void**)&c.p32b, sizeof(float) * nt);
   A((void**)&c.q32, sizeof(float) * nt);
   A((void**)&c.d32, sizeof(float) * nt);
   A((void**)&c.b64, sizeof(double) * nt);
   A((void**)&c.O, sizeof(OuterState));
   if (e == cudaSuccess) e = cudaMemset(c.O, 0, sizeof(OuterState));
+  if (e == cudaSuccess && c.fused_inner) {
+    // one wave of resident blocks (grid-stride loop over the rest)
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) {
+      PIRMCUT_DISPATCH_K(c.K, (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                   &per_sm, k_spmv32v_fused_dia<KK>, kThreads, 0)));
+    }
+    if (e == cudaSuccess) {
+      const int want = grid_for(c.nt / 4);
+      const int wave = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+      c.fused_grid = want < wave ? want : wave;
+    }
+  }
   if (e != cudaSuccess) mixed_free(c);
   return e;
 }
 
 void mixed_free(Ctx& c) {
-  void* ps[] = {c.g32, c.s64, c.s32, c.r32, c.p32, c.q32, c.d32, c.b64, c.O};
+  void* ps[] = {c.g32, c.s64, c.s32, c.r32, c.p32, c.p32b, c.q32, c.d32, c.b64, c.O};
   for (void* p : ps)
     if (p) cudaFree(p);
-  c.g32 = c.s32 = c.r32 = c.p32 = c.q32 = c.d32 = nullptr;
+  c.g32 = c.s32 = c.r32 = c.p32 = c.p32b = c.q32 = c.d32 = nullptr;
   c.s64 = c.b64 = nullptr;
   c.O = nullptr;
 }
@@ -835,7 +973,8 @@ cudaError_t build_step_graph_mixed(Ctx& c, bool initial, cudaGraphExec_t* out, i
 }
 
 cudaError_t launch_spmv32_once(Ctx& c) {
-  enqueue_spmv32(c, c.stream);
+  if (c.fused_inner) enqueue_fused_spmv32(c, c.stream, false);
+  else enqueue_spmv32(c, c.stream);
   c.launches += 1;
   return cudaGetLastError();
 }
