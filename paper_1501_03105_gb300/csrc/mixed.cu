@@ -46,10 +46,13 @@
 #ifndef PIRMCUT_FUSED_INNER
 #define PIRMCUT_FUSED_INNER 1
 #endif
-// Minimum resident blocks per SM for the fused SpMV (caps its registers).
+// Minimum resident blocks per SM for the fused SpMV (caps its registers at
+// 48); measured on grid2048: 3 -> 33.3 us, 4 -> 31.0, 5 -> 30.2-30.6, 6 -> 32.8
+// (spills), unbounded (84 registers) -> 40.8.
 #ifndef PIRMCUT_FUSED_MINB
-#define PIRMCUT_FUSED_MINB 4
+#define PIRMCUT_FUSED_MINB 5
 #endif
+
 
 namespace pirmcut {
 
