@@ -646,7 +646,7 @@ __device__ __forceinline__ void update32_finish(FF rr, double* partials, PcgStat
 // r -= alpha q; ||r||^2 -> beta and the stop test.  vec selects the float4
 // loop (n~ % 4 == 0).  end_loop: this kernel ends the WHILE loop when it
 // requests the stop (fused recurrence; otherwise k_update32_xp does).
-__global__ void __launch_bounds__(kThreads, PIRMCUT_INNER_MINB)
+__global__ void __launch_bounds__(kThreads, 8)
 k_update32_r(int64_t nt, int vec, const float* __restrict__ q, float* __restrict__ r,
              double* partials, PcgState* S, cudaGraphConditionalHandle h, int end_loop) {
   if (S->stop_req) {

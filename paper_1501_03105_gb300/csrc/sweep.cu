@@ -365,10 +365,27 @@ k_tile_argmin(int64_t nt, const uint32_t* __restrict__ order, const double* __re
     s_last = (atomicAdd(counter, 1u) == gridDim.x - 1) ? 1u : 0u;
   }
   __syncthreads();
-  if (!s_last || threadIdx.x != 0) return;
+  if (!s_last) return;
   __threadfence();
-  ArgMin all{cut0, 0};
-  for (unsigned int b = 0; b < gridDim.x; ++b) all = amin(all, ArgMin{__ldcg(bv + b), __ldcg(bk + b)});
+  // the last tile's block reduces the tile minima (amin is associative and
+  // breaks ties by k, so the result does not depend on the order)
+  ArgMin all{INFINITY, INT64_MAX};
+  if (threadIdx.x == 0) all = ArgMin{cut0, 0};
+  for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+    all = amin(all, ArgMin{__ldcg(bv + b), __ldcg(bk + b)});
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ArgMin other{__shfl_down_sync(0xffffffffu, all.v, o),
+                 (int64_t)__shfl_down_sync(0xffffffffu, (long long)all.k, o)};
+    all = amin(all, other);
+  }
+  if (lane == 0) {
+    sv[wid] = all.v;
+    sk[wid] = all.k;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) all = amin(all, ArgMin{sv[w], sk[w]});
   *counter = 0u;
   result[0] = all.v;
   result[3] = (double)all.k;
