@@ -91,12 +91,12 @@ pirmcut_status check_options(const pirmcut_options& o, std::string* msg) {
 
 // copy a caller buffer (host or device) into a host vector
 template <class T>
-cudaError_t to_host(std::vector<T>& dst, const T* src, size_t count, int mem_kind) {
+cudaError_t to_host(pirmcut::hvec<T>& dst, const T* src, size_t count, int mem_kind) {
   dst.resize(count);
   if (count == 0) return cudaSuccess;
   if (mem_kind == PIRMCUT_MEM_DEVICE)
     return cudaMemcpy(dst.data(), src, sizeof(T) * count, cudaMemcpyDeviceToHost);
-  std::memcpy(dst.data(), src, sizeof(T) * count);
+  pirmcut::parallel_copy(dst.data(), src, int64_t(count));
   return cudaSuccess;
 }
 
@@ -303,22 +303,28 @@ pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* 
   std::string msg;
   if (check_options(o, &msg) != PIRMCUT_OK) return fail(nullptr, PIRMCUT_EINVAL, msg);
 
-  std::vector<int64_t> rp;
-  std::vector<int32_t> cl;
-  std::vector<double> cv;
+  // the structure is kept (pirmcut_update_weights re-reduces it); host
+  // capacities are read in place, device ones through a host copy
+  pirmcut::hvec<int64_t> rp;
+  pirmcut::hvec<int32_t> cl;
+  pirmcut::hvec<double> cv;
   cudaError_t e = to_host(rp, row_ptr, size_t(n) + 1, mem_kind);
   if (e != cudaSuccess) return fail(nullptr, PIRMCUT_ECUDA, std::string("reading row_ptr: ") + cudaGetErrorString(e));
   const int64_t nnz = rp[n];
   if (nnz < 0 || rp[0] != 0) return fail(nullptr, PIRMCUT_EINVAL, "bad row_ptr");
   if (nnz > 0 && (!col || !c)) return fail(nullptr, PIRMCUT_EINVAL, "col and c must not be NULL");
   e = to_host(cl, col, size_t(nnz), mem_kind);
-  if (e == cudaSuccess) e = to_host(cv, c, size_t(nnz), mem_kind);
+  const double* cin = c;
+  if (e == cudaSuccess && mem_kind == PIRMCUT_MEM_DEVICE) {
+    e = to_host(cv, c, size_t(nnz), mem_kind);
+    cin = cv.data();
+  }
   if (e != cudaSuccess) return fail(nullptr, PIRMCUT_ECUDA, std::string("reading the graph: ") + cudaGetErrorString(e));
 
   pirmcut_ctx* h = new (std::nothrow) pirmcut_ctx();
   if (!h) return fail(nullptr, PIRMCUT_ENOMEM, "out of host memory");
   Ctx& cx = h->c;
-  pirmcut_status ps = pirmcut::reduce_graph(n, rp.data(), cl.data(), cv.data(), s, t, o.format, &cx.hg, &msg);
+  pirmcut_status ps = pirmcut::reduce_graph(n, rp.data(), cl.data(), cin, s, t, o.format, &cx.hg, &msg);
   if (ps != PIRMCUT_OK) {
     delete h;
     return fail(nullptr, ps, msg);
@@ -500,11 +506,15 @@ pirmcut_status pirmcut_update_weights(pirmcut_ctx* h, const double* cnew, int me
     return fail(h, PIRMCUT_EINVAL, "unknown mem_kind");
   const int64_t nnz = c.in_rp.back();
   if (nnz > 0 && !cnew) return fail(h, PIRMCUT_EINVAL, "c must not be NULL");
-  std::vector<double> cv;
-  CK(h, to_host(cv, cnew, size_t(nnz), mem_kind), "reading c");
+  pirmcut::hvec<double> cv;
+  const double* cin = cnew;
+  if (mem_kind == PIRMCUT_MEM_DEVICE) {
+    CK(h, to_host(cv, cnew, size_t(nnz), mem_kind), "reading c");
+    cin = cv.data();
+  }
   pirmcut::HostGraph ng;
   std::string msg;
-  pirmcut_status ps = pirmcut::reduce_graph(c.hg.n, c.in_rp.data(), c.in_col.data(), cv.data(),
+  pirmcut_status ps = pirmcut::reduce_graph(c.hg.n, c.in_rp.data(), c.in_col.data(), cin,
                                             c.hg.s, c.hg.t, c.format, &ng, &msg);
   if (ps != PIRMCUT_OK) return fail(h, ps, msg);
   bool same = ng.format == c.format && ng.nt == c.nt && ng.K == c.K;

@@ -102,8 +102,8 @@ struct MlpBuf {
 struct Ctx {
   // problem
   HostGraph hg;               // reduced problem (host copy kept for update_weights)
-  std::vector<int64_t> in_rp; // original CSR structure (for update_weights)
-  std::vector<int32_t> in_col;
+  hvec<int64_t> in_rp;        // original CSR structure (for update_weights)
+  hvec<int32_t> in_col;
   int64_t nt = 0;
   int format = PIRMCUT_FORMAT_CSR;
   int K = 0;

@@ -21,22 +21,26 @@ struct Entry {
   double c;
 };
 
-// Run fn(lo, hi) over [0, n) split across the host's cores.
-template <class F>
-void parallel_for(int64_t n, F fn) {
-  unsigned hw = std::thread::hardware_concurrency();
-  int64_t nth = std::max<int64_t>(1, std::min<int64_t>(hw ? hw : 1, 64));
-  if (n < 65536) nth = 1;
-  std::vector<std::thread> th;
-  for (int64_t k = 0; k < nth; ++k) {
-    int64_t lo = n * k / nth, hi = n * (k + 1) / nth;
-    if (k + 1 == nth) {
-      fn(lo, hi);
-    } else {
-      th.emplace_back([=] { fn(lo, hi); });
+
+// Stable sort of a row's entries by column: insertion sort for the short rows
+// of meshes and sparse graphs (no allocation), std::stable_sort otherwise.
+void sort_row(std::vector<Entry>& buf) {
+  bool sorted = true;
+  for (size_t k = 1; k < buf.size() && sorted; ++k) sorted = buf[k - 1].col <= buf[k].col;
+  if (sorted) return;
+  if (buf.size() <= 32) {
+    for (size_t k = 1; k < buf.size(); ++k) {
+      const Entry e = buf[k];
+      size_t j = k;
+      while (j > 0 && buf[j - 1].col > e.col) {
+        buf[j] = buf[j - 1];
+        --j;
+      }
+      buf[j] = e;
     }
+    return;
   }
-  for (auto& x : th) x.join();
+  std::stable_sort(buf.begin(), buf.end(), [](const Entry& a, const Entry& b) { return a.col < b.col; });
 }
 
 }  // namespace
@@ -77,15 +81,19 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
 
   // ---- per-row pass: validate entries, fold terminal edges, merge parallel
   // entries of the non-terminal rows (sorted by reduced column).
-  std::vector<int64_t> cnt(nt + 1, 0);
-  std::vector<double> cs(nt, 0.0), ct(nt, 0.0), cs_from_s(nt, 0.0), ct_from_t(nt, 0.0);
+  hvec<int64_t> cnt(nt + 1);
+  hvec<double> cs(nt), ct(nt), cs_from_s(nt), ct_from_t(nt);
+  cnt[0] = 0;
+  parallel_fill(cs_from_s.data(), nt, 0.0);
+  parallel_fill(ct_from_t.data(), nt, 0.0);
   double cst_s = 0.0, cst_t = 0.0;
   // pass 1 (parallel): count merged non-terminal entries per row, validate
-  std::vector<uint8_t> row_bad(n, 0);
+  hvec<uint8_t> row_bad(n);
   parallel_for(n, [&](int64_t lo, int64_t hi) {
     std::vector<Entry> buf;
     for (int64_t v = lo; v < hi; ++v) {
       const int64_t b = row_ptr[v], e = row_ptr[v + 1];
+      row_bad[v] = 0;
       for (int64_t k = b; k < e; ++k) {
         const int32_t u = col[k];
         const double w = c[k];
@@ -100,11 +108,7 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
         if (u == s || u == t) continue;
         buf.push_back({(int32_t)reduced_index(u, s, t), c[k]});
       }
-      bool sorted = true;
-      for (size_t k = 1; k < buf.size(); ++k) sorted &= buf[k - 1].col <= buf[k].col;
-      if (!sorted)
-        std::stable_sort(buf.begin(), buf.end(),
-                         [](const Entry& a, const Entry& b2) { return a.col < b2.col; });
+      sort_row(buf);
       int64_t m = 0;
       for (size_t k = 0; k < buf.size(); ++k)
         if (k == 0 || buf[k].col != buf[k - 1].col) ++m;
@@ -116,11 +120,12 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
     if (row_bad[v] == 2) { *err = "self-loop at vertex " + std::to_string(v); return PIRMCUT_EINVAL; }
     if (row_bad[v] == 3) { *err = "capacity not finite or negative in row " + std::to_string(v); return PIRMCUT_EINVAL; }
   }
-  std::vector<int64_t> rp(nt + 1, 0);
+  hvec<int64_t> rp(nt + 1);
+  rp[0] = 0;
   for (int64_t i = 0; i < nt; ++i) rp[i + 1] = rp[i] + cnt[i + 1];
   const int64_t mnt = rp[nt];
-  std::vector<int32_t> rc(mnt);
-  std::vector<double> rv(mnt);
+  hvec<int32_t> rc(mnt);
+  hvec<double> rv(mnt);
   // pass 2 (parallel): fill merged rows and the terminal capacities
   parallel_for(n, [&](int64_t lo, int64_t hi) {
     std::vector<Entry> buf;
@@ -137,8 +142,7 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
       }
       cs[i] = a;
       ct[i] = z;
-      std::stable_sort(buf.begin(), buf.end(),
-                       [](const Entry& x, const Entry& y) { return x.col < y.col; });
+      sort_row(buf);
       int64_t o = rp[i];
       for (size_t k = 0; k < buf.size(); ++k) {
         if (k > 0 && buf[k].col == buf[k - 1].col) {
@@ -167,16 +171,21 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
     *err = "CSR is not symmetric (s-t edge)";
     return PIRMCUT_EINVAL;
   }
+  hvec<uint8_t> asym(nt);
+  parallel_for(nt, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i)
+      asym[i] = (cs[i] != cs_from_s[i] || ct[i] != ct_from_t[i]) ? 1 : 0;
+  });
   for (int64_t i = 0; i < nt; ++i) {
-    if (cs[i] != cs_from_s[i] || ct[i] != ct_from_t[i]) {
+    if (asym[i]) {
       *err = "CSR is not symmetric (terminal edge of vertex " +
              std::to_string(original_index(i, s, t)) + ")";
       return PIRMCUT_EINVAL;
     }
   }
-  std::vector<uint8_t> asym(nt, 0);
   parallel_for(nt, [&](int64_t lo, int64_t hi) {
     for (int64_t i = lo; i < hi; ++i) {
+      asym[i] = 0;
       for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
         const int64_t j = rc[k];
         const int32_t* b = rc.data() + rp[j];
@@ -198,15 +207,27 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
   // ---- solvability (Prop. nonsingular): every non-terminal reaches a vertex
   // with a positive terminal capacity through positive-capacity edges.
   {
-    std::vector<uint8_t> seen(nt, 0);
-    std::vector<int64_t> stack;
-    stack.reserve(1024);
-    for (int64_t i = 0; i < nt; ++i) {
-      if (cs[i] > 0.0 || ct[i] > 0.0) {
-        seen[i] = 1;
-        stack.push_back(i);
+    hvec<uint8_t> seen(nt);
+    parallel_for(nt, [&](int64_t lo, int64_t hi) {
+      for (int64_t i = lo; i < hi; ++i) seen[i] = (cs[i] > 0.0 || ct[i] > 0.0) ? 1 : 0;
+    });
+    // a depth-first search from the seeds that have an unseen neighbour
+    // (on meshes where every vertex has a terminal edge there is none)
+    hvec<uint8_t> frontier(nt);
+    parallel_for(nt, [&](int64_t lo, int64_t hi) {
+      for (int64_t i = lo; i < hi; ++i) {
+        frontier[i] = 0;
+        if (!seen[i]) continue;
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+          if (!seen[rc[k]] && rv[k] > 0.0) {
+            frontier[i] = 1;
+            break;
+          }
       }
-    }
+    });
+    std::vector<int64_t> stack;
+    for (int64_t i = 0; i < nt; ++i)
+      if (frontier[i]) stack.push_back(i);
     while (!stack.empty()) {
       const int64_t i = stack.back();
       stack.pop_back();
@@ -239,18 +260,36 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
   int K = 0;
   int64_t offs[kMaxDiag + 1];
   bool dia_ok = true;
-  for (int64_t i = 0; i < nt && dia_ok; ++i) {
-    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
-      const int64_t o = int64_t(rc[k]) - i;
-      if (o <= 0) continue;
-      int f = 0;
-      while (f < K && offs[f] != o) ++f;
-      if (f == K) {
-        if (K == kMaxDiag) {
-          dia_ok = false;
-          break;
+  {
+    // each chunk collects up to kMaxDiag + 1 distinct positive offsets
+    constexpr int kChunks = 64;
+    int64_t chunk_offs[kChunks][kMaxDiag + 1];
+    int chunk_k[kChunks] = {0};
+    parallel_for(kChunks, [&](int64_t lo, int64_t hi) {
+      for (int64_t ch = lo; ch < hi; ++ch) {
+        int kk = 0;
+        const int64_t r0 = nt * ch / kChunks, r1 = nt * (ch + 1) / kChunks;
+        for (int64_t i = r0; i < r1 && kk <= kMaxDiag; ++i) {
+          for (int64_t k = rp[i]; k < rp[i + 1] && kk <= kMaxDiag; ++k) {
+            const int64_t o = int64_t(rc[k]) - i;
+            if (o <= 0) continue;
+            int f = 0;
+            while (f < kk && chunk_offs[ch][f] != o) ++f;
+            if (f == kk) chunk_offs[ch][kk++] = o;
+          }
         }
-        offs[K++] = o;
+        chunk_k[ch] = kk;
+      }
+    }, /*min_per_thread=*/1);
+    for (int ch = 0; ch < kChunks && dia_ok; ++ch) {
+      for (int j = 0; j < chunk_k[ch] && dia_ok; ++j) {
+        const int64_t o = chunk_offs[ch][j];
+        int f = 0;
+        while (f < K && offs[f] != o) ++f;
+        if (f == K) {
+          if (K == kMaxDiag) dia_ok = false;
+          else offs[K++] = o;
+        }
       }
     }
   }
@@ -270,7 +309,8 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
     g.format = PIRMCUT_FORMAT_DIA;
     g.K = K;
     for (int k = 0; k < K; ++k) g.off[k] = offs[k];
-    g.cdia.assign(size_t(K) * nt, 0.0);
+    g.cdia.resize(size_t(K) * nt);
+    parallel_fill(g.cdia.data(), int64_t(K) * nt, 0.0);
     parallel_for(nt, [&](int64_t lo, int64_t hi) {
       for (int64_t i = lo; i < hi; ++i) {
         for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {

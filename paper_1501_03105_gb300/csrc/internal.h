@@ -1,8 +1,11 @@
 // Internal declarations shared by the translation units of libpirmcut.
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
+#include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "pirmcut.h"
@@ -10,6 +13,58 @@
 namespace pirmcut {
 
 constexpr int kMaxDiag = 8;  // most upper diagonals the DIA storage accepts
+
+// Allocator whose value-less construction leaves the element uninitialised,
+// so that large host buffers are not zero-filled by one thread before a
+// parallel pass writes every element anyway.
+template <class T>
+struct NoInitAllocator : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = NoInitAllocator<U>;
+  };
+  NoInitAllocator() = default;
+  template <class U>
+  NoInitAllocator(const NoInitAllocator<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <class U, class... A>
+  void construct(U* p, A&&... a) {
+    ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+  }
+};
+template <class T>
+using hvec = std::vector<T, NoInitAllocator<T>>;
+
+// Run fn(lo, hi) over [0, n) split across the host's cores (at least
+// min_per_thread items per thread).
+template <class F>
+void parallel_for(int64_t n, F fn, int64_t min_per_thread = 32768) {
+  const unsigned hw = std::thread::hardware_concurrency();
+  int64_t nth = std::max<int64_t>(1, std::min<int64_t>(hw ? hw : 1, 64));
+  nth = std::min<int64_t>(nth, std::max<int64_t>(1, n / min_per_thread));
+  std::vector<std::thread> th;
+  for (int64_t k = 0; k < nth; ++k) {
+    const int64_t lo = n * k / nth, hi = n * (k + 1) / nth;
+    if (k + 1 == nth) fn(lo, hi);
+    else th.emplace_back([=] { fn(lo, hi); });
+  }
+  for (auto& x : th) x.join();
+}
+
+// dst[0, n) = v in parallel
+template <class T>
+void parallel_fill(T* dst, int64_t n, T v) {
+  parallel_for(n, [=](int64_t lo, int64_t hi) { std::fill(dst + lo, dst + hi, v); }, 1 << 20);
+}
+
+// dst[0, n) = src[0, n) in parallel
+template <class T>
+void parallel_copy(T* dst, const T* src, int64_t n) {
+  parallel_for(n, [=](int64_t lo, int64_t hi) { std::copy(src + lo, src + hi, dst + lo); }, 1 << 20);
+}
 
 // The reduced problem built once per instance on the host: the non-terminal
 // graph G~ (Section 2), the terminal capacities folded per vertex, and the
@@ -23,14 +78,14 @@ struct HostGraph {
   // DIA: capacity of edge (i, i + off[k]) at cdia[k * nt + i]; 0 where absent.
   int K = 0;
   int64_t off[kMaxDiag] = {0};
-  std::vector<double> cdia;
+  hvec<double> cdia;
   // CSR of G~ (both directions stored, rows sorted, parallel entries merged).
-  std::vector<int64_t> rp;
-  std::vector<int32_t> col;
-  std::vector<double> cval;
+  hvec<int64_t> rp;
+  hvec<int32_t> col;
+  hvec<double> cval;
   int group = 1;        // threads per row for the CSR kernels
   // Terminal capacities c(s, v), c(v, t) per non-terminal and c(s, t).
-  std::vector<double> cs, ct;
+  hvec<double> cs, ct;
   double c_st = 0.0;
   double sum_cs = 0.0;  // sum_v c(s, v) + c(s, t): the cut value of S = {s}
 };
