@@ -87,21 +87,35 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
   parallel_fill(cs_from_s.data(), nt, 0.0);
   parallel_fill(ct_from_t.data(), nt, 0.0);
   double cst_s = 0.0, cst_t = 0.0;
-  // pass 1 (parallel): count merged non-terminal entries per row, validate
+  // pass 1 (parallel): validate, count merged non-terminal entries per row.
+  // row_bad: 0 = valid and its non-terminal columns strictly increase (copied
+  // as they are), 4 = valid but unsorted or with parallel entries (sorted and
+  // merged), 1-3 = an error.
   hvec<uint8_t> row_bad(n);
   parallel_for(n, [&](int64_t lo, int64_t hi) {
     std::vector<Entry> buf;
     for (int64_t v = lo; v < hi; ++v) {
       const int64_t b = row_ptr[v], e = row_ptr[v + 1];
-      row_bad[v] = 0;
+      uint8_t code = 0;
+      int64_t m = 0, prev = -1;
       for (int64_t k = b; k < e; ++k) {
         const int32_t u = col[k];
         const double w = c[k];
-        if (u < 0 || u >= n) { row_bad[v] = 1; break; }
-        if (u == v) { row_bad[v] = 2; break; }
-        if (!std::isfinite(w) || w < 0.0) { row_bad[v] = 3; break; }
+        if (u < 0 || u >= n) { code = 1; break; }
+        if (u == v) { code = 2; break; }
+        if (!std::isfinite(w) || w < 0.0) { code = 3; break; }
+        if (u == s || u == t) continue;
+        const int64_t r = reduced_index(u, s, t);
+        if (r <= prev) code = 4;
+        prev = r;
+        ++m;
       }
-      if (row_bad[v] || v == s || v == t) continue;
+      row_bad[v] = code;
+      if ((code != 0 && code != 4) || v == s || v == t) continue;
+      if (code == 0) {
+        cnt[reduced_index(v, s, t) + 1] = m;
+        continue;
+      }
       buf.clear();
       for (int64_t k = b; k < e; ++k) {
         const int32_t u = col[k];
@@ -109,10 +123,10 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
         buf.push_back({(int32_t)reduced_index(u, s, t), c[k]});
       }
       sort_row(buf);
-      int64_t m = 0;
+      int64_t merged = 0;
       for (size_t k = 0; k < buf.size(); ++k)
-        if (k == 0 || buf[k].col != buf[k - 1].col) ++m;
-      cnt[reduced_index(v, s, t) + 1] = m;
+        if (k == 0 || buf[k].col != buf[k - 1].col) ++merged;
+      cnt[reduced_index(v, s, t) + 1] = merged;
     }
   });
   for (int64_t v = 0; v < n; ++v) {
@@ -132,8 +146,24 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
     for (int64_t v = lo; v < hi; ++v) {
       if (v == s || v == t) continue;
       const int64_t i = reduced_index(v, s, t);
-      buf.clear();
       double a = 0.0, z = 0.0;
+      if (row_bad[v] == 0) {
+        int64_t o = rp[i];
+        for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+          const int32_t u = col[k];
+          if (u == s) a += c[k];
+          else if (u == t) z += c[k];
+          else {
+            rc[o] = (int32_t)reduced_index(u, s, t);
+            rv[o] = c[k];
+            ++o;
+          }
+        }
+        cs[i] = a;
+        ct[i] = z;
+        continue;
+      }
+      buf.clear();
       for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
         const int32_t u = col[k];
         if (u == s) a += c[k];
@@ -155,17 +185,40 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
       }
     }
   });
-  // terminal rows
-  for (int64_t k = row_ptr[s]; k < row_ptr[s + 1]; ++k) {
-    const int32_t u = col[k];
-    if (u == t) cst_s += c[k];
-    else cs_from_s[reduced_index(u, s, t)] += c[k];
-  }
-  for (int64_t k = row_ptr[t]; k < row_ptr[t + 1]; ++k) {
-    const int32_t u = col[k];
-    if (u == s) cst_t += c[k];
-    else ct_from_t[reduced_index(u, s, t)] += c[k];
-  }
+  // terminal rows: c(s, v) and c(v, t) as seen from s and t.  A row whose
+  // columns strictly increase has no parallel entries: filled in parallel;
+  // otherwise the entries are summed in row order.
+  auto fold_terminal_row = [&](int32_t term, int32_t other, hvec<double>& dst, double& c_other) {
+    const int64_t b = row_ptr[term], e = row_ptr[term + 1];
+    constexpr int kChunks = 64;
+    uint8_t chunk_ok[kChunks];
+    parallel_for(kChunks, [&](int64_t lo, int64_t hi) {
+      for (int64_t ch = lo; ch < hi; ++ch) {
+        const int64_t k0 = b + (e - b) * ch / kChunks, k1 = b + (e - b) * (ch + 1) / kChunks;
+        uint8_t ok = 1;
+        for (int64_t k = (k0 > b ? k0 : b + 1); k < k1 && ok; ++k) ok = col[k - 1] < col[k];
+        chunk_ok[ch] = ok;
+      }
+    }, 1);
+    bool strict = true;
+    for (int ch = 0; ch < kChunks; ++ch) strict = strict && chunk_ok[ch];
+    if (strict) {
+      parallel_for(e - b, [&](int64_t lo, int64_t hi) {
+        for (int64_t k = b + lo; k < b + hi; ++k)
+          if (col[k] != other) dst[reduced_index(col[k], s, t)] = c[k];
+      });
+      for (int64_t k = b; k < e; ++k)
+        if (col[k] == other) c_other += c[k];
+      return;
+    }
+    for (int64_t k = b; k < e; ++k) {
+      const int32_t u = col[k];
+      if (u == other) c_other += c[k];
+      else dst[reduced_index(u, s, t)] += c[k];
+    }
+  };
+  fold_terminal_row(s, t, cs_from_s, cst_s);
+  fold_terminal_row(t, s, ct_from_t, cst_t);
   // ---- symmetry: every pair carries the same total capacity in both rows
   if (cst_s != cst_t) {
     *err = "CSR is not symmetric (s-t edge)";

@@ -200,6 +200,37 @@ def test_terminals_anywhere_and_duplicates(P):
     check_cut(prob, xs[-1], side, value, tau)
 
 
+def test_host_reduction_paths_give_identical_solves(P):
+    """The input reduction on a grid large enough to run in parallel: rows that
+    are already sorted (copied as they are) and rows with split, reversed
+    entries (sorted and merged), a terminal row in order and one reversed --
+    the same reduced problem, so bit-identical solves."""
+    g = gen.config_graph(1, scale=512)
+    rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    new_rp, new_col, new_c = [0], [], []
+    for r in range(g.n):
+        a, b = g.row_ptr[r], g.row_ptr[r + 1]
+        cols, caps = g.col[a:b], g.c[a:b]
+        if r % 3 == 0 or r == g.s:
+            # c/2 + c/2 is exact: the merged capacity equals the original
+            cols = np.repeat(cols, 2)[::-1]
+            caps = np.repeat(caps / 2, 2)[::-1]
+        new_col.append(cols)
+        new_c.append(caps)
+        new_rp.append(new_rp[-1] + len(cols))
+    gd = gen.Graph(g.n, np.array(new_rp, dtype=np.int64), np.concatenate(new_col).astype(np.int32),
+                   np.concatenate(new_c), g.s, g.t)
+    eps = O.eps_schedule(3)
+    out = []
+    for gg in (g, gd):
+        with solver(P, gg) as s:
+            s.solve(3, eps)
+            out.append((s.get_x(), s.cut()[1], s.problem_size()))
+    assert out[0][2] == out[1][2]
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+
+
 def test_one_vertex_and_no_source_edges(P):
     """n = 3 (s-v-t) closed form; and b = 0 (no s edges) gives x = 0."""
     rp, col, c = gen.csr_from_edges(3, [0, 1], [1, 2], [3.0, 1.0])
