@@ -318,8 +318,8 @@ def permute_graph(g: Graph, perm: np.ndarray) -> Graph:
 CONFIGS = {
     1: "grid64: 64x64 4-connected segmentation grid, one disk, T=50",
     2: "grid2048: 2048x2048 4-connected segmentation grid, 12 disks, T=50",
-    3: "vol256: 256^3 6-connected segmentation volume, ellipsoid, T=30",
-    5: "vol128: 128^3 6-connected segmentation volume (sequence base), T=30",
+    3: "vol256: 256^3 6-connected segmentation volume, ellipsoid, float32 capacities, T=30",
+    5: "vol128: 128^3 6-connected segmentation volume (sequence base), float32 capacities, T=30",
 }
 
 
@@ -341,8 +341,11 @@ def config_graph(k: int, scale: int | None = None) -> Graph:
         I = _noisy(I, rng, 0.05)
         return segmentation_grid(I, name=f"grid{W}")
     if k in (3, 5):
+        # capacities stored as float32 values (widened back to float64)
         W = scale or (256 if k == 3 else 128)
         f = W / 256.0
         I = image_ellipsoid_3d(W, W, W, (96 * f, 80 * f, 64 * f), seed=k)
-        return segmentation_grid(I, name=f"vol{W}")
+        g = segmentation_grid(I, name=f"vol{W}")
+        g.c = g.c.astype(np.float32).astype(np.float64)
+        return g
     raise ValueError(f"unknown workload {k}")

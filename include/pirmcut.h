@@ -214,8 +214,10 @@ int64_t pirmcut_kernel_launches(const pirmcut_ctx* ctx);
  * the FP32 inner one, which on DIA grids whose width is a multiple of 4 also
  * forms the new search direction and applies the previous d update) on the
  * current matrix and search direction, `reps` launches bracketed one by one
- * with CUDA events on the context's stream.  Needs a completed step (EINVAL
- * otherwise); leaves x untouched (the FP32 scratch vectors are overwritten).  avg_ms receives the mean launch time; bytes and flops
+ * with CUDA events on the context's stream, each after a 256 MB write that
+ * evicts L2 (outside the timed interval; the buffer is allocated for the call).
+ * Needs a completed step (EINVAL otherwise); leaves x untouched (the FP32
+ * scratch vectors are overwritten).  avg_ms receives the mean launch time; bytes and flops
  * (either may be NULL) the algorithmic bytes moved and floating-point
  * operations of one launch (every stored value, matrix index and vector entry
  * read or written once; an FMA counts 2).

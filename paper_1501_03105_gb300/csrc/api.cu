@@ -582,8 +582,19 @@ pirmcut_status pirmcut_time_spmv(pirmcut_ctx* h, int reps, double* avg_ms, doubl
   if (!a || !b) return fail(h, PIRMCUT_ECUDA, "cudaEventCreate failed");
   const bool m = c.opt.precision == PIRMCUT_PREC_MIXED;
   CK(h, m ? pirmcut::launch_spmv32_once(c) : pirmcut::launch_spmv_once(c), "spmv");  // warm-up
+  // every timed launch starts from a cold L2: a 256 MB buffer (about twice
+  // the L2) is written between launches, outside the timed interval
+  const size_t flush_bytes = size_t(256) << 20;
+  struct DeviceBuffer {
+    void* p = nullptr;
+    ~DeviceBuffer() {
+      if (p) cudaFree(p);
+    }
+  } flush;
+  CK(h, cudaMalloc(&flush.p, flush_bytes), "L2 flush buffer");
   double total = 0.0;
   for (int k = 0; k < reps; ++k) {
+    CK(h, cudaMemsetAsync(flush.p, k & 0xff, flush_bytes, c.stream), "L2 flush");
     CK(h, cudaEventRecord(a, c.stream), "event");
     CK(h, m ? pirmcut::launch_spmv32_once(c) : pirmcut::launch_spmv_once(c), "spmv");
     CK(h, cudaEventRecord(b, c.stream), "event");
