@@ -90,6 +90,9 @@ typedef struct {
                           into conditional graph nodes)                       */
   double inner_tol;    /* MIXED only: each FP32 inner solve reduces its residual
                           by this factor (or just enough for the FP64 test)   */
+  int time_spmv;       /* 1 (with graph_launch 0): bracket every PCG
+                          matrix-vector launch with CUDA events on the
+                          context's stream; pirmcut_spmv_timing reports them  */
 } pirmcut_options;
 
 typedef struct {
@@ -107,7 +110,7 @@ typedef struct {
 
 /* Fill *opt with the defaults: NORTH_STAR, FP64, pcg_tol 1e-10,
  * pcg_max_iter 20000, warm_start 1, FORMAT_AUTO, track_cut 0, graph_launch 1,
- * inner_tol 1e-5.  With MIXED, pcg_iters counts FP32 inner iterations, at most
+ * inner_tol 1e-5, time_spmv 0.  With MIXED, pcg_iters counts FP32 inner iterations, at most
  * min(pcg_max_iter, 2000) per refinement cycle and 64 cycles per system. */
 void pirmcut_default_options(pirmcut_options* opt);
 
@@ -224,6 +227,16 @@ int64_t pirmcut_kernel_launches(const pirmcut_ctx* ctx);
  */
 pirmcut_status pirmcut_time_spmv(pirmcut_ctx* ctx, int reps, double* avg_ms, double* bytes,
                                  double* flops);
+
+/*
+ * The matrix-vector launches timed during solves run with time_spmv = 1 and
+ * graph_launch = 0: their summed CUDA-event time in milliseconds and their
+ * count, since creation or the last reset (reset != 0 clears the totals after
+ * reading).  Launches that found the stop test already met (and skipped their
+ * work) are not counted; the algorithmic bytes of one launch are those that
+ * pirmcut_time_spmv reports.  Errors: EINVAL (NULL ctx).
+ */
+pirmcut_status pirmcut_spmv_timing(pirmcut_ctx* ctx, double* total_ms, int64_t* launches, int reset);
 
 /*
  * Two-level rounding (Section 3.3) of the current x: 1-D K-means on x with

@@ -37,6 +37,7 @@ from .binding import (  # noqa: F401
     pirmcut_mlp_features,
     MlpInfo,
     pirmcut_time_spmv,
+    pirmcut_spmv_timing,
     pirmcut_last_error,
     pirmcut_destroy,
 )

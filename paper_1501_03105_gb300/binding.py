@@ -34,7 +34,7 @@ class Options(ctypes.Structure):
                 ("pcg_tol", ctypes.c_double), ("pcg_max_iter", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("format", ctypes.c_int),
                 ("track_cut", ctypes.c_int), ("graph_launch", ctypes.c_int),
-                ("inner_tol", ctypes.c_double)]
+                ("inner_tol", ctypes.c_double), ("time_spmv", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):
@@ -136,6 +136,8 @@ def lib() -> ctypes.CDLL:
     L.pirmcut_mlp_stats.restype = ctypes.c_int
     L.pirmcut_mlp_features.argtypes = [_P, _P]
     L.pirmcut_mlp_features.restype = ctypes.c_int
+    L.pirmcut_spmv_timing.argtypes = [_P, ctypes.POINTER(dbl), ctypes.POINTER(i64), ctypes.c_int]
+    L.pirmcut_spmv_timing.restype = ctypes.c_int
     L.pirmcut_kernel_launches.argtypes = [_P]
     L.pirmcut_kernel_launches.restype = i64
     L.pirmcut_last_error.argtypes = [_P]
@@ -357,6 +359,14 @@ def pirmcut_mlp_features(h, nt: int):
     return out
 
 
+def pirmcut_spmv_timing(h, reset: bool = True):
+    """(total ms, launches) of the SpMV launches timed live (time_spmv=1,
+    graph_launch=0) since creation or the last reset."""
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(h, lib().pirmcut_spmv_timing(h, ctypes.byref(ms), ctypes.byref(n), int(bool(reset))))
+    return ms.value, n.value
+
+
 def pirmcut_kernel_launches(h) -> int:
     return int(lib().pirmcut_kernel_launches(h))
 
@@ -522,6 +532,9 @@ class Solver:
 
     def time_spmv(self, reps=20):
         return pirmcut_time_spmv(self.h, reps)
+
+    def spmv_timing(self, reset=True):
+        return pirmcut_spmv_timing(self.h, reset)
 
     def kernel_launches(self):
         return pirmcut_kernel_launches(self.h)

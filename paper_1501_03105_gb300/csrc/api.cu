@@ -54,6 +54,8 @@ void free_device(Ctx& c) {
   if (c.g_step) cudaGraphExecDestroy(c.g_step);
   if (c.g_cut) cudaGraphExecDestroy(c.g_cut);
   if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
+  for (cudaEvent_t ev : c.spmv_ev) cudaEventDestroy(ev);
+  c.spmv_ev.clear();
   if (c.h_recs) cudaFreeHost(c.h_recs);
 }
 
@@ -270,6 +272,26 @@ pirmcut_status run_steps(pirmcut_ctx* h, bool with_initial, int T, int first_ste
 
 namespace pirmcut {
 void set_global_error(const std::string& msg) { g_create_error = msg; }
+
+cudaEvent_t* spmv_events(Ctx& c, int pairs) {
+  while (c.spmv_ev.size() < size_t(2 * pairs)) {
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+    c.spmv_ev.push_back(ev);
+  }
+  return c.spmv_ev.data();
+}
+
+void spmv_events_collect(Ctx& c, int pairs, int executed) {
+  if (executed > pairs) executed = pairs;
+  for (int j = 0; j < executed; ++j) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c.spmv_ev[2 * j], c.spmv_ev[2 * j + 1]) == cudaSuccess) {
+      c.spmv_ms += ms;
+      c.spmv_count += 1;
+    }
+  }
+}
 }  // namespace pirmcut
 
 extern "C" {
@@ -285,6 +307,7 @@ void pirmcut_default_options(pirmcut_options* opt) {
   opt->track_cut = 0;
   opt->graph_launch = 1;
   opt->inner_tol = 1e-5;
+  opt->time_spmv = 0;
 }
 
 pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* col,
@@ -370,7 +393,7 @@ pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* 
   if (o.precision == PIRMCUT_PREC_MIXED && (e = pirmcut::mixed_alloc(cx)) != cudaSuccess)
     return bail(e, "cudaMalloc");
   if ((e = cudaMemset(cx.C, 0, sizeof(pirmcut::StepCounters))) != cudaSuccess) return bail(e, "cudaMemset");
-  if ((e = cudaHostAlloc((void**)&h->h_ctr, sizeof(pirmcut::StepCounters) + 8 * sizeof(double),
+  if ((e = cudaHostAlloc((void**)&h->h_ctr, sizeof(pirmcut::StepCounters) + 10 * sizeof(double),
                          cudaHostAllocDefault)) != cudaSuccess)
     return bail(e, "cudaHostAlloc");
   h->h_eps = reinterpret_cast<double*>(h->h_ctr + 1);
@@ -711,6 +734,17 @@ pirmcut_status pirmcut_mlp_features(pirmcut_ctx* h, float* f) {
   if (!f) return fail(h, PIRMCUT_EINVAL, "null feature buffer");
   if (!c.mlp.master) return fail(h, PIRMCUT_EINVAL, "no model: call pirmcut_mlp_enable first");
   CK(h, pirmcut::mlp_get_features(c, f), "reading the features");
+  return PIRMCUT_OK;
+}
+
+pirmcut_status pirmcut_spmv_timing(pirmcut_ctx* h, double* total_ms, int64_t* launches, int reset) {
+  if (!h) return fail(nullptr, PIRMCUT_EINVAL, "null context");
+  if (total_ms) *total_ms = h->c.spmv_ms;
+  if (launches) *launches = h->c.spmv_count;
+  if (reset) {
+    h->c.spmv_ms = 0.0;
+    h->c.spmv_count = 0;
+  }
   return PIRMCUT_OK;
 }
 

@@ -172,7 +172,17 @@ struct Ctx {
 
   bool x_set = false;
   int64_t launches = 0;
+
+  // live SpMV timing in stream-launch mode (options.time_spmv)
+  std::vector<cudaEvent_t> spmv_ev;  // 2 per SpMV launch of a chunk
+  double spmv_ms = 0.0;
+  int64_t spmv_count = 0;
 };
+
+// Events for timing `pairs` SpMV launches (created on first use); nullptr on failure.
+cudaEvent_t* spmv_events(Ctx& c, int pairs);
+// Add the first `executed` of `pairs` bracketed launches to the totals.
+void spmv_events_collect(Ctx& c, int pairs, int executed);
 
 // pcg.cu
 inline int row_grid(const Ctx& c) {
@@ -180,6 +190,10 @@ inline int row_grid(const Ctx& c) {
   return grid_for(threads);
 }
 int enqueue_reweight(Ctx& c, cudaStream_t st, bool initial);
+// offsets of the PCG counters the stream-launch loops read back
+struct PcgProgress {
+  int iters, maxit, stop_req;
+};
 int enqueue_step_end(Ctx& c, cudaStream_t st, bool initial, const OuterState* O);
 cudaError_t build_step_graph(Ctx& c, bool initial, cudaGraphExec_t* out, int* nodes);
 cudaError_t run_step_stream(Ctx& c, bool initial, int* stop_flag_host, int64_t* kernels);

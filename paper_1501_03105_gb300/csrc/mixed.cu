@@ -834,11 +834,14 @@ int enqueue_spmv32(Ctx& c, cudaStream_t st) {
 }
 
 // One launch of the fused SpMV: p_old = (odd ? pb : pa), p_new the other.
-int enqueue_fused_spmv32(Ctx& c, cudaStream_t st, bool odd) {
+int enqueue_fused_spmv32(Ctx& c, cudaStream_t st, bool odd, cudaEvent_t e0 = nullptr,
+                         cudaEvent_t e1 = nullptr) {
+  if (e0) cudaEventRecord(e0, st);
   const float* pold = odd ? c.p32b : c.p32;
   float* pnew = odd ? c.p32 : c.p32b;
   PIRMCUT_DISPATCH_K(c.K, (k_spmv32v_fused_dia<KK><<<c.fused_grid, PIRMCUT_FUSED_THREADS, 0, st>>>(
                               c.dd, c.g32, c.r32, pold, pnew, c.d32, c.q32, c.partials, c.S)));
+  if (e1) cudaEventRecord(e1, st);
   return 1;
 }
 
@@ -847,17 +850,23 @@ int enqueue_fused_spmv32(Ctx& c, cudaStream_t st, bool odd) {
 // iterations (spmv_fused(pa -> pb), update_r, spmv_fused(pb -> pa), update_r),
 // so that the body of a graph loop leaves p in its starting buffer; a stop
 // requested by the first update_r turns the second pair into no-ops.
-int enqueue_inner_iteration(Ctx& c, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
+// ev, when given, holds one event pair per SpMV launch (two with the fused
+// recurrence).
+int enqueue_inner_iteration(Ctx& c, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond,
+                            cudaEvent_t* ev = nullptr) {
   const int vec = vector_rows(c) ? 1 : 0;
   const int g = vec ? grid_for(c.nt / 4) : grid_for(c.nt);
   if (c.fused_inner) {
     for (int half = 0; half < 2; ++half) {
-      enqueue_fused_spmv32(c, st, half == 1);
+      enqueue_fused_spmv32(c, st, half == 1, ev ? ev[2 * half] : nullptr,
+                           ev ? ev[2 * half + 1] : nullptr);
       k_update32_r<<<g, kThreads, 0, st>>>(c.nt, vec, c.q32, c.r32, c.partials, c.S, h, use_cond);
     }
     return 4;
   }
+  if (ev) cudaEventRecord(ev[0], st);
   enqueue_spmv32(c, st);
+  if (ev) cudaEventRecord(ev[1], st);
   k_update32_r<<<g, kThreads, 0, st>>>(c.nt, vec, c.q32, c.r32, c.partials, c.S, h, 0);
   k_update32_xp<<<g, kThreads, 0, st>>>(c.nt, vec, c.d32, c.p32, c.r32, c.S, h, use_cond);
   return 3;
@@ -1020,19 +1029,27 @@ cudaError_t run_step_stream_mixed(Ctx& c, bool initial, int* flag_host, int64_t*
   if (initial || !c.opt.warm_start) cudaMemsetAsync(c.x, 0, sizeof(double) * c.nt, st);
   cudaError_t e = cudaGetLastError();
   const size_t off_o = offsetof(OuterState, outer_stop);
-  const size_t off_s = offsetof(PcgState, stop_req);
+  const size_t off_s = offsetof(PcgState, iters);
+  PcgProgress* prog = reinterpret_cast<PcgProgress*>(flag_host);
+  const int per_call = c.fused_inner ? 2 : 1;  // SpMV launches per enqueue_inner_iteration
+  cudaEvent_t* ev = c.opt.time_spmv ? spmv_events(c, 8 * per_call) : nullptr;
   for (int outer = 0; e == cudaSuccess && outer < 70; ++outer) {
     k += enqueue_resid(c, st, none, none, 0);
     e = cudaMemcpyAsync(flag_host, reinterpret_cast<char*>(c.O) + off_o, sizeof(int),
                         cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess || *flag_host) break;
+    int iters_before = 0;  // the residual kernel restarted the inner count
     for (int guard = 0; e == cudaSuccess; ++guard) {
-      for (int j = 0; j < 8; ++j) k += enqueue_inner_iteration(c, st, none, 0);
-      e = cudaMemcpyAsync(flag_host, reinterpret_cast<char*>(c.S) + off_s, sizeof(int),
+      for (int j = 0; j < 8; ++j)
+        k += enqueue_inner_iteration(c, st, none, 0, ev ? ev + 2 * per_call * j : nullptr);
+      e = cudaMemcpyAsync(prog, reinterpret_cast<char*>(c.S) + off_s, sizeof(PcgProgress),
                           cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess || *flag_host) break;
+      if (e != cudaSuccess) break;
+      if (ev) spmv_events_collect(c, 8 * per_call, prog->iters - iters_before);
+      iters_before = prog->iters;
+      if (prog->stop_req) break;
       if (guard > 2000 / 8 + 2) break;
     }
     k += enqueue_xupdate(c, st);

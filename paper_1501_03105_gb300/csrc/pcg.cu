@@ -570,10 +570,13 @@ int enqueue_prologue(Ctx& c, cudaStream_t st, bool initial, cudaGraphConditional
   return kernels;
 }
 
-// One PCG iteration: spmv -> update_r -> update_xp.
-int enqueue_iteration(Ctx& c, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
+// One PCG iteration: spmv -> update_r -> update_xp (events, when given,
+// bracket the spmv launch).
+int enqueue_iteration(Ctx& c, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond,
+                      cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
   const int grid = row_grid(c);
   const double* g = c.format == PIRMCUT_FORMAT_DIA ? c.gdia : c.gval;
+  if (e0) cudaEventRecord(e0, st);
   if (c.format == PIRMCUT_FORMAT_DIA) {
     PIRMCUT_DISPATCH_K(c.K, (k_spmv_dia<KK><<<grid, kThreads, 0, st>>>(
                                 c.dd, g, c.diag, c.p, c.q, c.partials, c.S)));
@@ -581,6 +584,7 @@ int enqueue_iteration(Ctx& c, cudaStream_t st, cudaGraphConditionalHandle h, int
     PIRMCUT_DISPATCH_G(c.group, (k_spmv_csr<GG><<<grid, kThreads, 0, st>>>(
                                     c.nt, c.rp, c.col, g, c.diag, c.p, c.q, c.partials, c.S)));
   }
+  if (e1) cudaEventRecord(e1, st);
   k_update_r<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.q, c.dinv, c.r, c.partials, c.S);
   k_update_xp<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.x, c.p, c.q, c.S, h, use_cond);
   return 3;
@@ -653,13 +657,23 @@ cudaError_t run_step_stream(Ctx& c, bool initial, int* stop_flag_host, int64_t* 
   cudaGraphConditionalHandle none{};
   int64_t k = enqueue_prologue(c, st, initial, none, 0);
   cudaError_t e = cudaGetLastError();
-  const size_t off = offsetof(PcgState, stop_req);
+  static_assert(offsetof(PcgState, maxit) == offsetof(PcgState, iters) + sizeof(int) &&
+                    offsetof(PcgState, stop_req) == offsetof(PcgState, iters) + 2 * sizeof(int),
+                "iters, maxit, stop_req are read back together");
+  const size_t off = offsetof(PcgState, iters);
+  PcgProgress* prog = reinterpret_cast<PcgProgress*>(stop_flag_host);
+  cudaEvent_t* ev = c.opt.time_spmv ? spmv_events(c, 8) : nullptr;
+  int iters_before = 0;
   for (int guard = 0; e == cudaSuccess; ++guard) {
-    for (int j = 0; j < 8; ++j) k += enqueue_iteration(c, st, none, 0);
-    e = cudaMemcpyAsync(stop_flag_host, reinterpret_cast<char*>(c.S) + off, sizeof(int),
+    for (int j = 0; j < 8; ++j)
+      k += enqueue_iteration(c, st, none, 0, ev ? ev[2 * j] : nullptr, ev ? ev[2 * j + 1] : nullptr);
+    e = cudaMemcpyAsync(prog, reinterpret_cast<char*>(c.S) + off, sizeof(PcgProgress),
                         cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess || *stop_flag_host) break;
+    if (e != cudaSuccess) break;
+    if (ev) spmv_events_collect(c, 8, prog->iters - iters_before);
+    iters_before = prog->iters;
+    if (prog->stop_req) break;
     if (guard > c.opt.pcg_max_iter / 8 + 2) break;  // the device caps iterations; belt and braces
   }
   if (e == cudaSuccess) {

@@ -231,6 +231,27 @@ def test_host_reduction_paths_give_identical_solves(P):
     assert out[0][1] == out[1][1]
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_live_spmv_timing_counts_every_working_launch(P, precision):
+    """time_spmv with host launches: one timed SpMV per PCG iteration (FP32
+    inner iterations for mixed), none for launches after the stop test; the
+    same x as the graph-launched solve."""
+    g = gen.config_graph(1)
+    T = 8
+    eps = O.eps_schedule(T)
+    with solver(P, g, precision=precision) as a, \
+            solver(P, g, precision=precision, graph_launch=0, time_spmv=1) as b:
+        ia = a.solve(T, eps)
+        ib = b.solve(T, eps)
+        ms, n = b.spmv_timing()
+        assert n == sum(i.pcg_iters for i in ib) and n > 0
+        assert ms > 0
+        assert b.spmv_timing() == (0.0, 0)       # reset by the first read
+        assert np.array_equal(a.get_x(), b.get_x())
+        assert [i.pcg_iters for i in ia] == [i.pcg_iters for i in ib]
+        assert a.spmv_timing() == (0.0, 0)       # graph launches are not timed
+
+
 def test_one_vertex_and_no_source_edges(P):
     """n = 3 (s-v-t) closed form; and b = 0 (no s edges) gives x = 0."""
     rp, col, c = gen.csr_from_edges(3, [0, 1], [1, 2], [3.0, 1.0])
