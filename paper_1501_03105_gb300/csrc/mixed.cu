@@ -204,9 +204,12 @@ __device__ __forceinline__ void massemble_row(const MAssemble& a, int64_t i, dou
                                               double& bb) {
   a.diag64[i] = sum;
   a.b64[i] = gs;
-  const double si = rsqrt(sum);
-  a.s64[i] = si;
-  a.s32[i] = float(si);
+  // the scaling only shapes the inner system (the FP64 residual decides
+  // convergence), so an FP32 reciprocal square root serves; the same value
+  // scales the matrix, the right-hand side and the correction
+  const float si = rsqrtf(float(sum));
+  a.s64[i] = double(si);
+  a.s32[i] = si;
   bb = fma(gs, gs, bb);
 }
 
@@ -289,15 +292,15 @@ k_massemble_csr(int64_t nt, const int64_t* __restrict__ rp, const double* __rest
 // scaled conductances g_uv d_u^-1/2 d_v^-1/2, rounded once to FP32
 template <int K>
 __global__ void __launch_bounds__(kThreads)
-k_mscale_dia(DiaDesc d, const double* __restrict__ g, const double* __restrict__ s64,
+k_mscale_dia(DiaDesc d, const double* __restrict__ g, const float* __restrict__ s32,
              float* __restrict__ g32) {
   const int64_t nt = d.nt;
   for (int64_t i = gtid(); i < nt; i += gstride()) {
-    const double si = s64[i];
+    const float si = s32[i];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int64_t j = i + d.off[k];
-      g32[k * nt + i] = j < nt ? float(g[k * nt + i] * si * s64[j]) : 0.0f;
+      g32[k * nt + i] = j < nt ? float(g[k * nt + i]) * si * s32[j] : 0.0f;
     }
   }
 }
@@ -305,12 +308,12 @@ k_mscale_dia(DiaDesc d, const double* __restrict__ g, const double* __restrict__
 template <int G>
 __global__ void __launch_bounds__(kThreads)
 k_mscale_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-             const double* __restrict__ g, const double* __restrict__ s64, float* __restrict__ g32) {
+             const double* __restrict__ g, const float* __restrict__ s32, float* __restrict__ g32) {
   const int lane = threadIdx.x % G;
   const int64_t ng = gstride() / G;
   for (int64_t i = gtid() / G; i < nt; i += ng) {
-    const double si = s64[i];
-    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) g32[e] = float(g[e] * si * s64[col[e]]);
+    const float si = s32[i];
+    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) g32[e] = float(g[e]) * si * s32[col[e]];
   }
 }
 
@@ -785,11 +788,11 @@ int enqueue_massemble(Ctx& c, cudaStream_t st, bool initial) {
   a.O = c.O;
   if (c.format == PIRMCUT_FORMAT_DIA) {
     PIRMCUT_DISPATCH_K(c.K, (k_massemble_dia<KK><<<grid, kThreads, 0, st>>>(c.dd, c.gdia, a)));
-    PIRMCUT_DISPATCH_K(c.K, (k_mscale_dia<KK><<<grid, kThreads, 0, st>>>(c.dd, c.gdia, c.s64, c.g32)));
+    PIRMCUT_DISPATCH_K(c.K, (k_mscale_dia<KK><<<grid, kThreads, 0, st>>>(c.dd, c.gdia, c.s32, c.g32)));
   } else {
     PIRMCUT_DISPATCH_G(c.group, (k_massemble_csr<GG><<<grid, kThreads, 0, st>>>(c.nt, c.rp, c.gval, a)));
     PIRMCUT_DISPATCH_G(c.group, (k_mscale_csr<GG><<<grid, kThreads, 0, st>>>(c.nt, c.rp, c.col, c.gval,
-                                                                             c.s64, c.g32)));
+                                                                             c.s32, c.g32)));
   }
   return 2;
 }
