@@ -1,6 +1,8 @@
 // Internal declarations shared by the translation units of libpirmcut.
 #pragma once
 
+#include <sched.h>
+
 #include <algorithm>
 #include <cstdint>
 #include <memory>
@@ -38,12 +40,25 @@ struct NoInitAllocator : std::allocator<T> {
 template <class T>
 using hvec = std::vector<T, NoInitAllocator<T>>;
 
+// Cores this process may run on (its CPU affinity mask; hardware_concurrency
+// counts every CPU of the machine, which oversubscribes a restricted process).
+inline int host_threads() {
+  static const int n = [] {
+    cpu_set_t set;
+    CPU_ZERO(&set);
+    int k = 0;
+    if (sched_getaffinity(0, sizeof(set), &set) == 0) k = CPU_COUNT(&set);
+    if (k <= 0) k = int(std::thread::hardware_concurrency());
+    return k > 0 ? k : 1;
+  }();
+  return n;
+}
+
 // Run fn(lo, hi) over [0, n) split across the host's cores (at least
 // min_per_thread items per thread).
 template <class F>
 void parallel_for(int64_t n, F fn, int64_t min_per_thread = 32768) {
-  const unsigned hw = std::thread::hardware_concurrency();
-  int64_t nth = std::max<int64_t>(1, std::min<int64_t>(hw ? hw : 1, 64));
+  int64_t nth = std::max<int64_t>(1, std::min<int64_t>(host_threads(), 64));
   nth = std::min<int64_t>(nth, std::max<int64_t>(1, n / min_per_thread));
   std::vector<std::thread> th;
   for (int64_t k = 0; k < nth; ++k) {
