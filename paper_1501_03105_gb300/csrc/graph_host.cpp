@@ -60,11 +60,9 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
     *err = "row_ptr[0] must be 0";
     return PIRMCUT_EINVAL;
   }
-  for (int64_t v = 0; v < n; ++v) {
-    if (row_ptr[v + 1] < row_ptr[v]) {
-      *err = "row_ptr must be non-decreasing";
-      return PIRMCUT_EINVAL;
-    }
+  if (parallel_find_first(n, [&](int64_t v) { return row_ptr[v + 1] < row_ptr[v]; }) < n) {
+    *err = "row_ptr must be non-decreasing";
+    return PIRMCUT_EINVAL;
   }
   const int64_t nnz = row_ptr[n];
   if (nnz > 0 && (!col || !c)) {
@@ -129,14 +127,17 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
       cnt[reduced_index(v, s, t) + 1] = merged;
     }
   });
-  for (int64_t v = 0; v < n; ++v) {
-    if (row_bad[v] == 1) { *err = "column index out of range in row " + std::to_string(v); return PIRMCUT_EINVAL; }
-    if (row_bad[v] == 2) { *err = "self-loop at vertex " + std::to_string(v); return PIRMCUT_EINVAL; }
-    if (row_bad[v] == 3) { *err = "capacity not finite or negative in row " + std::to_string(v); return PIRMCUT_EINVAL; }
+  {
+    const int64_t v = parallel_find_first(n, [&](int64_t i) { return row_bad[i] >= 1 && row_bad[i] <= 3; });
+    if (v < n) {
+      if (row_bad[v] == 1) *err = "column index out of range in row " + std::to_string(v);
+      else if (row_bad[v] == 2) *err = "self-loop at vertex " + std::to_string(v);
+      else *err = "capacity not finite or negative in row " + std::to_string(v);
+      return PIRMCUT_EINVAL;
+    }
   }
   hvec<int64_t> rp(nt + 1);
-  rp[0] = 0;
-  for (int64_t i = 0; i < nt; ++i) rp[i + 1] = rp[i] + cnt[i + 1];
+  parallel_scan_shifted(cnt.data() + 1, nt, rp.data());
   const int64_t mnt = rp[nt];
   hvec<int32_t> rc(mnt);
   hvec<double> rv(mnt);
@@ -229,8 +230,9 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
     for (int64_t i = lo; i < hi; ++i)
       asym[i] = (cs[i] != cs_from_s[i] || ct[i] != ct_from_t[i]) ? 1 : 0;
   });
-  for (int64_t i = 0; i < nt; ++i) {
-    if (asym[i]) {
+  {
+    const int64_t i = parallel_find_first(nt, [&](int64_t k) { return asym[k] != 0; });
+    if (i < nt) {
       *err = "CSR is not symmetric (terminal edge of vertex " +
              std::to_string(original_index(i, s, t)) + ")";
       return PIRMCUT_EINVAL;
@@ -251,8 +253,9 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
       }
     }
   });
-  for (int64_t i = 0; i < nt; ++i) {
-    if (asym[i]) {
+  {
+    const int64_t i = parallel_find_first(nt, [&](int64_t k) { return asym[k] != 0; });
+    if (i < nt) {
       *err = "CSR is not symmetric (row " + std::to_string(original_index(i, s, t)) + ")";
       return PIRMCUT_EINVAL;
     }
@@ -279,8 +282,9 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
       }
     });
     std::vector<int64_t> stack;
-    for (int64_t i = 0; i < nt; ++i)
-      if (frontier[i]) stack.push_back(i);
+    if (parallel_find_first(nt, [&](int64_t k) { return frontier[k] != 0; }) < nt)
+      for (int64_t i = 0; i < nt; ++i)
+        if (frontier[i]) stack.push_back(i);
     while (!stack.empty()) {
       const int64_t i = stack.back();
       stack.pop_back();
@@ -292,18 +296,16 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
         }
       }
     }
-    for (int64_t i = 0; i < nt; ++i) {
-      if (!seen[i]) {
-        *err = "disconnected: vertex " + std::to_string(original_index(i, s, t)) +
-               " reaches neither s nor t through positive capacity";
-        return PIRMCUT_EDISCONNECTED;
-      }
+    const int64_t i = parallel_find_first(nt, [&](int64_t k) { return seen[k] == 0; });
+    if (i < nt) {
+      *err = "disconnected: vertex " + std::to_string(original_index(i, s, t)) +
+             " reaches neither s nor t through positive capacity";
+      return PIRMCUT_EDISCONNECTED;
     }
   }
   g.n_edges = mnt / 2;
   g.c_st = cst_s;
-  double sc = 0.0;
-  for (int64_t i = 0; i < nt; ++i) sc += cs[i];
+  const double sc = chunked_sum(cs.data(), nt);
   g.sum_cs = sc + cst_s;
   g.cs = std::move(cs);
   g.ct = std::move(ct);

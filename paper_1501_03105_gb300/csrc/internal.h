@@ -69,6 +69,76 @@ void parallel_for(int64_t n, F fn, int64_t min_per_thread = 32768) {
   for (auto& x : th) x.join();
 }
 
+// Smallest i in [0, n) with pred(i), or n: a parallel search over fixed
+// chunks (the answer does not depend on the thread count).
+template <class P>
+int64_t parallel_find_first(int64_t n, P pred) {
+  constexpr int kChunks = 256;
+  int64_t first[kChunks];
+  parallel_for(kChunks, [&](int64_t lo, int64_t hi) {
+    for (int64_t ch = lo; ch < hi; ++ch) {
+      const int64_t a = n * ch / kChunks, b = n * (ch + 1) / kChunks;
+      int64_t f = n;
+      for (int64_t i = a; i < b; ++i)
+        if (pred(i)) {
+          f = i;
+          break;
+        }
+      first[ch] = f;
+    }
+  }, 1);
+  for (int ch = 0; ch < kChunks; ++ch)
+    if (first[ch] < n) return first[ch];
+  return n;
+}
+
+// out[0] = 0, out[i + 1] = out[i] + in[i] for i < n (inclusive running sum of
+// in, shifted): chunk sums in parallel, then each chunk fills its range.
+template <class T>
+void parallel_scan_shifted(const T* in, int64_t n, T* out) {
+  constexpr int kChunks = 256;
+  T part[kChunks + 1];
+  parallel_for(kChunks, [&](int64_t lo, int64_t hi) {
+    for (int64_t ch = lo; ch < hi; ++ch) {
+      const int64_t a = n * ch / kChunks, b = n * (ch + 1) / kChunks;
+      T acc = 0;
+      for (int64_t i = a; i < b; ++i) acc += in[i];
+      part[ch + 1] = acc;
+    }
+  }, 1);
+  part[0] = 0;
+  for (int ch = 0; ch < kChunks; ++ch) part[ch + 1] += part[ch];
+  out[0] = 0;
+  parallel_for(kChunks, [&](int64_t lo, int64_t hi) {
+    for (int64_t ch = lo; ch < hi; ++ch) {
+      const int64_t a = n * ch / kChunks, b = n * (ch + 1) / kChunks;
+      T acc = part[ch];
+      for (int64_t i = a; i < b; ++i) {
+        acc += in[i];
+        out[i + 1] = acc;
+      }
+    }
+  }, 1);
+}
+
+// Sum of v[0, n) in a fixed order (256 chunk sums, then the chunks in order),
+// independent of the thread count.
+inline double chunked_sum(const double* v, int64_t n) {
+  constexpr int kChunks = 256;
+  double part[kChunks];
+  parallel_for(kChunks, [&](int64_t lo, int64_t hi) {
+    for (int64_t ch = lo; ch < hi; ++ch) {
+      const int64_t a = n * ch / kChunks, b = n * (ch + 1) / kChunks;
+      double acc = 0.0;
+      for (int64_t i = a; i < b; ++i) acc += v[i];
+      part[ch] = acc;
+    }
+  }, 1);
+  double s = 0.0;
+  for (int ch = 0; ch < kChunks; ++ch) s += part[ch];
+  return s;
+}
+
 // dst[0, n) = v in parallel
 template <class T>
 void parallel_fill(T* dst, int64_t n, T v) {

@@ -21,9 +21,18 @@
 
 #include "ctx.h"
 
+// Resident blocks per SM the FP64 PCG-iteration kernels are launched with
+// (the grid is capped at 152 times this); fewer, longer-running blocks spend
+// less of GB300's FP64 pipe on the per-block reduction trees.
+#ifndef PIRMCUT_FP64_BLOCKS_PER_SM
+#define PIRMCUT_FP64_BLOCKS_PER_SM 8
+#endif
+
 namespace pirmcut {
 
 namespace {
+
+constexpr int kFp64MaxBlocks = 152 * PIRMCUT_FP64_BLOCKS_PER_SM;
 
 __device__ __forceinline__ int64_t gtid() {
   return int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -480,7 +489,8 @@ cudaError_t launch_gather_x(Ctx& c, const double* xfull) {
 }
 
 cudaError_t launch_spmv_once(Ctx& c) {
-  const int grid = row_grid(c);
+  const int rg = row_grid(c);
+  const int grid = rg < kFp64MaxBlocks ? rg : kFp64MaxBlocks;
   if (c.format == PIRMCUT_FORMAT_DIA) {
     PIRMCUT_DISPATCH_K(c.K, (k_spmv_dia<KK><<<grid, kThreads, 0, c.stream>>>(
                                 c.dd, c.gdia, c.diag, c.p, c.q, c.partials, c.S)));
@@ -574,7 +584,9 @@ int enqueue_prologue(Ctx& c, cudaStream_t st, bool initial, cudaGraphConditional
 // bracket the spmv launch).
 int enqueue_iteration(Ctx& c, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond,
                       cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
-  const int grid = row_grid(c);
+  const int rg = row_grid(c), vg = grid_for(c.nt);
+  const int grid = rg < kFp64MaxBlocks ? rg : kFp64MaxBlocks;
+  const int vgrid = vg < kFp64MaxBlocks ? vg : kFp64MaxBlocks;
   const double* g = c.format == PIRMCUT_FORMAT_DIA ? c.gdia : c.gval;
   if (e0) cudaEventRecord(e0, st);
   if (c.format == PIRMCUT_FORMAT_DIA) {
@@ -585,8 +597,8 @@ int enqueue_iteration(Ctx& c, cudaStream_t st, cudaGraphConditionalHandle h, int
                                     c.nt, c.rp, c.col, g, c.diag, c.p, c.q, c.partials, c.S)));
   }
   if (e1) cudaEventRecord(e1, st);
-  k_update_r<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.q, c.dinv, c.r, c.partials, c.S);
-  k_update_xp<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.x, c.p, c.q, c.S, h, use_cond);
+  k_update_r<<<vgrid, kThreads, 0, st>>>(c.nt, c.q, c.dinv, c.r, c.partials, c.S);
+  k_update_xp<<<vgrid, kThreads, 0, st>>>(c.nt, c.x, c.p, c.q, c.S, h, use_cond);
   return 3;
 }
 
