@@ -93,6 +93,11 @@ typedef struct {
   int time_spmv;       /* 1 (with graph_launch 0): bracket every PCG
                           matrix-vector launch with CUDA events on the
                           context's stream; pirmcut_spmv_timing reports them  */
+  int reduce_on_host;  /* 0: validate and pack the input on the GPU when every
+                          row lists strictly increasing columns and every
+                          non-terminal has a terminal capacity (else, and for
+                          every input error, on the host); 1: always on the
+                          host.  Both give the same problem.                  */
 } pirmcut_options;
 
 typedef struct {
@@ -110,7 +115,7 @@ typedef struct {
 
 /* Fill *opt with the defaults: NORTH_STAR, FP64, pcg_tol 1e-10,
  * pcg_max_iter 20000, warm_start 1, FORMAT_AUTO, track_cut 0, graph_launch 1,
- * inner_tol 1e-5, time_spmv 0.  With MIXED, pcg_iters counts FP32 inner iterations, at most
+ * inner_tol 1e-5, time_spmv 0, reduce_on_host 0.  With MIXED, pcg_iters counts FP32 inner iterations, at most
  * min(pcg_max_iter, 2000) per refinement cycle and 64 cycles per system. */
 void pirmcut_default_options(pirmcut_options* opt);
 

@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
                 ("pcg_tol", ctypes.c_double), ("pcg_max_iter", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("format", ctypes.c_int),
                 ("track_cut", ctypes.c_int), ("graph_launch", ctypes.c_int),
-                ("inner_tol", ctypes.c_double), ("time_spmv", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("time_spmv", ctypes.c_int),
+                ("reduce_on_host", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):

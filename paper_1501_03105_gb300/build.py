@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libpirmcut.so")
 
-SOURCES = ["api.cu", "pcg.cu", "mixed.cu", "batch.cu", "sweep.cu", "static_sweep.cu", "twolevel.cu", "mlp.cu", "graph_host.cpp"]
+SOURCES = ["api.cu", "pcg.cu", "mixed.cu", "batch.cu", "sweep.cu", "static_sweep.cu", "twolevel.cu", "mlp.cu", "graph_device.cu", "graph_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

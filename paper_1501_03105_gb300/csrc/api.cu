@@ -44,7 +44,7 @@ cudaError_t dalloc(T** p, size_t count) {
 void free_device(Ctx& c) {
   void* ps[] = {c.cdia, c.gdia, c.rp, c.col, c.cval, c.gval, c.cs, c.ct, c.x, c.r, c.p,
                 c.q, c.diag, c.dinv, c.partials, c.S, c.C, c.eps_list, c.recs, c.xfull,
-                c.side_full};
+                c.side_full, c.d_in_rp, c.d_in_col};
   for (void* p : ps)
     if (p) cudaFree(p);
   pirmcut::sweep_free(c);
@@ -108,6 +108,14 @@ pirmcut_status upload_problem(pirmcut_ctx* h) {
   cudaStream_t st = c.stream;
   // the conductances start as the capacities (W^(0) = C): a defined g^(l-1)
   // for the first step even when x is set by the caller
+  if (c.device_reduced) {  // built in place on the device
+    if (c.format == PIRMCUT_FORMAT_DIA)
+      CK(h, cudaMemcpyAsync(c.gdia, c.cdia, sizeof(double) * size_t(c.K) * size_t(c.nt), cudaMemcpyDeviceToDevice, st), "upload");
+    else
+      CK(h, cudaMemcpyAsync(c.gval, c.cval, sizeof(double) * size_t(g.nnz), cudaMemcpyDeviceToDevice, st), "upload");
+    CK(h, cudaStreamSynchronize(st), "upload");
+    return PIRMCUT_OK;
+  }
   if (c.format == PIRMCUT_FORMAT_DIA) {
     CK(h, cudaMemcpyAsync(c.cdia, g.cdia.data(), sizeof(double) * g.cdia.size(), cudaMemcpyHostToDevice, st), "upload");
     CK(h, cudaMemcpyAsync(c.gdia, c.cdia, sizeof(double) * g.cdia.size(), cudaMemcpyDeviceToDevice, st), "upload");
@@ -268,6 +276,108 @@ pirmcut_status run_steps(pirmcut_ctx* h, bool with_initial, int T, int first_ste
   return PIRMCUT_OK;
 }
 
+// Everything after the reduction: device arrays, staging, the upload (or
+// adoption of arrays the device reduction built), the step buffers.
+pirmcut_status finish_create(pirmcut_ctx* h, const pirmcut_options& o, void* stream,
+                             pirmcut::DeviceGraph* dg, pirmcut_ctx** out) {
+  Ctx& cx = h->c;
+  cudaError_t e = cudaSuccess;
+  if (dg) {  // the problem arrays were built on the device: adopt them (freed with cx)
+    cx.cdia = dg->cdia;
+    cx.rp = dg->rp;
+    cx.col = dg->col;
+    cx.cval = dg->cval;
+    cx.cs = dg->cs;
+    cx.ct = dg->ct;
+    cx.d_in_rp = dg->in_rp;
+    cx.d_in_col = dg->in_col;
+    *dg = pirmcut::DeviceGraph();
+    cx.device_reduced = true;
+  }
+  cx.opt = o;
+  cx.nt = cx.hg.nt;
+  cx.format = cx.hg.format;
+  cx.K = cx.hg.K;
+  cx.dd.nt = cx.nt;
+  for (int k = 0; k < pirmcut::kMaxDiag; ++k) cx.dd.off[k] = cx.hg.off[k];
+  cx.group = cx.hg.group;
+  cx.stream = reinterpret_cast<cudaStream_t>(stream);
+  auto bail = [&](cudaError_t err, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(err);
+    free_device(cx);
+    if (h->h_ctr) cudaFreeHost(h->h_ctr);
+    delete h;
+    return fail(nullptr, err == cudaErrorMemoryAllocation ? PIRMCUT_ENOMEM : PIRMCUT_ECUDA, m);
+  };
+  if ((e = cudaGetDevice(&cx.device)) != cudaSuccess) return bail(e, "cudaGetDevice");
+  if ((e = cudaStreamCreateWithFlags(&cx.cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(e, "cudaStreamCreate");
+  const size_t nt = size_t(cx.nt);
+  const size_t m = size_t(cx.hg.nnz);
+  if (!cx.device_reduced) {
+    if (cx.format == PIRMCUT_FORMAT_DIA) {
+      if ((e = dalloc(&cx.cdia, size_t(cx.K) * nt)) != cudaSuccess) return bail(e, "cudaMalloc");
+    } else {
+      if ((e = dalloc(&cx.rp, nt + 1)) != cudaSuccess) return bail(e, "cudaMalloc");
+      if ((e = dalloc(&cx.col, m)) != cudaSuccess) return bail(e, "cudaMalloc");
+      if ((e = dalloc(&cx.cval, m)) != cudaSuccess) return bail(e, "cudaMalloc");
+    }
+    if ((e = dalloc(&cx.cs, nt)) != cudaSuccess) return bail(e, "cudaMalloc");
+    if ((e = dalloc(&cx.ct, nt)) != cudaSuccess) return bail(e, "cudaMalloc");
+  }
+  if (cx.format == PIRMCUT_FORMAT_DIA) {
+    if ((e = dalloc(&cx.gdia, size_t(cx.K) * nt)) != cudaSuccess) return bail(e, "cudaMalloc");
+  } else {
+    if ((e = dalloc(&cx.gval, m)) != cudaSuccess) return bail(e, "cudaMalloc");
+  }
+  double** vecs[] = {&cx.x, &cx.r, &cx.p, &cx.q, &cx.diag, &cx.dinv};
+  for (double** v : vecs)
+    if ((e = dalloc(v, nt)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = dalloc(&cx.partials, 4 * size_t(pirmcut::kMaxBlocks))) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = dalloc(&cx.S, 1)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = dalloc(&cx.C, 1)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = cudaMemset(cx.S, 0, sizeof(pirmcut::PcgState))) != cudaSuccess) return bail(e, "cudaMemset");
+  if (o.precision == PIRMCUT_PREC_MIXED && (e = pirmcut::mixed_alloc(cx)) != cudaSuccess)
+    return bail(e, "cudaMalloc");
+  if ((e = cudaMemset(cx.C, 0, sizeof(pirmcut::StepCounters))) != cudaSuccess) return bail(e, "cudaMemset");
+  if ((e = cudaHostAlloc((void**)&h->h_ctr, sizeof(pirmcut::StepCounters) + 10 * sizeof(double),
+                         cudaHostAllocDefault)) != cudaSuccess)
+    return bail(e, "cudaHostAlloc");
+  h->h_eps = reinterpret_cast<double*>(h->h_ctr + 1);
+  h->h_result = h->h_eps + 2;
+  h->h_stop = reinterpret_cast<int*>(h->h_eps + 7);
+  pirmcut_status ps = upload_problem(h);
+  if (ps != PIRMCUT_OK) {
+    std::string m = cx.err;
+    free_device(cx);
+    cudaFreeHost(h->h_ctr);
+    delete h;
+    return fail(nullptr, ps, m);
+  }
+  ps = ensure_capacity(h, 1);
+  if (ps != PIRMCUT_OK) {
+    std::string m = cx.err;
+    free_device(cx);
+    cudaFreeHost(h->h_ctr);
+    delete h;
+    return fail(nullptr, ps, m);
+  }
+  *out = h;
+  return PIRMCUT_OK;
+}
+
+pirmcut_status create_from_device(int64_t n, const pirmcut_options& o, void* stream,
+                                  pirmcut::HostGraph&& g, pirmcut::DeviceGraph& dg, pirmcut_ctx** out) {
+  (void)n;
+  pirmcut_ctx* h = new (std::nothrow) pirmcut_ctx();
+  if (!h) {
+    dg.release();
+    return fail(nullptr, PIRMCUT_ENOMEM, "out of host memory");
+  }
+  h->c.hg = std::move(g);
+  return finish_create(h, o, stream, &dg, out);
+}
+
 }  // namespace
 
 namespace pirmcut {
@@ -308,6 +418,7 @@ void pirmcut_default_options(pirmcut_options* opt) {
   opt->graph_launch = 1;
   opt->inner_tol = 1e-5;
   opt->time_spmv = 0;
+  opt->reduce_on_host = 0;
 }
 
 pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* col,
@@ -326,8 +437,26 @@ pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* 
   std::string msg;
   if (check_options(o, &msg) != PIRMCUT_OK) return fail(nullptr, PIRMCUT_EINVAL, msg);
 
-  // the structure is kept (pirmcut_update_weights re-reduces it); host
-  // capacities are read in place, device ones through a host copy
+  // the GPU builds the problem when the input allows (rows in order, every
+  // non-terminal with a terminal capacity); otherwise, and for every input
+  // error, the host does
+  pirmcut::DeviceGraph dg;
+  pirmcut::HostGraph dhg;
+  bool taken = false;
+  if (!o.reduce_on_host) {
+    // a failed device attempt (no device, no memory, an unusable storage
+    // request) leaves the problem and its diagnosis to the host reduction
+    pirmcut_status dps = pirmcut::reduce_graph_device(n, row_ptr, col, c, s, t, o.format, mem_kind,
+                                                      stream, nullptr, nullptr, &dhg, &dg, &taken, &msg);
+    if (dps != PIRMCUT_OK) {
+      taken = false;
+      cudaGetLastError();
+    }
+  }
+  if (taken) return create_from_device(n, o, stream, std::move(dhg), dg, out);
+
+  // host reduction: the structure is kept (pirmcut_update_weights re-reduces
+  // it); host capacities are read in place, device ones through a host copy
   pirmcut::hvec<int64_t> rp;
   pirmcut::hvec<int32_t> cl;
   pirmcut::hvec<double> cv;
@@ -352,71 +481,9 @@ pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* 
     delete h;
     return fail(nullptr, ps, msg);
   }
-  cx.opt = o;
-  cx.nt = cx.hg.nt;
-  cx.format = cx.hg.format;
-  cx.K = cx.hg.K;
-  cx.dd.nt = cx.nt;
-  for (int k = 0; k < pirmcut::kMaxDiag; ++k) cx.dd.off[k] = cx.hg.off[k];
-  cx.group = cx.hg.group;
   cx.in_rp = std::move(rp);
   cx.in_col = std::move(cl);
-  cx.stream = reinterpret_cast<cudaStream_t>(stream);
-  auto bail = [&](cudaError_t err, const char* where) {
-    std::string m = std::string(where) + ": " + cudaGetErrorString(err);
-    free_device(cx);
-    if (h->h_ctr) cudaFreeHost(h->h_ctr);
-    delete h;
-    return fail(nullptr, err == cudaErrorMemoryAllocation ? PIRMCUT_ENOMEM : PIRMCUT_ECUDA, m);
-  };
-  if ((e = cudaGetDevice(&cx.device)) != cudaSuccess) return bail(e, "cudaGetDevice");
-  if ((e = cudaStreamCreateWithFlags(&cx.cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
-    return bail(e, "cudaStreamCreate");
-  const size_t nt = size_t(cx.nt);
-  if (cx.format == PIRMCUT_FORMAT_DIA) {
-    if ((e = dalloc(&cx.cdia, size_t(cx.K) * nt)) != cudaSuccess) return bail(e, "cudaMalloc");
-    if ((e = dalloc(&cx.gdia, size_t(cx.K) * nt)) != cudaSuccess) return bail(e, "cudaMalloc");
-  } else {
-    const size_t m = cx.hg.col.size();
-    if ((e = dalloc(&cx.rp, nt + 1)) != cudaSuccess) return bail(e, "cudaMalloc");
-    if ((e = dalloc(&cx.col, m)) != cudaSuccess) return bail(e, "cudaMalloc");
-    if ((e = dalloc(&cx.cval, m)) != cudaSuccess) return bail(e, "cudaMalloc");
-    if ((e = dalloc(&cx.gval, m)) != cudaSuccess) return bail(e, "cudaMalloc");
-  }
-  double** vecs[] = {&cx.cs, &cx.ct, &cx.x, &cx.r, &cx.p, &cx.q, &cx.diag, &cx.dinv};
-  for (double** v : vecs)
-    if ((e = dalloc(v, nt)) != cudaSuccess) return bail(e, "cudaMalloc");
-  if ((e = dalloc(&cx.partials, 4 * size_t(pirmcut::kMaxBlocks))) != cudaSuccess) return bail(e, "cudaMalloc");
-  if ((e = dalloc(&cx.S, 1)) != cudaSuccess) return bail(e, "cudaMalloc");
-  if ((e = dalloc(&cx.C, 1)) != cudaSuccess) return bail(e, "cudaMalloc");
-  if ((e = cudaMemset(cx.S, 0, sizeof(pirmcut::PcgState))) != cudaSuccess) return bail(e, "cudaMemset");
-  if (o.precision == PIRMCUT_PREC_MIXED && (e = pirmcut::mixed_alloc(cx)) != cudaSuccess)
-    return bail(e, "cudaMalloc");
-  if ((e = cudaMemset(cx.C, 0, sizeof(pirmcut::StepCounters))) != cudaSuccess) return bail(e, "cudaMemset");
-  if ((e = cudaHostAlloc((void**)&h->h_ctr, sizeof(pirmcut::StepCounters) + 10 * sizeof(double),
-                         cudaHostAllocDefault)) != cudaSuccess)
-    return bail(e, "cudaHostAlloc");
-  h->h_eps = reinterpret_cast<double*>(h->h_ctr + 1);
-  h->h_result = h->h_eps + 2;
-  h->h_stop = reinterpret_cast<int*>(h->h_eps + 7);
-  ps = upload_problem(h);
-  if (ps != PIRMCUT_OK) {
-    std::string m = cx.err;
-    free_device(cx);
-    cudaFreeHost(h->h_ctr);
-    delete h;
-    return fail(nullptr, ps, m);
-  }
-  ps = ensure_capacity(h, 1);
-  if (ps != PIRMCUT_OK) {
-    std::string m = cx.err;
-    free_device(cx);
-    cudaFreeHost(h->h_ctr);
-    delete h;
-    return fail(nullptr, ps, m);
-  }
-  *out = h;
-  return PIRMCUT_OK;
+  return finish_create(h, o, stream, nullptr, out);
 }
 
 pirmcut_status pirmcut_initial(pirmcut_ctx* h, pirmcut_step_info* info) {
@@ -527,6 +594,50 @@ pirmcut_status pirmcut_update_weights(pirmcut_ctx* h, const double* cnew, int me
   Ctx& c = h->c;
   if (mem_kind != PIRMCUT_MEM_HOST && mem_kind != PIRMCUT_MEM_DEVICE)
     return fail(h, PIRMCUT_EINVAL, "unknown mem_kind");
+  if (c.device_reduced) {
+    // the structure is on the device: rebuild there; an input the device
+    // reduction does not take goes through the host for its message or result
+    pirmcut::DeviceGraph dg;
+    pirmcut::HostGraph ng;
+    bool taken = false;
+    std::string msg;
+    pirmcut_status dps = pirmcut::reduce_graph_device(c.hg.n, nullptr, nullptr, cnew, c.hg.s, c.hg.t,
+                                                      c.format, mem_kind, c.stream, c.d_in_rp,
+                                                      c.d_in_col, &ng, &dg, &taken, &msg);
+    if (dps != PIRMCUT_OK) return fail(h, dps, msg);
+    if (taken) {
+      bool same = ng.format == c.format && ng.nt == c.nt && ng.K == c.K && ng.nnz == c.hg.nnz;
+      for (int k = 0; same && k < c.K; ++k) same = ng.off[k] == c.hg.off[k];
+      if (!same) {
+        dg.release();
+        return fail(h, PIRMCUT_EINVAL, "the new capacities change the stored structure");
+      }
+      if (c.format == PIRMCUT_FORMAT_DIA) {
+        cudaFree(c.cdia);
+        c.cdia = dg.cdia;
+        dg.cdia = nullptr;
+      } else {
+        cudaFree(c.cval);
+        c.cval = dg.cval;
+        dg.cval = nullptr;
+      }
+      cudaFree(c.cs);
+      cudaFree(c.ct);
+      c.cs = dg.cs;
+      c.ct = dg.ct;
+      dg.cs = dg.ct = nullptr;
+      dg.release();  // the reduced structure arrays of the rebuild (same as c's)
+      c.hg = std::move(ng);
+      if (c.g_cut) {
+        cudaGraphExecDestroy(c.g_cut);
+        c.g_cut = nullptr;
+      }
+      return PIRMCUT_OK;
+    }
+    // host reduction of the device-resident structure
+    CK(h, to_host(c.in_rp, static_cast<const int64_t*>(c.d_in_rp), size_t(c.hg.n) + 1, PIRMCUT_MEM_DEVICE), "reading the structure");
+    CK(h, to_host(c.in_col, static_cast<const int32_t*>(c.d_in_col), size_t(c.in_rp.back()), PIRMCUT_MEM_DEVICE), "reading the structure");
+  }
   const int64_t nnz = c.in_rp.back();
   if (nnz > 0 && !cnew) return fail(h, PIRMCUT_EINVAL, "c must not be NULL");
   pirmcut::hvec<double> cv;
@@ -540,14 +651,9 @@ pirmcut_status pirmcut_update_weights(pirmcut_ctx* h, const double* cnew, int me
   pirmcut_status ps = pirmcut::reduce_graph(c.hg.n, c.in_rp.data(), c.in_col.data(), cin,
                                             c.hg.s, c.hg.t, c.format, &ng, &msg);
   if (ps != PIRMCUT_OK) return fail(h, ps, msg);
-  bool same = ng.format == c.format && ng.nt == c.nt && ng.K == c.K;
+  bool same = ng.format == c.format && ng.nt == c.nt && ng.K == c.K && ng.nnz == c.hg.nnz;
   for (int k = 0; same && k < c.K; ++k) same = ng.off[k] == c.hg.off[k];
-  if (same && c.format == PIRMCUT_FORMAT_CSR) same = ng.col.size() == c.hg.col.size();
   if (!same) return fail(h, PIRMCUT_EINVAL, "the new capacities change the stored structure");
-  if (c.format == PIRMCUT_FORMAT_CSR) {
-    ng.rp.swap(c.hg.rp);  // structure unchanged; keep the uploaded copy
-    ng.col.swap(c.hg.col);
-  }
   c.hg = std::move(ng);
   if (c.format == PIRMCUT_FORMAT_CSR) {
     CK(h, cudaMemcpyAsync(c.cval, c.hg.cval.data(), sizeof(double) * c.hg.cval.size(), cudaMemcpyHostToDevice, c.stream), "upload");
@@ -584,7 +690,7 @@ pirmcut_status pirmcut_time_spmv(pirmcut_ctx* h, int reps, double* avg_ms, doubl
   if (reps < 1 || !avg_ms) return fail(h, PIRMCUT_EINVAL, "reps must be >= 1 and avg_ms non-NULL");
   const double nt = double(c.nt);
   const double nnz = c.format == PIRMCUT_FORMAT_DIA ? 2.0 * double(c.hg.n_edges)
-                                                     : double(c.hg.col.size());
+                                                     : double(c.hg.nnz);
   const bool mx = c.opt.precision == PIRMCUT_PREC_MIXED;
   const double V = mx ? 4.0 : 8.0;
   // vectors read/written once per row: diag, p, q (the FP32 inner system is

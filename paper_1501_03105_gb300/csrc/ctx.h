@@ -102,8 +102,11 @@ struct MlpBuf {
 struct Ctx {
   // problem
   HostGraph hg;               // reduced problem (host copy kept for update_weights)
-  hvec<int64_t> in_rp;        // original CSR structure (for update_weights)
+  hvec<int64_t> in_rp;        // original CSR structure (for update_weights), host reduction
   hvec<int32_t> in_col;
+  int64_t* d_in_rp = nullptr; // the same on the device, device reduction
+  int32_t* d_in_col = nullptr;
+  bool device_reduced = false;  // the problem was built on the GPU (hg holds scalars only)
   int64_t nt = 0;
   int format = PIRMCUT_FORMAT_CSR;
   int K = 0;

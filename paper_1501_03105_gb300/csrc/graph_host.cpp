@@ -304,6 +304,7 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
     }
   }
   g.n_edges = mnt / 2;
+  g.nnz = mnt;
   g.c_st = cst_s;
   const double sc = chunked_sum(cs.data(), nt);
   g.sum_cs = sc + cst_s;

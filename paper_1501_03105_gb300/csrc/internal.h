@@ -173,6 +173,22 @@ struct HostGraph {
   hvec<double> cs, ct;
   double c_st = 0.0;
   double sum_cs = 0.0;  // sum_v c(s, v) + c(s, t): the cut value of S = {s}
+  int64_t nnz = 0;      // stored entries of G~'s CSR (both directions)
+};
+
+// The reduced problem built on the GPU (device arrays, owned): the input
+// structure kept for later capacity updates, the terminal capacities, and
+// either the DIA capacities or the reduced CSR.
+struct DeviceGraph {
+  int64_t* in_rp = nullptr;
+  int32_t* in_col = nullptr;
+  double* cs = nullptr;
+  double* ct = nullptr;
+  double* cdia = nullptr;
+  int64_t* rp = nullptr;
+  int32_t* col = nullptr;
+  double* cval = nullptr;
+  void release();  // cudaFree of every non-null array
 };
 
 // Validate the full CSR and build the reduced problem.  Returns PIRMCUT_OK or
@@ -180,6 +196,17 @@ struct HostGraph {
 pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* col,
                             const double* c, int32_t s, int32_t t, int format_req,
                             HostGraph* out, std::string* err);
+
+// The same reduction on the GPU for inputs whose rows list strictly increasing
+// columns and whose non-terminals all have a terminal capacity; *taken says
+// whether it built the problem (otherwise the host reduction must run).
+// mem_kind says where row_ptr, col and c live; rp_dev / col_dev, when non-null,
+// are an input structure already on the device (owned by the caller).
+pirmcut_status reduce_graph_device(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                                   const double* c, int32_t s, int32_t t, int format_req,
+                                   int mem_kind, void* stream, const int64_t* rp_dev,
+                                   const int32_t* col_dev, HostGraph* g, DeviceGraph* dg,
+                                   bool* taken, std::string* err);
 
 // Record the message returned by pirmcut_last_error(NULL) for calls that have
 // no context.

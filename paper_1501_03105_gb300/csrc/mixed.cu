@@ -907,7 +907,7 @@ cudaError_t mixed_alloc(Ctx& c) {
   if (c.O) return cudaSuccess;
   const size_t nt = size_t(c.nt);
   const size_t ng = c.format == PIRMCUT_FORMAT_DIA ? size_t(c.K) * nt
-                                                    : (c.hg.col.empty() ? 1 : c.hg.col.size());
+                                                    : (c.hg.nnz ? size_t(c.hg.nnz) : 1);
   cudaError_t e = cudaSuccess;
   auto A = [&](void** p, size_t bytes) {
     if (e == cudaSuccess) e = cudaMalloc(p, bytes ? bytes : 1);

@@ -427,7 +427,7 @@ const double* reweight_point(const Ctx& c, bool initial) {
 cudaError_t mlp_alloc(Ctx& c) {
   if (c.mlp.master) return cudaSuccess;
   MlpBuf& b = c.mlp;
-  const size_t ng = c.format == PIRMCUT_FORMAT_DIA ? size_t(c.K) * c.nt : c.hg.col.size();
+  const size_t ng = c.format == PIRMCUT_FORMAT_DIA ? size_t(c.K) * c.nt : size_t(c.hg.nnz);
   cudaError_t e = cudaSuccess;
   auto A = [&](void** p, size_t bytes) {
     if (e == cudaSuccess) e = cudaMalloc(p, bytes ? bytes : 16);
@@ -504,7 +504,7 @@ cudaError_t mlp_get_features(Ctx& c, float* host) {
 
 // Before the reweighting of a step: keep x^(l-1) and g^(l-1).
 int enqueue_mlp_pre(Ctx& c, cudaStream_t st) {
-  const size_t ng = c.format == PIRMCUT_FORMAT_DIA ? size_t(c.K) * c.nt : c.hg.col.size();
+  const size_t ng = c.format == PIRMCUT_FORMAT_DIA ? size_t(c.K) * c.nt : size_t(c.hg.nnz);
   cudaMemcpyAsync(c.mlp.xprev, c.x, sizeof(double) * size_t(c.nt), cudaMemcpyDeviceToDevice, st);
   if (ng)
     cudaMemcpyAsync(c.mlp.gprev, c.format == PIRMCUT_FORMAT_DIA ? c.gdia : c.gval,

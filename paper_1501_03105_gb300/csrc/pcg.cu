@@ -514,7 +514,7 @@ int enqueue_reweight(Ctx& c, cudaStream_t st, bool initial) {
   const double* cap = c.format == PIRMCUT_FORMAT_DIA ? c.cdia : c.cval;
   const size_t gbytes = sizeof(double) * (c.format == PIRMCUT_FORMAT_DIA
                                               ? size_t(c.K) * c.nt
-                                              : size_t(c.hg.rp.empty() ? 0 : c.hg.rp.back()));
+                                              : size_t(c.hg.nnz));
   if (initial) {
     cudaMemcpyAsync(g, cap, gbytes, cudaMemcpyDeviceToDevice, st);
     return 0;

@@ -179,6 +179,36 @@ extern "C" pirmcut_status pirmcut_cut_two_level(pirmcut_ctx* h, uint8_t* side, d
     return fail(PIRMCUT_EINVAL, "unknown mem_kind");
   cudaError_t e = sweep_alloc(c);
   if (e != cudaSuccess) return cuda(e, "sweep buffers");
+  // the contraction reads the reduced graph on the host: a problem built on
+  // the device is copied back once
+  if (c.device_reduced && c.hg.cs.empty() && c.nt > 0) {
+    HostGraph& hg = c.hg;
+    const size_t nt = size_t(c.nt);
+    hg.cs.resize(nt);
+    hg.ct.resize(nt);
+    e = cudaMemcpyAsync(hg.cs.data(), c.cs, sizeof(double) * nt, cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hg.ct.data(), c.ct, sizeof(double) * nt, cudaMemcpyDeviceToHost, c.stream);
+    if (c.format == PIRMCUT_FORMAT_DIA) {
+      hg.cdia.resize(size_t(c.K) * nt);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hg.cdia.data(), c.cdia, sizeof(double) * hg.cdia.size(), cudaMemcpyDeviceToHost, c.stream);
+    } else {
+      hg.rp.resize(nt + 1);
+      hg.col.resize(size_t(hg.nnz));
+      hg.cval.resize(size_t(hg.nnz));
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hg.rp.data(), c.rp, sizeof(int64_t) * (nt + 1), cudaMemcpyDeviceToHost, c.stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hg.col.data(), c.col, sizeof(int32_t) * hg.col.size(), cudaMemcpyDeviceToHost, c.stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hg.cval.data(), c.cval, sizeof(double) * hg.cval.size(), cudaMemcpyDeviceToHost, c.stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) {
+      hg.cs.clear();
+      return cuda(e, "reading the reduced graph");
+    }
+  }
   const HostGraph& g = c.hg;
   const int64_t nt = c.nt;
   // --- K-means on x (s and t included: x_s = 1, x_t = 0)
