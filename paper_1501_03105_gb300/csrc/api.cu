@@ -612,21 +612,21 @@ pirmcut_status pirmcut_update_weights(pirmcut_ctx* h, const double* cnew, int me
         dg.release();
         return fail(h, PIRMCUT_EINVAL, "the new capacities change the stored structure");
       }
-      if (c.format == PIRMCUT_FORMAT_DIA) {
-        cudaFree(c.cdia);
-        c.cdia = dg.cdia;
-        dg.cdia = nullptr;
-      } else {
-        cudaFree(c.cval);
-        c.cval = dg.cval;
-        dg.cval = nullptr;
-      }
-      cudaFree(c.cs);
-      cudaFree(c.ct);
-      c.cs = dg.cs;
-      c.ct = dg.ct;
-      dg.cs = dg.ct = nullptr;
-      dg.release();  // the reduced structure arrays of the rebuild (same as c's)
+      // copy into the context's arrays: captured graphs hold their addresses
+      cudaError_t ce = cudaSuccess;
+      if (c.format == PIRMCUT_FORMAT_DIA)
+        ce = cudaMemcpyAsync(c.cdia, dg.cdia, sizeof(double) * size_t(c.K) * size_t(c.nt),
+                             cudaMemcpyDeviceToDevice, c.stream);
+      else
+        ce = cudaMemcpyAsync(c.cval, dg.cval, sizeof(double) * size_t(c.hg.nnz),
+                             cudaMemcpyDeviceToDevice, c.stream);
+      if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(c.cs, dg.cs, sizeof(double) * size_t(c.nt), cudaMemcpyDeviceToDevice, c.stream);
+      if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(c.ct, dg.ct, sizeof(double) * size_t(c.nt), cudaMemcpyDeviceToDevice, c.stream);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(c.stream);
+      dg.release();
+      if (ce != cudaSuccess) return cuda_fail(h, ce, "updating the capacities");
       c.hg = std::move(ng);
       if (c.g_cut) {
         cudaGraphExecDestroy(c.g_cut);
