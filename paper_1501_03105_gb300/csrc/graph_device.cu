@@ -36,14 +36,16 @@ __device__ __forceinline__ int64_t gtid() { return int64_t(blockIdx.x) * blockDi
 __device__ __forceinline__ int64_t gstride() { return int64_t(gridDim.x) * blockDim.x; }
 __device__ __forceinline__ int64_t red(int64_t v, int32_t s, int32_t t) { return v - (v > s) - (v > t); }
 
-// Per input row: bounds of the row, validity of its entries, strict order of
-// its columns; non-terminal rows also count their non-terminal entries and
-// take their terminal capacities (one entry each at most, by the order).
+// Per non-terminal input row: bounds of the row, validity of its entries,
+// strict order of its columns, the count of its non-terminal entries and its
+// terminal capacities (one entry each at most, by the order).  The rows of s
+// and t, which can hold an entry per vertex, are k_terminal_rows' work.
 __global__ void __launch_bounds__(kThreads)
 k_rows(int64_t n, int64_t nnz, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
        const double* __restrict__ c, int32_t s, int32_t t, int64_t* __restrict__ cnt,
        double* __restrict__ cs, double* __restrict__ ct, unsigned int* flags) {
   for (int64_t v = gtid(); v < n; v += gstride()) {
+    if (v == s || v == t) continue;
     const int64_t b = rp[v], e = rp[v + 1];
     if (b < 0 || e < b || e > nnz) {
       atomicOr(flags, kFlagRowPtr);
@@ -66,12 +68,10 @@ k_rows(int64_t n, int64_t nnz, const int64_t* __restrict__ rp, const int32_t* __
       else ++m;
     }
     if (f) atomicOr(flags, f);
-    if (v != s && v != t) {
-      const int64_t i = red(v, s, t);
-      cnt[i] = m;
-      cs[i] = a;
-      ct[i] = z;
-    }
+    const int64_t i = red(v, s, t);
+    cnt[i] = m;
+    cs[i] = a;
+    ct[i] = z;
   }
 }
 
@@ -167,18 +167,32 @@ k_fill(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ co
   }
 }
 
-// Rows s and t: c(s, v) as seen from s, c(v, t) as seen from t, and c(s, t)
-// from both sides (one entry per column, by the order).
+// Rows s and t, one entry per thread: their bounds, the validity and strict
+// order of their entries (as k_rows checks the other rows), then c(s, v) as
+// seen from s, c(v, t) as seen from t, and c(s, t) from both sides (one entry
+// per column, by the order).
 __global__ void __launch_bounds__(kThreads)
-k_terminal_rows(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                const double* __restrict__ c, int32_t s, int32_t t, double* __restrict__ cs_from_s,
-                double* __restrict__ ct_from_t, double* __restrict__ cst /* [2] */) {
+k_terminal_rows(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
+                const int32_t* __restrict__ col, const double* __restrict__ c, int32_t s,
+                int32_t t, double* __restrict__ cs_from_s, double* __restrict__ ct_from_t,
+                double* __restrict__ cst /* [2] */, unsigned int* flags) {
   const int64_t bs = rp[s], es = rp[s + 1], bt = rp[t], et = rp[t + 1];
+  if (bs < 0 || es < bs || es > nnz || bt < 0 || et < bt || et > nnz) {
+    if (gtid() == 0) atomicOr(flags, kFlagRowPtr);
+    return;
+  }
   const int64_t ls = es - bs, total = ls + (et - bt);
   for (int64_t q = gtid(); q < total; q += gstride()) {
     const bool from_s = q < ls;
     const int64_t k = from_s ? bs + q : bt + (q - ls);
+    const int64_t row = from_s ? s : t, first = from_s ? bs : bt;
     const int32_t u = col[k];
+    const double w = c[k];
+    if (u < 0 || u >= n || u == row || !isfinite(w) || w < 0.0) {
+      atomicOr(flags, kFlagInput);
+      continue;
+    }
+    if (k > first && col[k - 1] >= u) atomicOr(flags, kFlagOrder);
     if (from_s) {
       if (u == t) cst[0] = c[k];
       else cs_from_s[red(u, s, t)] = c[k];
@@ -411,8 +425,8 @@ pirmcut_status reduce_graph_device(int64_t n, const int64_t* row_ptr, const int3
   if ((e = dmalloc(&out.col, size_t(mnt))) != cudaSuccess || (e = dmalloc(&out.cval, size_t(mnt))) != cudaSuccess)
     return cuda_error(e, "cudaMalloc");
   k_fill<<<grid_for(n), kThreads, 0, st>>>(n, out.in_rp, out.in_col, dc, s, t, out.rp, out.col, out.cval);
-  k_terminal_rows<<<grid_for(nt), kThreads, 0, st>>>(out.in_rp, out.in_col, dc, s, t, d_cs_s, d_ct_t,
-                                                      d_small);
+  k_terminal_rows<<<grid_for(nt), kThreads, 0, st>>>(n, nnz, out.in_rp, out.in_col, dc, s, t, d_cs_s,
+                                                      d_ct_t, d_small, d_flags);
   k_check<<<grid_for(nt), kThreads, 0, st>>>(nt, out.rp, out.col, out.cval, out.cs, out.ct, d_cs_s,
                                              d_ct_t, d_flags);
   k_sum_chunks<<<1, kSumChunks, 0, st>>>(out.cs, nt, d_small + 2);
