@@ -646,6 +646,12 @@ def main():
         e_iters = 0
         reps = max(1, min(args.steps, 3))
         opt = B.pirmcut_default_options(pcg_tol=PCG_TOL, graph_launch=int(args.launch == "graph"))
+        # one untimed pass: the first call of a process loads the library's
+        # device code (a one-time cost, like the device-timed warm-up steps)
+        h = B.pirmcut_create(g.n, g.row_ptr, g.col, g.c, g.s, g.t, opt, stream)
+        B.pirmcut_solve(h, T_STEPS, eps_arr)
+        B.pirmcut_cut(h, side_host)
+        B.pirmcut_destroy(h)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -661,7 +667,8 @@ def main():
         e_units, dt = job_totals(ne * e_iters, dt, dist, "cuda")
         e2e = {"value": e_units / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * dt / reps,
-               "includes": "create (host CSR upload + packing), solve, sweep cut, side D2H, destroy"}
+               "includes": "create (host CSR upload, validation and packing on the GPU), solve, "
+                           "sweep cut, side D2H, destroy; one untimed pass first"}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == "grid2048":
