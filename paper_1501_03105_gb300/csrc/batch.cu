@@ -940,6 +940,7 @@ pirmcut_status pirmcut_batch_cut(pirmcut_batch* h, int index, uint8_t* side, dou
     BCK(h, sweep_alloc(v), "sweep buffers");
     v.nt = keep;
   }
+  BCK(h, sweep_set_heavy(v, b.hg[index].rp.data()), "sweep rows");  // this instance's hubs
   int kernels = 0;
   BCK(h, enqueue_sweep(v, b.stream, false, &kernels), "sweep");
   b.launches += kernels;

@@ -1,6 +1,7 @@
 // The solver context behind the opaque pirmcut_ctx handle.
 #pragma once
 
+#include <climits>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -63,7 +64,12 @@ struct SweepBuf {
   double* result = nullptr;   // [value_prefix, value_exact, tau, k]
   int nblocks_sort = 0;
   int ntiles = 0;
+  // CSR rows of high degree, one block each in the per-row sweep kernels
+  int32_t* heavy = nullptr;   // row ids (at most kSweepHeavyMax), ascending
+  int n_heavy = 0;
+  int64_t heavy_deg = INT64_MAX;  // rows with more entries than this are heavy
 };
+constexpr int kSweepHeavyMax = 1024;
 
 // Learned warm start (per-node MLP, 6 -> 64 -> 64 -> 1).
 constexpr int kMlpFeatures = 6;
@@ -229,6 +235,9 @@ cudaError_t enqueue_sweep(Ctx& c, cudaStream_t st, bool record, int* nodes);
 cudaError_t enqueue_cut_value(Ctx& c, cudaStream_t st, const uint8_t* side_red);
 cudaError_t build_cut_graph(Ctx& c, cudaGraphExec_t* out, int* nodes);
 cudaError_t launch_side_full(Ctx& c, uint8_t* side_full);
+// The heavy rows of a CSR problem from its host row pointers (global entry
+// offsets for a batch instance's view).
+cudaError_t sweep_set_heavy(Ctx& c, const int64_t* host_rp);
 void sweep_free(Ctx& c);
 
 }  // namespace pirmcut

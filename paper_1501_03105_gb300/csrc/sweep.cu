@@ -16,7 +16,11 @@
 //  6. side, threshold, and the exact FP64 cut value of the chosen side.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <climits>
 #include <cmath>
+#include <utility>
+#include <vector>
 
 #include "ctx.h"
 
@@ -258,11 +262,26 @@ __global__ void __launch_bounds__(kThreads)
 k_delta_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
             const double* __restrict__ c, const double* __restrict__ cs,
             const double* __restrict__ ct, const int32_t* __restrict__ rank,
-            double* __restrict__ delta) {
+            double* __restrict__ delta, int64_t heavy_deg, const int32_t* __restrict__ heavy,
+            int light_blocks) {
+  if (int(blockIdx.x) >= light_blocks) {  // one heavy row per block
+    const int64_t i = heavy[blockIdx.x - light_blocks];
+    const int32_t ri = rank[i];
+    double acc = 0.0;
+    for (int64_t e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x) {
+      const double w = c[e];
+      acc += (ri < rank[col[e]]) ? w : -w;
+    }
+    double v[1] = {acc};
+    block_sum<1>(v);
+    if (threadIdx.x == 0) delta[i] = (ct[i] - cs[i]) + v[0];
+    return;
+  }
   const int lane = threadIdx.x % G;
   const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
-  const int64_t ng = gstride() / G;
+  const int64_t ng = int64_t(light_blocks) * blockDim.x / G;
   for (int64_t i = gtid() / G; i < nt; i += ng) {
+    if (rp[i + 1] - rp[i] > heavy_deg) continue;  // the group agrees: same row
     const int32_t ri = rank[i];
     double acc = 0.0;
     for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) {
@@ -443,21 +462,33 @@ k_cut_dia(DiaDesc d, const double* __restrict__ c, CutArgs a) {
 template <int G>
 __global__ void __launch_bounds__(kThreads)
 k_cut_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-          const double* __restrict__ c, CutArgs a) {
-  const int lane = threadIdx.x % G;
-  const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
-  const int64_t ng = gstride() / G;
+          const double* __restrict__ c, CutArgs a, int64_t heavy_deg,
+          const int32_t* __restrict__ heavy, int light_blocks) {
   double acc = 0.0;
-  for (int64_t i = gtid() / G; i < nt; i += ng) {
+  if (int(blockIdx.x) >= light_blocks) {  // one heavy row per block
+    const int64_t i = heavy[blockIdx.x - light_blocks];
     const uint8_t si = a.side[i];
-    double t = 0.0;
-    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) {
+    for (int64_t e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x) {
       const int32_t j = col[e];
-      if (j > i && a.side[j] != si) t += c[e];
+      if (j > i && a.side[j] != si) acc += c[e];
     }
+    if (threadIdx.x == 0) acc += si ? a.ct[i] : a.cs[i];
+  } else {
+    const int lane = threadIdx.x % G;
+    const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
+    const int64_t ng = int64_t(light_blocks) * blockDim.x / G;
+    for (int64_t i = gtid() / G; i < nt; i += ng) {
+      if (rp[i + 1] - rp[i] > heavy_deg) continue;
+      const uint8_t si = a.side[i];
+      double t = 0.0;
+      for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) {
+        const int32_t j = col[e];
+        if (j > i && a.side[j] != si) t += c[e];
+      }
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) t += __shfl_down_sync(mask, t, o, G);
-    if (lane == 0) acc += t + (si ? a.ct[i] : a.cs[i]);
+      for (int o = G / 2; o > 0; o >>= 1) t += __shfl_down_sync(mask, t, o, G);
+      if (lane == 0) acc += t + (si ? a.ct[i] : a.cs[i]);
+    }
   }
   cut_finish(a, acc);
 }
@@ -519,7 +550,8 @@ cudaError_t sweep_alloc(Ctx& c) {
   A((void**)&b.digit_tot, sizeof(uint32_t) * 256);
   A((void**)&b.rank, sizeof(int32_t) * nt);
   A((void**)&b.delta, sizeof(double) * nt);
-  A((void**)&b.blk, sizeof(double) * (size_t(b.ntiles) + kMaxBlocks) * 2);
+  A((void**)&b.blk, sizeof(double) * ((size_t(b.ntiles) + kMaxBlocks) * 2 + kSweepHeavyMax));
+  A((void**)&b.heavy, sizeof(int32_t) * kSweepHeavyMax);
   A((void**)&b.blk_k, sizeof(int64_t) * (size_t(b.ntiles) + 1));
   A((void**)&b.side_red, nt);
   A((void**)&b.result, sizeof(double) * 4 + sizeof(unsigned int) * 8);
@@ -529,12 +561,52 @@ cudaError_t sweep_alloc(Ctx& c) {
     return e;
   }
   b.cap = nt;
-  return cudaSuccess;
+  b.n_heavy = 0;
+  b.heavy_deg = INT64_MAX;
+  if (c.format == PIRMCUT_FORMAT_CSR && c.rp && !c.hg.rp.empty()) e = sweep_set_heavy(c, c.hg.rp.data());
+  else if (c.format == PIRMCUT_FORMAT_CSR && c.rp && c.hg.nnz > 0) {
+    hvec<int64_t> hrp(size_t(nt) + 1);  // problem built on the device: its row pointers
+    e = cudaMemcpy(hrp.data(), c.rp, sizeof(int64_t) * (size_t(nt) + 1), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = sweep_set_heavy(c, hrp.data());
+  }
+  return e;
+}
+
+// Rows with more than max(512, 16 x mean) entries, at most kSweepHeavyMax of
+// them (the longest), listed in ascending order.
+cudaError_t sweep_set_heavy(Ctx& c, const int64_t* rp) {
+  SweepBuf& b = c.sw;
+  const int64_t nt = c.nt;
+  const int64_t mean = nt ? (rp[nt] - rp[0]) / nt : 0;
+  int64_t thr = std::max<int64_t>(512, 16 * mean);
+  std::vector<std::pair<int64_t, int32_t>> rows;  // (degree, row)
+  for (int64_t i = 0; i < nt; ++i) {
+    const int64_t d = rp[i + 1] - rp[i];
+    if (d > thr) rows.push_back({d, int32_t(i)});
+  }
+  if (int64_t(rows.size()) > kSweepHeavyMax) {
+    std::nth_element(rows.begin(), rows.begin() + kSweepHeavyMax, rows.end(),
+                     [](const std::pair<int64_t, int32_t>& x, const std::pair<int64_t, int32_t>& y) {
+                       return x.first > y.first;
+                     });
+    thr = rows[kSweepHeavyMax].first;  // heavy: strictly longer than the first one left out
+    std::vector<std::pair<int64_t, int32_t>> keep;
+    for (const auto& r : rows)
+      if (r.first > thr) keep.push_back(r);
+    rows.swap(keep);
+  }
+  std::vector<int32_t> ids;
+  for (const auto& r : rows) ids.push_back(r.second);
+  std::sort(ids.begin(), ids.end());
+  b.n_heavy = int(ids.size());
+  b.heavy_deg = thr;
+  if (ids.empty()) return cudaSuccess;
+  return cudaMemcpy(b.heavy, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice);
 }
 
 void sweep_free(Ctx& c) {
   SweepBuf& b = c.sw;
-  void* ps[] = {b.keys[0], b.keys[1], b.vals[0], b.vals[1], b.hist, b.digit_tot, b.rank,
+  void* ps[] = {b.heavy, b.keys[0], b.keys[1], b.vals[0], b.vals[1], b.hist, b.digit_tot, b.rank,
                 b.delta, b.blk, b.blk_k, b.side_red, b.result};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -571,8 +643,9 @@ cudaError_t enqueue_sweep(Ctx& c, cudaStream_t st, bool record, int* nodes) {
   if (c.format == PIRMCUT_FORMAT_DIA) {
     SW_DISPATCH_K(c.K, (k_delta_dia<KK><<<rgrid, kThreads, 0, st>>>(c.dd, c.cdia, c.cs, c.ct, b.rank, b.delta)));
   } else {
-    SW_DISPATCH_G(c.group, (k_delta_csr<GG><<<rgrid, kThreads, 0, st>>>(c.nt, c.rp, c.col, c.cval, c.cs,
-                                                                          c.ct, b.rank, b.delta)));
+    SW_DISPATCH_G(c.group, (k_delta_csr<GG><<<rgrid + b.n_heavy, kThreads, 0, st>>>(
+                                c.nt, c.rp, c.col, c.cval, c.cs, c.ct, b.rank, b.delta, b.heavy_deg,
+                                b.heavy, rgrid)));
   }
   ++n_nodes;
   k_tile_sum<<<ntiles, kThreads, 0, st>>>(nt, order, b.delta, b.blk);
@@ -595,7 +668,8 @@ cudaError_t enqueue_sweep(Ctx& c, cudaStream_t st, bool record, int* nodes) {
   if (c.format == PIRMCUT_FORMAT_DIA) {
     SW_DISPATCH_K(c.K, (k_cut_dia<KK><<<rgrid, kThreads, 0, st>>>(c.dd, c.cdia, a)));
   } else {
-    SW_DISPATCH_G(c.group, (k_cut_csr<GG><<<rgrid, kThreads, 0, st>>>(c.nt, c.rp, c.col, c.cval, a)));
+    SW_DISPATCH_G(c.group, (k_cut_csr<GG><<<rgrid + b.n_heavy, kThreads, 0, st>>>(
+                                c.nt, c.rp, c.col, c.cval, a, b.heavy_deg, b.heavy, rgrid)));
   }
   ++n_nodes;
   if (nodes) *nodes = n_nodes;
@@ -623,7 +697,8 @@ cudaError_t enqueue_cut_value(Ctx& c, cudaStream_t st, const uint8_t* side_red) 
   if (c.format == PIRMCUT_FORMAT_DIA) {
     SW_DISPATCH_K(c.K, (k_cut_dia<KK><<<rgrid, kThreads, 0, st>>>(c.dd, c.cdia, a)));
   } else {
-    SW_DISPATCH_G(c.group, (k_cut_csr<GG><<<rgrid, kThreads, 0, st>>>(c.nt, c.rp, c.col, c.cval, a)));
+    SW_DISPATCH_G(c.group, (k_cut_csr<GG><<<rgrid + b.n_heavy, kThreads, 0, st>>>(
+                                c.nt, c.rp, c.col, c.cval, a, b.heavy_deg, b.heavy, rgrid)));
   }
   return cudaGetLastError();
 }

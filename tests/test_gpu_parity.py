@@ -252,6 +252,39 @@ def test_live_spmv_timing_counts_every_working_launch(P, precision):
         assert a.spmv_timing() == (0.0, 0)       # graph launches are not timed
 
 
+def _hub_graph(n_nt=2800, seed=31):
+    """A sparse random graph plus one hub joined to every other non-terminal
+    (a row far longer than the rest, as in power-law FlowImprove graphs)."""
+    g = gen.random_graph(n_nt, 4.0 / n_nt, seed)
+    rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    m = rows < g.col
+    u, v, c = rows[m], g.col[m].astype(np.int64), g.c[m]
+    hub = 0
+    others = np.setdiff1d(np.arange(n_nt), np.r_[hub, v[u == hub], u[v == hub]])
+    u = np.r_[u, np.full(others.shape, hub)]
+    v = np.r_[v, others]
+    c = np.r_[c, np.random.default_rng(seed).uniform(0.01, 0.05, others.shape[0])]
+    rp, col, cc = gen.csr_from_edges(g.n, u, v, c)
+    return gen.Graph(g.n, rp, col, cc, g.s, g.t)
+
+
+def test_sweep_with_a_hub_row(P):
+    """Rows far longer than the mean are swept by a block each."""
+    g = _hub_graph()
+    prob = O.Problem.from_graph(g)
+    assert np.diff(g.row_ptr).max() > 2000
+    xs, _ = O.irls(prob, 8)
+    with solver(P, g) as s:
+        s.set_x(xs[-1])
+        side, value, tau = s.cut()
+    check_cut(prob, xs[-1], side, value, tau)
+    with P.Batch([g, gen.random_graph(40, 0.1, 12), g], pcg_tol=1e-13) as b:
+        b.solve(8, O.eps_schedule(8))
+        for i in (0, 2):
+            side_b, value_b, tau_b = b.cut(i)
+            assert abs(value_b - O.sweep_cut(prob, b.get_x(i))["value"]) <= 1e-9 * value_b
+
+
 def test_one_vertex_and_no_source_edges(P):
     """n = 3 (s-v-t) closed form; and b = 0 (no s edges) gives x = 0."""
     rp, col, c = gen.csr_from_edges(3, [0, 1], [1, 2], [3.0, 1.0])
