@@ -57,10 +57,10 @@ typedef enum {
 
 enum { PIRMCUT_MEM_HOST = 0, PIRMCUT_MEM_DEVICE = 1 };
 
-/* Reweighting form.  NORTH_STAR: g_e = c_e / sqrt(d_e^2 + eps^2), d = x_u - x_v.
+/* Reweighting form.  WEIGHTED_L1: g_e = c_e / sqrt(d_e^2 + eps^2), d = x_u - x_v.
  * PAPER: the literal Eq. (define-reweight-vector) + Eq. (reweighted-laplacian),
  * w_e = sqrt((c_e d_e)^2 + eps^2) and g_e = c_e^2 / w_e. */
-enum { PIRMCUT_REWEIGHT_NORTH_STAR = 0, PIRMCUT_REWEIGHT_PAPER = 1 };
+enum { PIRMCUT_REWEIGHT_WEIGHTED_L1 = 0, PIRMCUT_REWEIGHT_PAPER = 1 };
 
 /* Arithmetic of the PCG.  FP64: every vector, matrix value and reduction in
  * FP64.  MIXED: FP32 matrix values and vectors in the inner PCG with
@@ -113,7 +113,7 @@ typedef struct {
                           started an inner solve); 0 for FP64                 */
 } pirmcut_step_info;
 
-/* Fill *opt with the defaults: NORTH_STAR, FP64, pcg_tol 1e-10,
+/* Fill *opt with the defaults: WEIGHTED_L1, FP64, pcg_tol 1e-10,
  * pcg_max_iter 20000, warm_start 1, FORMAT_AUTO, track_cut 0, graph_launch 1,
  * inner_tol 1e-5, time_spmv 0, reduce_on_host 0.  With MIXED, pcg_iters counts FP32 inner iterations, at most
  * min(pcg_max_iter, 2000) per refinement cycle and 64 cycles per system. */
@@ -273,7 +273,7 @@ pirmcut_status pirmcut_cut_two_level(pirmcut_ctx* ctx, uint8_t* side, double* va
  *   alpha = d^T r / d^T L~ d,  r = b - L~ x^(l-1)   (alpha = 0 if d^T L~ d <= 0).
  * E is the error norm that CG minimises, so the learned start is never
  * worse than x^(l-1) in that norm: the plain warm start is the fallback and
- * the judge.  The conductances always come from x^(l-1), so the solved system
+ * the yardstick.  The conductances always come from x^(l-1), so the solved system
  * is unchanged and every result keeps the solver's tolerance.
  * The features of node v, all of step l:
  *   f0 x^(l-1)_v;

@@ -10,7 +10,7 @@ sweep cut) and :mod:`oracle.exact` for the exact references (brute-force cut
 enumeration and an augmenting-path max-flow).
 """
 from .pirmcut import (  # noqa: F401
-    NORTH_STAR,
+    WEIGHTED_L1,
     PAPER,
     Problem,
     eps_schedule,

@@ -14,7 +14,7 @@ primitives used as single steps: sparse matrix products, a sparse direct solve
 Readings of points the paper leaves open (each one is also listed in the
 design notes of the repository):
 
-* reweighting form: the default ``NORTH_STAR`` form gives edge e the
+* reweighting form: the default ``WEIGHTED_L1`` form gives edge e the
   conductance g_e = c_e / sqrt(d_e^2 + eps^2), d = B x.  The ``PAPER`` form is
   the literal Eq. (define-reweight-vector) + Eq. (reweighted-laplacian):
   w_e = sqrt((C B x)_e^2 + eps^2) and g_e = c_e^2 / w_e.
@@ -41,7 +41,7 @@ import scipy.sparse as sp
 import scipy.sparse.csgraph as csgraph
 import scipy.sparse.linalg as spla
 
-NORTH_STAR = 0
+WEIGHTED_L1 = 0
 PAPER = 1
 
 
@@ -146,18 +146,18 @@ def initial_conductance(prob: Problem) -> np.ndarray:
     return prob.cap.copy()
 
 
-def reweight(prob: Problem, x: np.ndarray, eps: float, form: int = NORTH_STAR) -> np.ndarray:
+def reweight(prob: Problem, x: np.ndarray, eps: float, form: int = WEIGHTED_L1) -> np.ndarray:
     """Per-edge conductance of the next WLS (Step 1, Eq. define-reweight-vector).
 
     PAPER form: w = sqrt((C B x)^2 + eps^2) and the Laplacian weight is the
     diagonal of C W^-1 C (Eq. reweighted-laplacian), i.e. c^2 / w.
-    NORTH_STAR form: c / sqrt((B x)^2 + eps^2).
+    WEIGHTED_L1 form: c / sqrt((B x)^2 + eps^2).
     """
     d = prob.B @ x
     if form == PAPER:
         w = np.sqrt((prob.cap * d) ** 2 + eps ** 2)
         return prob.cap * prob.cap / w
-    if form == NORTH_STAR:
+    if form == WEIGHTED_L1:
         return prob.cap / np.sqrt(d ** 2 + eps ** 2)
     raise ValueError("unknown reweighting form")
 
@@ -241,7 +241,7 @@ def wls_step(prob: Problem, g: np.ndarray, solver: str = "direct", v0=None,
     return x, info
 
 
-def irls(prob: Problem, T: int, eps=None, form: int = NORTH_STAR, solver: str = "direct",
+def irls(prob: Problem, T: int, eps=None, form: int = WEIGHTED_L1, solver: str = "direct",
          tol: float = 1e-12, maxit: int = 1000000, warm_start: bool = True):
     """The IRLS loop (Section 2.1 and Algorithm 1, rounding excluded).
 
@@ -267,11 +267,11 @@ def irls(prob: Problem, T: int, eps=None, form: int = NORTH_STAR, solver: str = 
     return xs, infos
 
 
-def smoothed_objective(prob: Problem, x: np.ndarray, eps: float, form: int = NORTH_STAR) -> float:
+def smoothed_objective(prob: Problem, x: np.ndarray, eps: float, form: int = WEIGHTED_L1) -> float:
     """Smoothed l1 objective (Eq. l1-min-smooth-version).
 
-    PAPER: sum_e sqrt((C B x)_e^2 + eps^2).  NORTH_STAR: sum_e c_e sqrt((B x)_e^2 + eps^2),
-    the function whose majorise-minimise iteration is the NORTH_STAR reweighting.
+    PAPER: sum_e sqrt((C B x)_e^2 + eps^2).  WEIGHTED_L1: sum_e c_e sqrt((B x)_e^2 + eps^2),
+    the function whose majorise-minimise iteration is the WEIGHTED_L1 reweighting.
     """
     d = prob.B @ x
     if form == PAPER:

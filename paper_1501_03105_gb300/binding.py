@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpirmcut.so")
 
 MEM_HOST, MEM_DEVICE = 0, 1
-REWEIGHT_NORTH_STAR, REWEIGHT_PAPER = 0, 1
+REWEIGHT_WEIGHTED_L1, REWEIGHT_PAPER = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 FORMAT_AUTO, FORMAT_DIA, FORMAT_CSR = 0, 1, 2
 MLP_PREDICT, MLP_TRAIN = 1, 2

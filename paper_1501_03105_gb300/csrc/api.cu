@@ -60,7 +60,7 @@ void free_device(Ctx& c) {
 }
 
 pirmcut_status check_options(const pirmcut_options& o, std::string* msg) {
-  if (o.reweight_form != PIRMCUT_REWEIGHT_NORTH_STAR && o.reweight_form != PIRMCUT_REWEIGHT_PAPER) {
+  if (o.reweight_form != PIRMCUT_REWEIGHT_WEIGHTED_L1 && o.reweight_form != PIRMCUT_REWEIGHT_PAPER) {
     *msg = "unknown reweight_form";
     return PIRMCUT_EINVAL;
   }
@@ -408,7 +408,7 @@ extern "C" {
 
 void pirmcut_default_options(pirmcut_options* opt) {
   if (!opt) return;
-  opt->reweight_form = PIRMCUT_REWEIGHT_NORTH_STAR;
+  opt->reweight_form = PIRMCUT_REWEIGHT_WEIGHTED_L1;
   opt->precision = PIRMCUT_PREC_FP64;
   opt->pcg_tol = 1e-10;
   opt->pcg_max_iter = 20000;

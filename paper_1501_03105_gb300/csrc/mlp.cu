@@ -16,7 +16,7 @@
 // (FP64): alpha = delta^T r / delta^T L~ delta with r = b - L~ x^(l-1).  E is
 // the error norm CG minimises, so the learned start is never worse than the
 // plain warm start (alpha = 0 is always available): x^(l-1) is both the
-// fallback and the judge.  The reweighting point stays x^(l-1) (in xprev).
+// fallback and the yardstick.  The reweighting point stays x^(l-1) (in xprev).
 // Training runs on the trajectory the solver itself produces: after a step,
 // minibatches of nodes drawn by a counter-based hash go through hand-written
 // forward/backward kernels; each block accumulates its samples' gradients in

@@ -49,7 +49,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_default_options(lib):
     from paper_1501_03105_gb300 import binding as B
     o = B.pirmcut_default_options()
-    assert o.reweight_form == B.REWEIGHT_NORTH_STAR and o.precision == B.PREC_FP64
+    assert o.reweight_form == B.REWEIGHT_WEIGHTED_L1 and o.precision == B.PREC_FP64
     assert o.pcg_tol == 1e-10 and o.pcg_max_iter == 20000 and o.warm_start == 1
 
 

@@ -14,14 +14,14 @@ import oracle.pirmcut as OP
 from tests import test_oracle_pins as pins
 
 
-def _reweight_no_square(prob, x, eps, form=OP.NORTH_STAR):
+def _reweight_no_square(prob, x, eps, form=OP.WEIGHTED_L1):
     d = prob.B @ x
     if form == OP.PAPER:
         return prob.cap * prob.cap / np.sqrt(np.abs(prob.cap * d) + eps ** 2)
     return prob.cap / np.sqrt(np.abs(d) + eps ** 2)
 
 
-def _reweight_paper_one_c(prob, x, eps, form=OP.NORTH_STAR):
+def _reweight_paper_one_c(prob, x, eps, form=OP.WEIGHTED_L1):
     d = prob.B @ x
     if form == OP.PAPER:
         return prob.cap / np.sqrt((prob.cap * d) ** 2 + eps ** 2)
@@ -76,7 +76,7 @@ def _cut_value_count_internal(prob, side):
     return float(np.sum(prob.cap[crossing]) + 0.5 * np.sum(prob.cap[inside]))
 
 
-def _objective_no_eps(prob, x, eps, form=OP.NORTH_STAR):
+def _objective_no_eps(prob, x, eps, form=OP.WEIGHTED_L1):
     d = prob.B @ x
     if form == OP.PAPER:
         return float(np.sum(np.abs(prob.cap * d)))
@@ -100,12 +100,12 @@ MUTANTS = {
 PIN_TESTS = [
     lambda: [pins.test_x0_single_vertex_divider(a, b) for a, b in [(3.0, 1.0), (0.25, 2.0)]],
     pins.test_x0_series_chain_voltage_divider,
-    lambda: [pins.test_one_irls_step_closed_form(f, 3.0, 1.0, 0.75, 0.1) for f in (OP.NORTH_STAR, OP.PAPER)],
+    lambda: [pins.test_one_irls_step_closed_form(f, 3.0, 1.0, 0.75, 0.1) for f in (OP.WEIGHTED_L1, OP.PAPER)],
     pins.test_reduced_system_hand_example,
     lambda: [pins.test_smoothed_objective_closed_form(v, e) for v, e in [(0.3, 0.1), (0.5, 0.0)]],
-    lambda: [pins.test_laplacian_structure(f) for f in (OP.NORTH_STAR, OP.PAPER)],
+    lambda: [pins.test_laplacian_structure(f) for f in (OP.WEIGHTED_L1, OP.PAPER)],
     pins.test_maximum_principle_every_step,
-    lambda: [pins.test_monotone_majorise_minimise(f) for f in (OP.NORTH_STAR, OP.PAPER)],
+    lambda: [pins.test_monotone_majorise_minimise(f) for f in (OP.WEIGHTED_L1, OP.PAPER)],
     lambda: [pins.test_exact_references_on_hand_examples(n) for n in sorted(pins.load_hand())],
     pins.test_sweep_cut_ties_and_candidates,
     pins.test_sweep_cut_order_hand_example,

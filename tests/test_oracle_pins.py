@@ -58,7 +58,7 @@ def test_x0_series_chain_voltage_divider():
         assert abs(x[i] - expect) < 1e-14
 
 
-@pytest.mark.parametrize("form", [O.NORTH_STAR, O.PAPER])
+@pytest.mark.parametrize("form", [O.WEIGHTED_L1, O.PAPER])
 @pytest.mark.parametrize("a,b,v,eps", [(3.0, 1.0, 0.75, 0.1), (0.5, 2.0, 0.2, 1e-3),
                                        (1.5, 1.4, 0.5, 1e-6)])
 def test_one_irls_step_closed_form(form, a, b, v, eps):
@@ -66,11 +66,11 @@ def test_one_irls_step_closed_form(form, a, b, v, eps):
 
     The s-v edge has |Bx| = 1 - v, the v-t edge |Bx| = v.  The new voltage is
     the divider g_a / (g_a + g_b) of the reweighted conductances:
-    spec g = c / sqrt(d^2 + eps^2); paper g = c^2 / sqrt(c^2 d^2 + eps^2).
+    weighted-l1 g = c / sqrt(d^2 + eps^2); paper g = c^2 / sqrt(c^2 d^2 + eps^2).
     """
     P = svt(a, b)
     x = np.array([1.0, v, 0.0])
-    if form == O.NORTH_STAR:
+    if form == O.WEIGHTED_L1:
         ga = a / np.sqrt((1 - v) ** 2 + eps ** 2)
         gb = b / np.sqrt(v ** 2 + eps ** 2)
     else:
@@ -101,7 +101,7 @@ def test_irls_polarises_towards_min_cut(a, b):
 def test_smoothed_objective_closed_form(v, eps):
     """S_eps on s-v-t at x_v = v (Eq. l1-min-smooth-version):
     paper sum_e sqrt((c_e d_e)^2 + eps^2) = sqrt((a(1-v))^2 + eps^2) + sqrt((b v)^2 + eps^2);
-    spec sum_e c_e sqrt(d_e^2 + eps^2) = a sqrt((1-v)^2 + eps^2) + b sqrt(v^2 + eps^2).
+    weighted-l1 sum_e c_e sqrt(d_e^2 + eps^2) = a sqrt((1-v)^2 + eps^2) + b sqrt(v^2 + eps^2).
     At eps = 0 both equal the l1 objective ||C B x||_1 (Eq. l1-min)."""
     a, b = 3.0, 0.5
     P = svt(a, b)
@@ -109,7 +109,7 @@ def test_smoothed_objective_closed_form(v, eps):
     paper = np.sqrt((a * (1 - v)) ** 2 + eps ** 2) + np.sqrt((b * v) ** 2 + eps ** 2)
     ns = a * np.sqrt((1 - v) ** 2 + eps ** 2) + b * np.sqrt(v ** 2 + eps ** 2)
     assert abs(O.smoothed_objective(P, x, eps, O.PAPER) - paper) < 1e-14
-    assert abs(O.smoothed_objective(P, x, eps, O.NORTH_STAR) - ns) < 1e-14
+    assert abs(O.smoothed_objective(P, x, eps, O.WEIGHTED_L1) - ns) < 1e-14
     if eps == 0.0:
         assert abs(ns - (a * (1 - v) + b * v)) < 1e-15
 
@@ -145,7 +145,7 @@ def random_problems():
     return out
 
 
-@pytest.mark.parametrize("form", [O.NORTH_STAR, O.PAPER])
+@pytest.mark.parametrize("form", [O.WEIGHTED_L1, O.PAPER])
 def test_laplacian_structure(form):
     """L is symmetric with zero row sums (it is a Laplacian); L~ keeps the
     off-diagonals, its row sums equal the terminal conductances, and b >= 0
@@ -178,7 +178,7 @@ def test_laplacian_structure(form):
 def test_maximum_principle_every_step():
     """0 <= x^(l) <= 1 for every IRLS iterate (Prop. interval-constraint-satisfaction)."""
     for P in random_problems():
-        for form in (O.NORTH_STAR, O.PAPER):
+        for form in (O.WEIGHTED_L1, O.PAPER):
             xs, _ = O.irls(P, 25, form=form)
             for x in xs:
                 assert x.min() >= -1e-12 and x.max() <= 1 + 1e-12
@@ -200,7 +200,7 @@ def test_electrical_flow_conservation_and_value():
             assert abs(y[P.t] + mu) < 1e-10 * max(1.0, mu)
 
 
-@pytest.mark.parametrize("form", [O.NORTH_STAR, O.PAPER])
+@pytest.mark.parametrize("form", [O.WEIGHTED_L1, O.PAPER])
 def test_monotone_majorise_minimise(form):
     """Each IRLS step minimises a majoriser of the smoothed objective, so
     S_eps_l(x^(l)) <= S_eps_l(x^(l-1)) (Section 2.2, Eq. l1-min-smooth-version),
@@ -220,11 +220,11 @@ def test_monotone_majorise_minimise(form):
 
 
 def test_forms_coincide_for_unit_capacities():
-    """With c = 1 the spec and the paper reweighting are the same map."""
+    """With c = 1 the weighted-l1 and the paper reweighting are the same map."""
     g = gen.random_graph(12, 0.3, 7)
     g.c[:] = 1.0
     P = O.Problem.from_graph(g)
-    xa, _ = O.irls(P, 10, form=O.NORTH_STAR)
+    xa, _ = O.irls(P, 10, form=O.WEIGHTED_L1)
     xb, _ = O.irls(P, 10, form=O.PAPER)
     for a, b in zip(xa, xb):
         assert np.max(np.abs(a - b)) < 1e-12
@@ -376,7 +376,7 @@ def test_vertex_permutation_invariance():
 
 
 def test_capacity_scaling_invariance():
-    """North-star form: c -> alpha c leaves every iterate unchanged.
+    """Weighted-l1 form: c -> alpha c leaves every iterate unchanged.
     Paper form: (c, eps) -> (alpha c, alpha eps) leaves it unchanged."""
     g = gen.random_graph(13, 0.3, 502)
     P = O.Problem.from_graph(g)
