@@ -169,7 +169,7 @@ def kernel_source_hash():
     with open(os.path.join(csrc, "pcg.cu")) as f:
         text = f.read()
     a = text.index("// PCG iteration")
-    b = text.index("// r -= alpha q", a)
+    b = text.index("// r^ -= alpha q", a)
     h = hashlib.sha256(text[a:b].encode())
     with open(os.path.join(csrc, "device.cuh"), "rb") as f:
         h.update(f.read())
@@ -676,7 +676,11 @@ def main():
         cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
     if rank == 0:
-        bytes_iter = nt * (8 * 2 + 8 * 3) + nt * 8 * 5 + nt * 8 * 5  # spmv + update_r + update_xp
+        # spmv (g^: one value per edge in DIA, value + column per direction
+        # and the row pointers in CSR; p, q) + update_r (q, r^ read and
+        # written, FP32 d^1/2) + update_xp (x^, p read and written, r^)
+        g_bytes = 8 * ne if fmt == 1 else 12 * 2 * ne + 8 * nt
+        bytes_iter = g_bytes + nt * 8 * 2 + nt * (8 * 3 + 4) + nt * 8 * 5
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,

@@ -43,8 +43,8 @@ cudaError_t dalloc(T** p, size_t count) {
 
 void free_device(Ctx& c) {
   void* ps[] = {c.cdia, c.gdia, c.rp, c.col, c.cval, c.gval, c.cs, c.ct, c.x, c.r, c.p,
-                c.q, c.diag, c.dinv, c.partials, c.S, c.C, c.eps_list, c.recs, c.xfull,
-                c.side_full, c.d_in_rp, c.d_in_col};
+                c.q, c.diag, c.rsd, c.sq32, c.xs, c.ghat, c.partials, c.S, c.C, c.eps_list,
+                c.recs, c.xfull, c.side_full, c.d_in_rp, c.d_in_col};
   for (void* p : ps)
     if (p) cudaFree(p);
   pirmcut::sweep_free(c);
@@ -330,9 +330,16 @@ pirmcut_status finish_create(pirmcut_ctx* h, const pirmcut_options& o, void* str
   } else {
     if ((e = dalloc(&cx.gval, m)) != cudaSuccess) return bail(e, "cudaMalloc");
   }
-  double** vecs[] = {&cx.x, &cx.r, &cx.p, &cx.q, &cx.diag, &cx.dinv};
+  double** vecs[] = {&cx.x, &cx.r, &cx.p, &cx.q, &cx.diag};
   for (double** v : vecs)
     if ((e = dalloc(v, nt)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if (o.precision == PIRMCUT_PREC_FP64) {
+    if ((e = dalloc(&cx.rsd, nt)) != cudaSuccess) return bail(e, "cudaMalloc");
+    if ((e = dalloc(&cx.xs, nt)) != cudaSuccess) return bail(e, "cudaMalloc");
+    if ((e = dalloc(&cx.sq32, nt)) != cudaSuccess) return bail(e, "cudaMalloc");
+    if ((e = dalloc(&cx.ghat, cx.format == PIRMCUT_FORMAT_DIA ? size_t(cx.K) * nt : size_t(m))) != cudaSuccess)
+      return bail(e, "cudaMalloc");
+  }
   if ((e = dalloc(&cx.partials, 4 * size_t(pirmcut::kMaxBlocks))) != cudaSuccess) return bail(e, "cudaMalloc");
   if ((e = dalloc(&cx.S, 1)) != cudaSuccess) return bail(e, "cudaMalloc");
   if ((e = dalloc(&cx.C, 1)) != cudaSuccess) return bail(e, "cudaMalloc");
@@ -693,16 +700,17 @@ pirmcut_status pirmcut_time_spmv(pirmcut_ctx* h, int reps, double* avg_ms, doubl
                                                      : double(c.hg.nnz);
   const bool mx = c.opt.precision == PIRMCUT_PREC_MIXED;
   const double V = mx ? 4.0 : 8.0;
-  // vectors read/written once per row: diag, p, q (the FP32 inner system is
-  // scaled to unit diagonal: p and q only; the fused FP32 kernel also reads
-  // r and d and writes the new p and d)
-  const double nvec = mx ? (c.fused_inner ? 6.0 : 2.0) : 3.0;
+  // vectors read/written once per row: p and q (both systems are scaled to
+  // unit diagonal; the fused FP32 kernel also reads r and d and writes the
+  // new p and d)
+  const double nvec = mx && c.fused_inner ? 6.0 : 2.0;
   if (bytes) {
     *bytes = c.format == PIRMCUT_FORMAT_DIA ? nt * (V * c.K + V * nvec)
                                             : nnz * (V + 4.0) + nt * (V * nvec + 8.0);
   }
-  // nnz + diagonal FMAs (an add when scaled), plus the (p, q) FMA per row
-  if (flops) *flops = 2.0 * (nnz + 2.0 * nt);
+  // one FMA per stored off-diagonal entry, the unit diagonal's add and the
+  // (p, q) FMA per row
+  if (flops) *flops = 2.0 * nnz + 3.0 * nt;
   // the solve left stop_req set: clear it so the kernel runs, restore after
   const size_t off_stop = offsetof(pirmcut::PcgState, stop_req);
   int one = 1, zero = 0;

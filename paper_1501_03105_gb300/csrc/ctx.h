@@ -140,8 +140,13 @@ struct Ctx {
   double* p = nullptr;
   double* q = nullptr;
   double* diag = nullptr;
-  double* dinv = nullptr;
   double* partials = nullptr;   // 4 * kMaxBlocks
+  // FP64 path: CG on the Jacobi-scaled system D^-1/2 L~ D^-1/2 (unit
+  // diagonal), allocated for precision FP64 only
+  double* rsd = nullptr;        // d_v^-1/2
+  float* sq32 = nullptr;        // d_v^1/2 in FP32 (norm of the stopping test)
+  double* xs = nullptr;         // scaled iterate D^1/2 x
+  double* ghat = nullptr;       // scaled conductances g_uv d_u^-1/2 d_v^-1/2 (DIA K*nt or CSR nnz)
   PcgState* S = nullptr;
   // mixed precision: FP32 CG on the Jacobi-scaled system D^-1/2 L~ D^-1/2
   // (unit diagonal) inside FP64 iterative refinement

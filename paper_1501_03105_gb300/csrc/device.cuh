@@ -31,6 +31,10 @@ struct PcgState {
   int status;       // PIRMCUT_OK or PIRMCUT_ENUMERIC
   int pad;
   unsigned int counter[4];  // last-block counters (one per reduction site)
+  // FP64 path: ||r||^2 of the stopping test is summed in FP32 from
+  // |r_v| 2^rr_shift unless rr_fp64 (a diagonal outside [2^-80, 2^80])
+  int rr_shift;
+  int rr_fp64;
 };
 
 // Geometry of the DIA storage (upper diagonals only; L~ is symmetric).

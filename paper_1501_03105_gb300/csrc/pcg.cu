@@ -2,15 +2,25 @@
 //
 // A step is (Section 2.1, Steps 1-2; Section 3.1):
 //   reweight   g_e from x^(l-1) for every stored edge  (Eq. define-reweight-vector)
-//   assemble   terminal conductances, b_v = g(s,v), Jacobi diagonal and its
-//              inverse, r = b - L~ x, z = D^-1 r, p = z, (r,z), ||r||^2, ||b||^2
-//              (Eq. reduced-laplacian-system with x_s = 1, x_t = 0)
+//   assemble   terminal conductances, b_v = g(s,v), the Jacobi diagonal D,
+//              r = b - L~ x (Eq. reduced-laplacian-system with x_s = 1,
+//              x_t = 0), then the Jacobi-scaled start x^ = D^1/2 x,
+//              r^ = D^-1/2 r, p = r^, (r^, r^), ||r||^2, ||b||^2
+//   scale      g^_uv = g_uv d_u^-1/2 d_v^-1/2: the matrix A^ = D^-1/2 L~ D^-1/2
+//              with unit diagonal
 //   PCG loop   a CUDA-graph WHILE node whose body is three kernels:
-//                spmv      q = L~ p, (p, q) -> alpha
-//                update_r  r -= alpha q, z = D^-1 r, (r, z), ||r||^2 -> beta, stop?
-//                update_xp x += alpha p, p = z + beta p; clears the loop
+//                spmv      q = A^ p, (p, q) -> alpha
+//                update_r  r^ -= alpha q, (r^, r^), ||D^1/2 r^||^2 -> beta, stop?
+//                update_xp x^ += alpha p, p = r^ + beta p; clears the loop
 //                          condition once stop is requested
-//   step_end   range of x, per-step record.
+//   step_end   x = D^-1/2 x^, range of x, per-step record.
+// CG on A^ from x^ is Jacobi-preconditioned CG on L~ from x (the iterates are
+// the same in exact arithmetic; z = D^-1 r becomes r^ itself), with two FP64
+// operations per row fewer per iteration -- GB300 issues FP64 at 1/64 of its
+// FP32 rate, and these kernels are bound by that pipe.  The stopping test is
+// the unpreconditioned ||r|| / ||b|| <= tol with ||r||^2 = sum_v d_v r^_v^2,
+// summed in FP32 from integer-built FP32 copies of r^ and d^1/2 (relative
+// error below 1e-6: it decides only when to stop).
 // Every reduction is a fixed-order tree over fixed per-thread row sets, so
 // results are bit-identical from run to run.  Scalars (alpha, beta, the stop
 // flag) live in device memory; the host never synchronises inside a solve.
@@ -97,8 +107,10 @@ struct AssembleArgs {
   double tol2;
   int maxit;
   double* diag;
-  double* dinv;
-  double* r;
+  double* rsd;     // d^-1/2
+  float* sq32;     // d^1/2 in FP32
+  double* xs;      // scaled start D^1/2 x
+  double* r;       // scaled residual D^-1/2 r
   double* p;
   double* partials;
   PcgState* S;
@@ -106,10 +118,49 @@ struct AssembleArgs {
   int use_cond;    // 1 inside the step graph (set the WHILE condition), 0 for stream launches
 };
 
+// Range of d^1/2 for which the FP32 norm of the stopping test is used: with
+// |r| 2^rr_shift near 2^20, every FP32 value it forms (r^ 2^rr_shift, d^1/2
+// and their product) stays inside the FP32 normal range.
+constexpr double kSqrtDiagLo = 0x1p-40, kSqrtDiagHi = 0x1p40;
+
+// |v| 2^sh as a float, built from v's bit pattern with integer instructions
+// only (GB300 runs FP64 <-> FP32 conversions on its narrow FP64 pipe).  The
+// significand is truncated to 24 bits (relative error below 2^-23);
+// magnitudes below the FP32 normal range give 0, above it (and NaN) +inf.
+__device__ __forceinline__ float abs_f32_scaled(double v, int sh) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  const unsigned hi = unsigned(b >> 32), lo = unsigned(b);
+  const int e = int((hi >> 20) & 0x7FFu) - 896 + sh;  // FP32 biased exponent (1023 - 127 = 896)
+  const unsigned m = __funnelshift_r(lo, hi, 29) & 0x7FFFFFu;
+  if (e <= 0) return 0.0f;
+  if (e >= 255) return __int_as_float(0x7f800000);
+  return __uint_as_float((unsigned(e) << 23) | m);
+}
+
+// Assembly of one row after its diagonal d and residual r are known: the
+// scaled quantities, and the row's terms of (r^, r^), ||r||^2, ||b||^2.
+__device__ __forceinline__ void assemble_store(const AssembleArgs& a, int64_t i, double d,
+                                               double ri, double xi, double bi, double& rz,
+                                               double& rr, double& bb, double& nbad) {
+  const double si = rsqrt(d);
+  const double qi = d * si;
+  const double rh = si * ri;
+  a.diag[i] = d;
+  a.rsd[i] = si;
+  a.sq32[i] = abs_f32_scaled(qi, 0);
+  a.xs[i] = a.zero_start ? 0.0 : xi * qi;
+  a.r[i] = rh;
+  a.p[i] = rh;
+  rz = fma(rh, rh, rz);
+  rr = fma(ri, ri, rr);
+  bb = fma(bi, bi, bb);
+  if (!(qi >= kSqrtDiagLo && qi <= kSqrtDiagHi)) nbad += 1.0;
+}
+
 __device__ __forceinline__ void assemble_finish(const AssembleArgs& a, double rz, double rr,
-                                                double bb) {
-  double v[3] = {rz, rr, bb}, tot[3];
-  if (grid_sum<3>(v, a.partials, &a.S->counter[0], tot) && threadIdx.x == 0) {
+                                                double bb, double nbad) {
+  double v[4] = {rz, rr, bb, nbad}, tot[4];
+  if (grid_sum<4>(v, a.partials, &a.S->counter[0], tot) && threadIdx.x == 0) {
     PcgState* S = a.S;
     S->rz = tot[0];
     S->rr = tot[1];
@@ -121,6 +172,11 @@ __device__ __forceinline__ void assemble_finish(const AssembleArgs& a, double rz
     S->status = PIRMCUT_OK;
     S->alpha = 0.0;
     S->beta = 0.0;
+    // FP32 stopping norm: scale |r| to about 2^20 at the start
+    S->rr_fp64 = tot[3] > 0.0 ? 1 : 0;
+    int sh = 0;
+    if (tot[1] > 0.0 && isfinite(tot[1])) sh = 20 - ilogb(tot[1]) / 2;
+    S->rr_shift = sh < -200 ? -200 : (sh > 200 ? 200 : sh);
     int stop = (tot[1] <= a.tol2 * tot[2]) || a.maxit <= 0 || tot[2] == 0.0;
     if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) {
       stop = 1;
@@ -132,13 +188,13 @@ __device__ __forceinline__ void assemble_finish(const AssembleArgs& a, double rz
 }
 
 template <int K>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 k_assemble_dia(DiaDesc d, const double* __restrict__ g, AssembleArgs a) {
   const int64_t nt = d.nt;
   const double eps = a.initial ? 0.0 : a.eps_list[a.C->eps_idx];
   const double eps2 = eps * eps;
   const double* __restrict__ x = a.x;
-  double rz = 0.0, rr = 0.0, bb = 0.0;
+  double rz = 0.0, rr = 0.0, bb = 0.0, nbad = 0.0;
   for (int64_t i = gtid(); i < nt; i += gstride()) {
     const double xi = x[i];
     double gs = a.cs[i], gt = a.ct[i];
@@ -162,22 +218,14 @@ k_assemble_dia(DiaDesc d, const double* __restrict__ g, AssembleArgs a) {
         ax = fma(gg, x[i - o], ax);
       }
     }
-    const double di = 1.0 / sum;
     const double ri = a.zero_start ? gs : gs - fma(sum, xi, -ax);
-    const double zi = di * ri;
-    a.diag[i] = sum;
-    a.dinv[i] = di;
-    a.r[i] = ri;
-    a.p[i] = zi;
-    rz = fma(ri, zi, rz);
-    rr = fma(ri, ri, rr);
-    bb = fma(gs, gs, bb);
+    assemble_store(a, i, sum, ri, xi, gs, rz, rr, bb, nbad);
   }
-  assemble_finish(a, rz, rr, bb);
+  assemble_finish(a, rz, rr, bb, nbad);
 }
 
 template <int G>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 k_assemble_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                const double* __restrict__ g, AssembleArgs a) {
   const double eps = a.initial ? 0.0 : a.eps_list[a.C->eps_idx];
@@ -186,7 +234,7 @@ k_assemble_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __rest
   const int lane = threadIdx.x % G;
   const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
   const int64_t ng = gstride() / G;
-  double rz = 0.0, rr = 0.0, bb = 0.0;
+  double rz = 0.0, rr = 0.0, bb = 0.0, nbad = 0.0;
   for (int64_t i = gtid() / G; i < nt; i += ng) {
     double sum = 0.0, ax = 0.0;
     for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) {
@@ -208,19 +256,42 @@ k_assemble_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __rest
         gt = conductance(gt, wi, eps2, a.form);
       }
       sum += gs + gt;
-      const double di = 1.0 / sum;
       const double ri = a.zero_start ? gs : gs - fma(sum, xi, -ax);
-      const double zi = di * ri;
-      a.diag[i] = sum;
-      a.dinv[i] = di;
-      a.r[i] = ri;
-      a.p[i] = zi;
-      rz = fma(ri, zi, rz);
-      rr = fma(ri, ri, rr);
-      bb = fma(gs, gs, bb);
+      assemble_store(a, i, sum, ri, xi, gs, rz, rr, bb, nbad);
     }
   }
-  assemble_finish(a, rz, rr, bb);
+  assemble_finish(a, rz, rr, bb, nbad);
+}
+
+// g^_uv = g_uv (d_u^-1/2 d_v^-1/2): the off-diagonal of A^.  The product of
+// the two scale factors is formed first, so both directions of an edge get
+// the same bits (A^ stays exactly symmetric).
+template <int K>
+__global__ void __launch_bounds__(kThreads)
+k_scale_dia(DiaDesc d, const double* __restrict__ g, const double* __restrict__ rsd,
+            double* __restrict__ gh) {
+  const int64_t nt = d.nt;
+  for (int64_t i = gtid(); i < nt; i += gstride()) {
+    const double si = rsd[i];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int64_t j = i + d.off[k];
+      gh[k * nt + i] = j < nt ? g[k * nt + i] * (si * rsd[j]) : 0.0;
+    }
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(kThreads)
+k_scale_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+            const double* __restrict__ g, const double* __restrict__ rsd,
+            double* __restrict__ gh) {
+  const int lane = threadIdx.x % G;
+  const int64_t ng = gstride() / G;
+  for (int64_t i = gtid() / G; i < nt; i += ng) {
+    const double si = rsd[i];
+    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) gh[e] = g[e] * (si * rsd[col[e]]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -242,11 +313,11 @@ __device__ __forceinline__ void spmv_finish(double pq, double* partials, PcgStat
   }
 }
 
+// q = A^ p with A^ = I - (scaled conductances), and (p, q)
 template <int K>
 __global__ void __launch_bounds__(kThreads)
-k_spmv_dia(DiaDesc d, const double* __restrict__ g, const double* __restrict__ diag,
-           const double* __restrict__ p, double* __restrict__ q, double* partials,
-           PcgState* S) {
+k_spmv_dia(DiaDesc d, const double* __restrict__ g, const double* __restrict__ p,
+           double* __restrict__ q, double* partials, PcgState* S) {
   if (S->stop_req) {
     if (blockIdx.x == 0 && threadIdx.x == 0) S->stopped = 1;
     return;
@@ -255,7 +326,7 @@ k_spmv_dia(DiaDesc d, const double* __restrict__ g, const double* __restrict__ d
   double pq = 0.0;
   for (int64_t i = gtid(); i < nt; i += gstride()) {
     const double pi = p[i];
-    double acc = diag[i] * pi;
+    double acc = pi;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int64_t o = d.off[k];
@@ -271,9 +342,8 @@ k_spmv_dia(DiaDesc d, const double* __restrict__ g, const double* __restrict__ d
 template <int G>
 __global__ void __launch_bounds__(kThreads)
 k_spmv_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-           const double* __restrict__ g, const double* __restrict__ diag,
-           const double* __restrict__ p, double* __restrict__ q, double* partials,
-           PcgState* S) {
+           const double* __restrict__ g, const double* __restrict__ p, double* __restrict__ q,
+           double* partials, PcgState* S) {
   if (S->stop_req) {
     if (blockIdx.x == 0 && threadIdx.x == 0) S->stopped = 1;
     return;
@@ -289,7 +359,7 @@ k_spmv_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(mask, acc, o, G);
     if (lane == 0) {
       const double pi = p[i];
-      acc = fma(diag[i], pi, acc);
+      acc += pi;
       q[i] = acc;
       pq = fma(pi, acc, pq);
     }
@@ -297,31 +367,48 @@ k_spmv_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict
   spmv_finish(pq, partials, S);
 }
 
-// r -= alpha q; z = D^-1 r is written over q; (r, z) and ||r||^2 -> beta, stop.
+// r^ -= alpha q; (r^, r^) and ||r||^2 = sum_v d_v r^_v^2 -> beta, stop.  The
+// norm is summed in FP32 from |r^_v| 2^rr_shift and d_v^1/2 (both built with
+// integer instructions), in FP64 when a diagonal lies outside the FP32-safe
+// range.
 __global__ void __launch_bounds__(kThreads)
-k_update_r(int64_t nt, double* __restrict__ qz, const double* __restrict__ dinv,
-           double* __restrict__ r, double* partials, PcgState* S) {
+k_update_r(int64_t nt, const double* __restrict__ q, const float* __restrict__ sq32,
+           const double* __restrict__ diag, double* __restrict__ r, double* partials,
+           PcgState* S) {
   if (S->stop_req) return;
   const double alpha = S->alpha;
+  const int sh = S->rr_shift;
+  const bool fp64_norm = S->rr_fp64 != 0;
   double rz = 0.0, rr = 0.0;
-  for (int64_t i = gtid(); i < nt; i += gstride()) {
-    const double ri = fma(-alpha, qz[i], r[i]);
-    const double zi = dinv[i] * ri;
-    r[i] = ri;
-    qz[i] = zi;
-    rz = fma(ri, zi, rz);
-    rr = fma(ri, ri, rr);
+  if (fp64_norm) {
+    for (int64_t i = gtid(); i < nt; i += gstride()) {
+      const double ri = fma(-alpha, q[i], r[i]);
+      r[i] = ri;
+      rz = fma(ri, ri, rz);
+      rr = fma(diag[i] * ri, ri, rr);
+    }
+  } else {
+    float rr32 = 0.0f;
+    for (int64_t i = gtid(); i < nt; i += gstride()) {
+      const double ri = fma(-alpha, q[i], r[i]);
+      r[i] = ri;
+      rz = fma(ri, ri, rz);
+      const float ui = sq32[i] * abs_f32_scaled(ri, sh);
+      rr32 = fmaf(ui, ui, rr32);
+    }
+    rr = double(rr32);
   }
   double v[2] = {rz, rr}, tot[2];
   if (grid_sum<2>(v, partials, &S->counter[2], tot) && threadIdx.x == 0) {
     const int it = S->iters + 1;
     S->iters = it;
     const double beta = tot[0] / S->rz;
+    const double rrt = fp64_norm ? tot[1] : ldexp(tot[1], -2 * sh);
     S->beta = beta;
     S->rz = tot[0];
-    S->rr = tot[1];
-    int stop = (tot[1] <= S->tol2 * S->bb) || it >= S->maxit;
-    if (!isfinite(tot[1]) || !isfinite(beta)) {
+    S->rr = rrt;
+    int stop = (rrt <= S->tol2 * S->bb) || it >= S->maxit;
+    if (!isfinite(rrt) || !isfinite(beta)) {
       stop = 1;
       S->status = PIRMCUT_ENUMERIC;
       S->beta = 0.0;
@@ -330,8 +417,8 @@ k_update_r(int64_t nt, double* __restrict__ qz, const double* __restrict__ dinv,
   }
 }
 
-// x += alpha p; p = z + beta p (z read from the q buffer).  Ends the loop
-// once a stop was requested in this or an earlier kernel.
+// x^ += alpha p; p = r^ + beta p.  Ends the loop once a stop was requested
+// in this or an earlier kernel.
 __global__ void __launch_bounds__(kThreads)
 k_update_xp(int64_t nt, double* __restrict__ x, double* __restrict__ p,
             const double* __restrict__ z, PcgState* S, cudaGraphConditionalHandle h,
@@ -362,8 +449,10 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+// xs, when given, is the scaled iterate of the FP64 path: x = rsd * xs.
 __global__ void __launch_bounds__(kThreads)
-k_step_end(int64_t nt, double* __restrict__ x, PcgState* S, StepCounters* C, StepRec* recs,
+k_step_end(int64_t nt, double* __restrict__ x, const double* __restrict__ xs,
+           const double* __restrict__ rsd, PcgState* S, StepCounters* C, StepRec* recs,
            const double* __restrict__ eps_list, int consumes_eps, double* partials,
            const OuterState* O) {
   __shared__ double smn[32], smx[32];
@@ -371,10 +460,15 @@ k_step_end(int64_t nt, double* __restrict__ x, PcgState* S, StepCounters* C, Ste
   const bool zero = S->bb == 0.0;  // b = 0: the solution of L~ v = b is v = 0
   double mn = INFINITY, mx = -INFINITY;
   for (int64_t i = gtid(); i < nt; i += gstride()) {
-    double xi = x[i];
+    double xi;
     if (zero) {
       xi = 0.0;
       x[i] = 0.0;
+    } else if (xs) {
+      xi = rsd[i] * xs[i];
+      x[i] = xi;
+    } else {
+      xi = x[i];
     }
     mn = fmin(mn, xi);
     mx = fmax(mx, xi);
@@ -493,10 +587,10 @@ cudaError_t launch_spmv_once(Ctx& c) {
   const int grid = rg < kFp64MaxBlocks ? rg : kFp64MaxBlocks;
   if (c.format == PIRMCUT_FORMAT_DIA) {
     PIRMCUT_DISPATCH_K(c.K, (k_spmv_dia<KK><<<grid, kThreads, 0, c.stream>>>(
-                                c.dd, c.gdia, c.diag, c.p, c.q, c.partials, c.S)));
+                                c.dd, c.ghat, c.p, c.q, c.partials, c.S)));
   } else {
     PIRMCUT_DISPATCH_G(c.group, (k_spmv_csr<GG><<<grid, kThreads, 0, c.stream>>>(
-                                    c.nt, c.rp, c.col, c.gval, c.diag, c.p, c.q, c.partials, c.S)));
+                                    c.nt, c.rp, c.col, c.ghat, c.p, c.q, c.partials, c.S)));
   }
   c.launches += 1;
   return cudaGetLastError();
@@ -530,17 +624,21 @@ int enqueue_reweight(Ctx& c, cudaStream_t st, bool initial) {
   return 1;
 }
 
-// Epilogue of a step: range of x and the step record.
+// Epilogue of a step: x from the scaled iterate (FP64 path), range of x and
+// the step record.
 int enqueue_step_end(Ctx& c, cudaStream_t st, bool initial, const OuterState* O) {
-  k_step_end<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.x, c.S, c.C, c.recs, c.eps_list,
-                                                  initial ? 0 : 1, c.partials, O);
+  const bool scaled = c.opt.precision == PIRMCUT_PREC_FP64;
+  k_step_end<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.x, scaled ? c.xs : nullptr,
+                                                  scaled ? c.rsd : nullptr, c.S, c.C, c.recs,
+                                                  c.eps_list, initial ? 0 : 1, c.partials, O);
   return 1;
 }
 
 namespace {
 
 // Kernels of a step before the PCG loop:
-//   [keep x^(l-1), g^(l-1)] -> [c -> g | reweight] -> [features, learned start] -> assemble -> [x = 0].
+//   [keep x^(l-1), g^(l-1)] -> [c -> g | reweight] -> [features, learned start]
+//   -> assemble -> scale.
 int enqueue_prologue(Ctx& c, cudaStream_t st, bool initial, cudaGraphConditionalHandle h,
                      int use_cond) {
   const int grid = row_grid(c);
@@ -563,7 +661,9 @@ int enqueue_prologue(Ctx& c, cudaStream_t st, bool initial, cudaGraphConditional
   a.tol2 = c.opt.pcg_tol * c.opt.pcg_tol;
   a.maxit = c.opt.pcg_max_iter;
   a.diag = c.diag;
-  a.dinv = c.dinv;
+  a.rsd = c.rsd;
+  a.sq32 = c.sq32;
+  a.xs = c.xs;
   a.r = c.r;
   a.p = c.p;
   a.partials = c.partials;
@@ -572,12 +672,13 @@ int enqueue_prologue(Ctx& c, cudaStream_t st, bool initial, cudaGraphConditional
   a.use_cond = use_cond;
   if (c.format == PIRMCUT_FORMAT_DIA) {
     PIRMCUT_DISPATCH_K(c.K, (k_assemble_dia<KK><<<grid, kThreads, 0, st>>>(c.dd, g, a)));
+    PIRMCUT_DISPATCH_K(c.K, (k_scale_dia<KK><<<grid, kThreads, 0, st>>>(c.dd, g, c.rsd, c.ghat)));
   } else {
     PIRMCUT_DISPATCH_G(c.group, (k_assemble_csr<GG><<<grid, kThreads, 0, st>>>(c.nt, c.rp, c.col, g, a)));
+    PIRMCUT_DISPATCH_G(c.group, (k_scale_csr<GG><<<grid, kThreads, 0, st>>>(
+                                    c.nt, c.rp, c.col, g, c.rsd, c.ghat)));
   }
-  ++kernels;
-  if (zero_start) cudaMemsetAsync(c.x, 0, sizeof(double) * c.nt, st);
-  return kernels;
+  return kernels + 2;
 }
 
 // One PCG iteration: spmv -> update_r -> update_xp (events, when given,
@@ -587,18 +688,17 @@ int enqueue_iteration(Ctx& c, cudaStream_t st, cudaGraphConditionalHandle h, int
   const int rg = row_grid(c), vg = grid_for(c.nt);
   const int grid = rg < kFp64MaxBlocks ? rg : kFp64MaxBlocks;
   const int vgrid = vg < kFp64MaxBlocks ? vg : kFp64MaxBlocks;
-  const double* g = c.format == PIRMCUT_FORMAT_DIA ? c.gdia : c.gval;
   if (e0) cudaEventRecord(e0, st);
   if (c.format == PIRMCUT_FORMAT_DIA) {
     PIRMCUT_DISPATCH_K(c.K, (k_spmv_dia<KK><<<grid, kThreads, 0, st>>>(
-                                c.dd, g, c.diag, c.p, c.q, c.partials, c.S)));
+                                c.dd, c.ghat, c.p, c.q, c.partials, c.S)));
   } else {
     PIRMCUT_DISPATCH_G(c.group, (k_spmv_csr<GG><<<grid, kThreads, 0, st>>>(
-                                    c.nt, c.rp, c.col, g, c.diag, c.p, c.q, c.partials, c.S)));
+                                    c.nt, c.rp, c.col, c.ghat, c.p, c.q, c.partials, c.S)));
   }
   if (e1) cudaEventRecord(e1, st);
-  k_update_r<<<vgrid, kThreads, 0, st>>>(c.nt, c.q, c.dinv, c.r, c.partials, c.S);
-  k_update_xp<<<vgrid, kThreads, 0, st>>>(c.nt, c.x, c.p, c.q, c.S, h, use_cond);
+  k_update_r<<<vgrid, kThreads, 0, st>>>(c.nt, c.q, c.sq32, c.diag, c.r, c.partials, c.S);
+  k_update_xp<<<vgrid, kThreads, 0, st>>>(c.nt, c.xs, c.p, c.r, c.S, h, use_cond);
   return 3;
 }
 
@@ -650,8 +750,9 @@ cudaError_t build_step_graph(Ctx& c, bool initial, cudaGraphExec_t* out, int* no
   }
   if (e == cudaSuccess)
     e = cudaStreamUpdateCaptureDependencies(st, &cond_node, nullptr, 1, cudaStreamSetCaptureDependencies);
-  if (e == cudaSuccess && mlp_active(c, initial)) n_nodes += enqueue_mlp_train(c, st);
+  // the step end writes x = D^-1/2 x^, which the learned start trains on
   if (e == cudaSuccess) n_nodes += enqueue_step_end(c, st, initial, nullptr);
+  if (e == cudaSuccess && mlp_active(c, initial)) n_nodes += enqueue_mlp_train(c, st);
   cudaGraph_t captured = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(st, &captured);
   if (e == cudaSuccess) e = e2;
@@ -689,8 +790,8 @@ cudaError_t run_step_stream(Ctx& c, bool initial, int* stop_flag_host, int64_t* 
     if (guard > c.opt.pcg_max_iter / 8 + 2) break;  // the device caps iterations; belt and braces
   }
   if (e == cudaSuccess) {
-    if (mlp_active(c, initial)) k += enqueue_mlp_train(c, st);
     k += enqueue_step_end(c, st, initial, nullptr);
+    if (mlp_active(c, initial)) k += enqueue_mlp_train(c, st);
     e = cudaGetLastError();
   }
   *kernels = k;

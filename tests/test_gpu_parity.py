@@ -135,6 +135,55 @@ def test_free_running_solve_grid64(P):
     assert abs(value - ref["value"]) <= CUT_RTOL * ref["value"]
 
 
+@pytest.mark.parametrize("fmt", [0, 2])
+def test_stopping_norm_is_the_true_residual(P, fmt):
+    """The FP64 path sums ||r||^2 of its stopping test in FP32 (from r^ =
+    D^-1/2 r and d^1/2): every step stops with the reported ||r|| / ||b|| at
+    most pcg_tol, and the residual of the returned x, recomputed here in FP64
+    from the oracle's system, agrees with it."""
+    g = gen.config_graph(1)
+    prob = O.Problem.from_graph(g)
+    T = 20
+    eps = O.eps_schedule(T)
+    xs, _ = O.irls(prob, T, eps)
+    tol = 1e-6
+    with solver(P, g, format=fmt, pcg_tol=tol) as s:
+        for l in range(1, T + 1):
+            s.set_x(xs[l - 1])
+            info = s.irls_step(eps[l - 1])
+            assert info.status == 0 and info.rel_residual <= tol, l
+            Lt, b = O.reduced_system(prob, O.laplacian(prob, O.reweight(prob, xs[l - 1], eps[l - 1])))
+            v = prob.Z.T @ s.get_x()
+            true = np.linalg.norm(b - Lt @ v) / np.linalg.norm(b)
+            assert true <= 1.01 * tol and abs(true - info.rel_residual) <= 1e-2 * tol, (l, true, info.rel_residual)
+
+
+@pytest.mark.parametrize("fmt", [0, 2])
+def test_capacity_scaling_and_the_fp32_stopping_norm(P, fmt):
+    """x is invariant under c -> lambda c (weighted-l1 form).  With lambda =
+    2^20 every diagonal stays in the range where the stopping norm is summed
+    in FP32 and every quantity scales by a power of two; lambda = 2^100 or
+    2^-100 puts diagonals outside it, where the norm is summed in FP64."""
+    g = gen.config_graph(1, scale=32)
+    T = 8
+    eps = O.eps_schedule(T)
+
+    def run(lam):
+        gg = gen.Graph(g.n, g.row_ptr, g.col, g.c * lam, g.s, g.t)
+        with solver(P, gg, format=fmt, pcg_tol=1e-12) as s:
+            infos = s.solve(T, eps)
+            assert all(i.status == 0 and i.rel_residual <= 1e-12 for i in infos), lam
+            return s.get_x(), [i.pcg_iters for i in infos]
+
+    x1, it1 = run(1.0)
+    x2, it2 = run(2.0 ** 20)
+    assert all(abs(a - b) <= 1 for a, b in zip(it1, it2)) and np.max(np.abs(x2 - x1)) <= 1e-12
+    for lam in (2.0 ** 100, 2.0 ** -100):
+        x3, it3 = run(lam)
+        assert np.max(np.abs(x3 - x1)) <= 1e-10, lam
+        assert all(abs(a - b) <= 2 for a, b in zip(it1, it3)), (lam, it1, it3)
+
+
 @pytest.mark.parametrize("name,make", GRAPHS)
 @pytest.mark.parametrize("fmt", [0, 2])
 def test_sweep_cut_on_given_x(P, name, make, fmt):
