@@ -317,7 +317,8 @@ def run_batch(args):
                                "avg degree 10, n log-uniform 1e4-1e6, seed 4",
                    "instances": len(graphs), "total_rows": info["rows"], "total_nnz": info["nnz"],
                    "autotuned": {"threads_per_row": info["threads_per_row"],
-                                 "tile_rows": info["tile_rows"], "tiles": info["tiles"]},
+                                 "tile_rows": info["tile_rows"], "tiles": info["tiles"],
+                                 "warp_rows_above_deg": info["medium_deg"]},
                    "T": T, "pcg_tol": PCG_TOL, "step": "batched x0 + 50 IRLS steps + 64 sweep cuts"},
         "sequential_ms_per_step": seq_ms,
         "batched_speedup_vs_sequential": seq_ms / (ms / args.steps),

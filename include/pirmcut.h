@@ -98,6 +98,12 @@ typedef struct {
                           non-terminal has a terminal capacity (else, and for
                           every input error, on the host); 1: always on the
                           host.  Both give the same problem.                  */
+  int batch_threads_per_row; /* batches: threads per short row (1, 2, 4, 8, 16
+                          or 32), rows per consecutive-row tile (64 to 65536),
+                          and the warp-row threshold (1 to 512; 512 turns the
+                          warp tier off); 0 = chosen by the autotuner          */
+  int batch_tile_rows;
+  int batch_medium_deg;
 } pirmcut_options;
 
 typedef struct {
@@ -115,7 +121,8 @@ typedef struct {
 
 /* Fill *opt with the defaults: WEIGHTED_L1, FP64, pcg_tol 1e-10,
  * pcg_max_iter 20000, warm_start 1, FORMAT_AUTO, track_cut 0, graph_launch 1,
- * inner_tol 1e-5, time_spmv 0, reduce_on_host 0.  With MIXED, pcg_iters counts FP32 inner iterations, at most
+ * inner_tol 1e-5, time_spmv 0, reduce_on_host 0, batch_* 0.  With MIXED,
+ * pcg_iters counts FP32 inner iterations, at most
  * min(pcg_max_iter, 2000) per refinement cycle and 64 cycles per system. */
 void pirmcut_default_options(pirmcut_options* opt);
 
@@ -390,8 +397,11 @@ pirmcut_status pirmcut_sweep_cut_static(int64_t n, const int64_t* row_ptr, const
  *
  * pirmcut_batch_create: count instances; n[i], row_ptr[i], col[i], c[i],
  * s[i], t[i] describe instance i exactly as the arguments of pirmcut_create
- * (host memory).  At creation an autotuner times the batched SpMV for several
- * (threads per row, tile height) pairs and keeps the fastest.
+ * (host memory).  Rows are processed in three tiers by degree: short rows by
+ * groups of threads per row in consecutive-row tiles, longer rows a warp each,
+ * hub rows (more than 512 entries) a block each.  At creation an autotuner
+ * times the batched SpMV for several (threads per row, tile height, warp-row
+ * threshold) choices and keeps the fastest.
  * Errors: EINVAL (with the failing instance in the message), EDISCONNECTED,
  * ENOMEM, ECUDA.
  */
@@ -410,9 +420,13 @@ pirmcut_status pirmcut_batch_cut(pirmcut_batch* b, int index, uint8_t* side, dou
                                  double* tau);
 /* x of instance index, double[n_index] in host memory (x_s = 1, x_t = 0). */
 pirmcut_status pirmcut_batch_get_x(pirmcut_batch* b, int index, double* x);
-/* Totals and the autotuner's choice. */
+/* Totals and the autotuner's choice: threads per short row, rows per
+ * consecutive-row tile, the number of tiles, and medium_deg (rows with more
+ * entries, up to the hub threshold, are processed a warp each; equal to the
+ * hub threshold when that tier is off).  Any output pointer may be NULL. */
 pirmcut_status pirmcut_batch_info(const pirmcut_batch* b, int64_t* total_rows, int64_t* total_nnz,
-                                  int* threads_per_row, int* tile_rows, int* tiles);
+                                  int* threads_per_row, int* tile_rows, int* tiles,
+                                  int64_t* medium_deg);
 int64_t pirmcut_batch_kernel_launches(const pirmcut_batch* b);
 void pirmcut_batch_destroy(pirmcut_batch* b);
 

@@ -35,7 +35,8 @@ class Options(ctypes.Structure):
                 ("warm_start", ctypes.c_int), ("format", ctypes.c_int),
                 ("track_cut", ctypes.c_int), ("graph_launch", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("time_spmv", ctypes.c_int),
-                ("reduce_on_host", ctypes.c_int)]
+                ("reduce_on_host", ctypes.c_int), ("batch_threads_per_row", ctypes.c_int),
+                ("batch_tile_rows", ctypes.c_int), ("batch_medium_deg", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):
@@ -119,7 +120,7 @@ def lib() -> ctypes.CDLL:
     L.pirmcut_batch_get_x.restype = ctypes.c_int
     L.pirmcut_batch_info.argtypes = [_P, ctypes.POINTER(i64), ctypes.POINTER(i64),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                                     ctypes.POINTER(ctypes.c_int)]
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64)]
     L.pirmcut_batch_info.restype = ctypes.c_int
     L.pirmcut_batch_kernel_launches.argtypes = [_P]
     L.pirmcut_batch_kernel_launches.restype = i64
@@ -435,11 +436,12 @@ def pirmcut_batch_get_x(h, index: int, n: int):
 
 
 def pirmcut_batch_info(h):
-    a, b = ctypes.c_int64(), ctypes.c_int64()
+    a, b, m = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     g, t, nt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     lib().pirmcut_batch_info(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(g), ctypes.byref(t),
-                             ctypes.byref(nt))
-    return dict(rows=a.value, nnz=b.value, threads_per_row=g.value, tile_rows=t.value, tiles=nt.value)
+                             ctypes.byref(nt), ctypes.byref(m))
+    return dict(rows=a.value, nnz=b.value, threads_per_row=g.value, tile_rows=t.value, tiles=nt.value,
+                medium_deg=m.value)
 
 
 def pirmcut_batch_kernel_launches(h) -> int:

@@ -43,7 +43,7 @@ cudaError_t dalloc(T** p, size_t count) {
 
 void free_device(Ctx& c) {
   void* ps[] = {c.cdia, c.gdia, c.rp, c.col, c.cval, c.gval, c.cs, c.ct, c.x, c.r, c.p,
-                c.q, c.diag, c.rsd, c.sq32, c.xs, c.ghat, c.partials, c.S, c.C, c.eps_list,
+                c.q, c.diag, c.rsd, c.sq32, c.xs, c.ghat, c.heavy, c.partials, c.S, c.C, c.eps_list,
                 c.recs, c.xfull, c.side_full, c.d_in_rp, c.d_in_col};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -340,7 +340,8 @@ pirmcut_status finish_create(pirmcut_ctx* h, const pirmcut_options& o, void* str
     if ((e = dalloc(&cx.ghat, cx.format == PIRMCUT_FORMAT_DIA ? size_t(cx.K) * nt : size_t(m))) != cudaSuccess)
       return bail(e, "cudaMalloc");
   }
-  if ((e = dalloc(&cx.partials, 4 * size_t(pirmcut::kMaxBlocks))) != cudaSuccess) return bail(e, "cudaMalloc");
+  if ((e = dalloc(&cx.partials, 4 * size_t(pirmcut::kMaxBlocks + pirmcut::kHeavyRowsMax))) != cudaSuccess)
+    return bail(e, "cudaMalloc");
   if ((e = dalloc(&cx.S, 1)) != cudaSuccess) return bail(e, "cudaMalloc");
   if ((e = dalloc(&cx.C, 1)) != cudaSuccess) return bail(e, "cudaMalloc");
   if ((e = cudaMemset(cx.S, 0, sizeof(pirmcut::PcgState))) != cudaSuccess) return bail(e, "cudaMemset");
@@ -362,6 +363,20 @@ pirmcut_status finish_create(pirmcut_ctx* h, const pirmcut_options& o, void* str
     return fail(nullptr, ps, m);
   }
   ps = ensure_capacity(h, 1);
+  if (ps == PIRMCUT_OK && cx.format == PIRMCUT_FORMAT_CSR) {
+    // rows far longer than the mean get a block each in the per-row kernels
+    if (!cx.hg.rp.empty()) {
+      e = pirmcut::set_heavy_rows(cx, cx.hg.rp.data());
+    } else {
+      pirmcut::hvec<int64_t> hrp(nt + 1);  // problem built on the device: its row pointers
+      e = cudaMemcpy(hrp.data(), cx.rp, sizeof(int64_t) * (nt + 1), cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = pirmcut::set_heavy_rows(cx, hrp.data());
+    }
+    if (e != cudaSuccess) {
+      cx.err = std::string("heavy rows: ") + cudaGetErrorString(e);
+      ps = PIRMCUT_ECUDA;
+    }
+  }
   if (ps != PIRMCUT_OK) {
     std::string m = cx.err;
     free_device(cx);
@@ -426,6 +441,9 @@ void pirmcut_default_options(pirmcut_options* opt) {
   opt->inner_tol = 1e-5;
   opt->time_spmv = 0;
   opt->reduce_on_host = 0;
+  opt->batch_threads_per_row = 0;
+  opt->batch_tile_rows = 0;
+  opt->batch_medium_deg = 0;
 }
 
 pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* col,

@@ -4,9 +4,12 @@
 //
 // The instances' reduced graphs are concatenated into one block-diagonal
 // CSR (global row offsets, instance-local column ids).  Rows are cut into
-// tiles that never straddle two instances; a row whose degree exceeds a
+// tiles that never straddle two instances, in three tiers by degree: range
+// tiles cover consecutive rows, a group of G threads per row; rows above a
+// middle threshold are listed in medium tiles, a warp per row (so one long
+// row no longer holds up the short rows of its warp); a row above the hub
 // threshold (a power-law hub) gets a tile of its own, processed by a whole
-// block, and is skipped by the range tile that contains it.  Every kernel runs
+// block.  Range tiles skip the rows of the other two tiers.  Every kernel runs
 // one block per tile.  Each instance keeps its own PCG scalars: a tile's block
 // writes its partial sums, and the last tile of an instance to finish (an
 // atomic ticket per instance) adds that instance's partials in tile order and
@@ -33,10 +36,16 @@ namespace {
 
 constexpr int kBT = 256;  // threads per block (one block per tile)
 
+// Tile kinds: consecutive rows [r0, r1); one hub row r0 for the whole block;
+// entries [r0, r1) of the medium-row list, a warp per row.
+constexpr int32_t kRangeTile = 0, kHubTile = 1, kMediumTile = 2;
+constexpr int kMediumRowsPerTile = 64;  // 8 rows per warp
+constexpr int kHubDeg = 512;            // rows with more entries: a block each
+
 struct Tile {
   int32_t inst;
-  int32_t heavy;  // 1: a single hub row [r0, r0+1) processed by the whole block
-  int64_t r0, r1; // global rows
+  int32_t kind;
+  int64_t r0, r1;
 };
 
 struct BInst {
@@ -50,7 +59,9 @@ struct BArgs {
   const BInst* insts;
   const int64_t* rp;    // global offsets into col/val
   const int32_t* col;   // instance-local ids
-  int64_t heavy_deg;    // rows with more entries go to heavy tiles
+  int64_t mid_deg;      // rows with more entries go to medium or hub tiles
+  int64_t heavy_deg;    // rows with more entries go to hub tiles
+  const int64_t* med;   // medium rows (global ids), grouped by tile
   PcgState* S;          // per instance
   double* partials;     // NV * ntiles
   int ntiles;
@@ -122,16 +133,26 @@ kb_reweight(BArgs a, const double* __restrict__ c, const double* __restrict__ x,
   const int64_t base = a.insts[tl.inst].base;
   const double eps = eps_list[C->eps_idx];
   const double eps2 = eps * eps;
-  if (tl.heavy) {
+  if (tl.kind == kHubTile) {
     const int64_t r = tl.r0;
     const double xr = x[r];
     for (int64_t e = a.rp[r] + threadIdx.x; e < a.rp[r + 1]; e += kBT)
       g[e] = conductance(c[e], xr - x[base + a.col[e]], eps2, form);
     return;
   }
+  if (tl.kind == kMediumTile) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t m = tl.r0 + threadIdx.x / 32; m < tl.r1; m += kBT / 32) {
+      const int64_t r = a.med[m];
+      const double xr = x[r];
+      for (int64_t e = a.rp[r] + lane; e < a.rp[r + 1]; e += 32)
+        g[e] = conductance(c[e], xr - x[base + a.col[e]], eps2, form);
+    }
+    return;
+  }
   const int lane = threadIdx.x % G;
   for (int64_t r = tl.r0 + threadIdx.x / G; r < tl.r1; r += kBT / G) {
-    if (deg_of(a, r) > a.heavy_deg) continue;
+    if (deg_of(a, r) > a.mid_deg) continue;
     const double xr = x[r];
     for (int64_t e = a.rp[r] + lane; e < a.rp[r + 1]; e += G)
       g[e] = conductance(c[e], xr - x[base + a.col[e]], eps2, form);
@@ -186,7 +207,7 @@ kb_assemble(BArgs a, const double* __restrict__ g, BAssemble b) {
   const double eps = b.initial ? 0.0 : b.eps_list[b.C->eps_idx];
   const double eps2 = eps * eps;
   double rz = 0.0, rr = 0.0, bb = 0.0;
-  if (tl.heavy) {
+  if (tl.kind == kHubTile) {
     const int64_t r = tl.r0;
     double sum = 0.0, ax = 0.0;
     for (int64_t e = a.rp[r] + threadIdx.x; e < a.rp[r + 1]; e += kBT) {
@@ -196,11 +217,24 @@ kb_assemble(BArgs a, const double* __restrict__ g, BAssemble b) {
     sum = block_total(sum);
     ax = block_total(ax);
     if (threadIdx.x == 0) bassemble_row(b, r, sum, ax, eps2, rz, rr, bb);
+  } else if (tl.kind == kMediumTile) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t m = tl.r0 + threadIdx.x / 32; m < tl.r1; m += kBT / 32) {
+      const int64_t r = a.med[m];
+      double sum = 0.0, ax = 0.0;
+      for (int64_t e = a.rp[r] + lane; e < a.rp[r + 1]; e += 32) {
+        sum += g[e];
+        ax = fma(g[e], b.x[base + a.col[e]], ax);
+      }
+      sum = group_reduce<32>(sum, 0xffffffffu);
+      ax = group_reduce<32>(ax, 0xffffffffu);
+      if (lane == 0) bassemble_row(b, r, sum, ax, eps2, rz, rr, bb);
+    }
   } else {
     const int lane = threadIdx.x % G;
     const unsigned mask = group_mask<G>();
     for (int64_t r = tl.r0 + threadIdx.x / G; r < tl.r1; r += kBT / G) {
-      if (deg_of(a, r) > a.heavy_deg) continue;
+      if (deg_of(a, r) > a.mid_deg) continue;
       double sum = 0.0, ax = 0.0;
       for (int64_t e = a.rp[r] + lane; e < a.rp[r + 1]; e += G) {
         sum += g[e];
@@ -250,7 +284,7 @@ kb_spmv(BArgs a, const double* __restrict__ g, const double* __restrict__ diag,
   }
   const int64_t base = a.insts[tl.inst].base;
   double pq = 0.0;
-  if (tl.heavy) {
+  if (tl.kind == kHubTile) {
     const int64_t r = tl.r0;
     double acc = 0.0;
     for (int64_t e = a.rp[r] + threadIdx.x; e < a.rp[r + 1]; e += kBT)
@@ -261,11 +295,25 @@ kb_spmv(BArgs a, const double* __restrict__ g, const double* __restrict__ diag,
       q[r] = acc;
       pq = p[r] * acc;
     }
+  } else if (tl.kind == kMediumTile) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t m = tl.r0 + threadIdx.x / 32; m < tl.r1; m += kBT / 32) {
+      const int64_t r = a.med[m];
+      double acc = 0.0;
+      for (int64_t e = a.rp[r] + lane; e < a.rp[r + 1]; e += 32) acc = fma(-g[e], p[base + a.col[e]], acc);
+      acc = group_reduce<32>(acc, 0xffffffffu);
+      if (lane == 0) {
+        const double pr = p[r];
+        acc = fma(diag[r], pr, acc);
+        q[r] = acc;
+        pq = fma(pr, acc, pq);
+      }
+    }
   } else {
     const int lane = threadIdx.x % G;
     const unsigned mask = group_mask<G>();
     for (int64_t r = tl.r0 + threadIdx.x / G; r < tl.r1; r += kBT / G) {
-      if (deg_of(a, r) > a.heavy_deg) continue;
+      if (deg_of(a, r) > a.mid_deg) continue;
       double acc = 0.0;
       for (int64_t e = a.rp[r] + lane; e < a.rp[r + 1]; e += G) acc = fma(-g[e], p[base + a.col[e]], acc);
       acc = group_reduce<G>(acc, mask);
@@ -292,8 +340,8 @@ kb_spmv(BArgs a, const double* __restrict__ g, const double* __restrict__ diag,
   }
 }
 
-// elementwise kernels visit the full row range of range tiles (hub rows
-// included) and only post a zero partial for heavy tiles
+// elementwise kernels visit the full row range of range tiles (medium and
+// hub rows included) and only post a zero partial for the other tiles
 __global__ void __launch_bounds__(kBT)
 kb_update_r(BArgs a, double* __restrict__ qz, const double* __restrict__ dinv,
             double* __restrict__ r) {
@@ -302,7 +350,7 @@ kb_update_r(BArgs a, double* __restrict__ qz, const double* __restrict__ dinv,
   if (S->stop_req) return;
   const double alpha = S->alpha;
   double rz = 0.0, rr = 0.0;
-  if (!tl.heavy) {
+  if (tl.kind == kRangeTile) {
     for (int64_t i = tl.r0 + threadIdx.x; i < tl.r1; i += kBT) {
       const double ri = fma(-alpha, qz[i], r[i]);
       const double zi = dinv[i] * ri;
@@ -336,7 +384,7 @@ kb_update_xp(BArgs a, double* __restrict__ x, double* __restrict__ p, const doub
              cudaGraphConditionalHandle h, int use_cond) {
   const Tile tl = a.tiles[blockIdx.x];
   PcgState* S = &a.S[tl.inst];
-  if (!tl.heavy && !S->stopped) {
+  if (tl.kind == kRangeTile && !S->stopped) {
     const double alpha = S->alpha, beta = S->beta;
     for (int64_t i = tl.r0 + threadIdx.x; i < tl.r1; i += kBT) {
       const double pi = p[i];
@@ -353,7 +401,7 @@ kb_step_end(BArgs a, const double* __restrict__ x, StepRec* recs, int rec_cap,
             const StepCounters* C, const double* eps_list, int consumes_eps) {
   const Tile tl = a.tiles[blockIdx.x];
   double mn = INFINITY, mx = -INFINITY;
-  if (!tl.heavy) {
+  if (tl.kind == kRangeTile) {
     for (int64_t i = tl.r0 + threadIdx.x; i < tl.r1; i += kBT) {
       mn = fmin(mn, x[i]);
       mx = fmax(mx, x[i]);
@@ -418,7 +466,7 @@ __global__ void kb_advance(StepCounters* C, int consumes_eps) {
 // b = 0 instances: the solution of L~ v = 0 is v = 0
 __global__ void __launch_bounds__(kBT) kb_zero_if_b0(BArgs a, double* __restrict__ x) {
   const Tile tl = a.tiles[blockIdx.x];
-  if (tl.heavy || a.S[tl.inst].bb != 0.0) return;
+  if (tl.kind != kRangeTile || a.S[tl.inst].bb != 0.0) return;
   for (int64_t i = tl.r0 + threadIdx.x; i < tl.r1; i += kBT) x[i] = 0.0;
 }
 
@@ -455,13 +503,16 @@ struct Batch {
   int64_t N = 0, M = 0;
   int G = 8;
   int tile_rows = 1024;
-  int64_t heavy_deg = 512;
+  int64_t mid_deg = 512;    // rows above: a warp each (medium tiles)
+  int64_t heavy_deg = 512;  // rows above: a block each (hub tiles)
+  std::vector<int64_t> h_med;
   // device
   int64_t* rp = nullptr;
   int32_t* col = nullptr;
   double *cval = nullptr, *gval = nullptr, *cs = nullptr, *ct = nullptr;
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *diag = nullptr, *dinv = nullptr;
   Tile* tiles = nullptr;
+  int64_t* med = nullptr;
   BInst* insts = nullptr;
   PcgState* S = nullptr;
   double* partials = nullptr;
@@ -490,7 +541,9 @@ BArgs make_args(Batch& b) {
   a.insts = b.insts;
   a.rp = b.rp;
   a.col = b.col;
+  a.mid_deg = b.mid_deg;
   a.heavy_deg = b.heavy_deg;
+  a.med = b.med;
   a.S = b.S;
   a.partials = b.partials;
   a.ntiles = int(b.h_tiles.size());
@@ -500,18 +553,26 @@ BArgs make_args(Batch& b) {
 
 void build_tiles(Batch& b) {
   b.h_tiles.clear();
+  b.h_med.clear();
   for (int i = 0; i < b.count; ++i) {
     BInst& in = b.h_insts[i];
     const HostGraph& g = b.hg[i];
     in.t0 = int32_t(b.h_tiles.size());
     for (int64_t r0 = 0; r0 < g.nt; r0 += b.tile_rows) {
       const int64_t r1 = std::min<int64_t>(g.nt, r0 + b.tile_rows);
-      b.h_tiles.push_back(Tile{i, 0, in.base + r0, in.base + r1});
+      b.h_tiles.push_back(Tile{i, kRangeTile, in.base + r0, in.base + r1});
     }
+    const int64_t m0 = int64_t(b.h_med.size());
     for (int64_t r = 0; r < g.nt; ++r) {
-      if (g.rp[r + 1] - g.rp[r] > b.heavy_deg)
-        b.h_tiles.push_back(Tile{i, 1, in.base + r, in.base + r + 1});
+      const int64_t deg = g.rp[r + 1] - g.rp[r];
+      if (deg > b.heavy_deg)
+        b.h_tiles.push_back(Tile{i, kHubTile, in.base + r, in.base + r + 1});
+      else if (deg > b.mid_deg)
+        b.h_med.push_back(in.base + r);
     }
+    const int64_t m1 = int64_t(b.h_med.size());
+    for (int64_t m = m0; m < m1; m += kMediumRowsPerTile)
+      b.h_tiles.push_back(Tile{i, kMediumTile, m, std::min<int64_t>(m1, m + kMediumRowsPerTile)});
     in.t1 = int32_t(b.h_tiles.size());
   }
 }
@@ -519,9 +580,14 @@ void build_tiles(Batch& b) {
 cudaError_t upload_tiles(Batch& b) {
   if (b.tiles) cudaFree(b.tiles);
   if (b.partials) cudaFree(b.partials);
+  if (b.med) cudaFree(b.med);
   b.tiles = nullptr;
   b.partials = nullptr;
+  b.med = nullptr;
   cudaError_t e = cudaMalloc(&b.tiles, sizeof(Tile) * b.h_tiles.size());
+  if (e == cudaSuccess) e = cudaMalloc(&b.med, sizeof(int64_t) * std::max<size_t>(1, b.h_med.size()));
+  if (e == cudaSuccess && !b.h_med.empty())
+    e = cudaMemcpy(b.med, b.h_med.data(), sizeof(int64_t) * b.h_med.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&b.partials, sizeof(double) * 4 * b.h_tiles.size());
   if (e == cudaSuccess)
     e = cudaMemcpy(b.tiles, b.h_tiles.data(), sizeof(Tile) * b.h_tiles.size(), cudaMemcpyHostToDevice);
@@ -631,10 +697,11 @@ cudaError_t build_bgraph(Batch& b, bool initial, cudaGraphExec_t* out) {
 
 void free_batch(Batch& b) {
   void* ps[] = {b.rp, b.col, b.cval, b.gval, b.cs, b.ct, b.x, b.r, b.p, b.q, b.diag, b.dinv,
-                b.tiles, b.insts, b.S, b.partials, b.active, b.C, b.eps_list, b.recs, b.xfull};
+                b.tiles, b.med, b.insts, b.S, b.partials, b.active, b.C, b.eps_list, b.recs, b.xfull};
   for (void* p : ps)
     if (p) cudaFree(p);
   sweep_free(b.view);
+  if (b.view.heavy) cudaFree(b.view.heavy);
   if (b.g_init) cudaGraphExecDestroy(b.g_init);
   if (b.g_step) cudaGraphExecDestroy(b.g_step);
   if (b.cap_stream) cudaStreamDestroy(b.cap_stream);
@@ -644,10 +711,15 @@ void free_batch(Batch& b) {
 }
 
 // Autotuner: time the batched SpMV (capacities as conductances) for each
-// (threads per row, tile height) candidate and keep the fastest.
+// (threads per row, tile height, medium-row threshold) candidate and keep the
+// fastest.  A medium threshold equal to the hub threshold disables that tier.
+// A value fixed in the options replaces its list of candidates.
 cudaError_t autotune(Batch& b) {
-  const int Gs[] = {2, 4, 8, 16, 32};
-  const int Ts[] = {512, 2048};
+  std::vector<int> Gs = {1, 2, 4, 8, 16, 32}, Ts = {512, 2048};
+  std::vector<int64_t> Ms = {16, 32, 64, b.heavy_deg};
+  if (b.opt.batch_threads_per_row) Gs = {b.opt.batch_threads_per_row};
+  if (b.opt.batch_tile_rows) Ts = {b.opt.batch_tile_rows};
+  if (b.opt.batch_medium_deg) Ms = {int64_t(b.opt.batch_medium_deg)};
   cudaError_t e = cudaMemcpy(b.gval, b.cval, sizeof(double) * b.M, cudaMemcpyDeviceToDevice);
   if (e == cudaSuccess) e = cudaMemset(b.p, 0, sizeof(double) * b.N);
   if (e == cudaSuccess) e = cudaMemset(b.diag, 0, sizeof(double) * b.N);
@@ -661,8 +733,13 @@ cudaError_t autotune(Batch& b) {
   cudaEventCreate(&e1);
   float best = 1e30f;
   int bestG = b.G, bestT = b.tile_rows;
-  for (int T : Ts) {
+  int64_t bestM = b.heavy_deg;
+  const int nM = int(Ms.size());
+  for (int tm = 0; tm < int(Ts.size()) * nM; ++tm) {
+    const int T = Ts[tm / nM];
+    const int64_t M = Ms[tm % nM];
     b.tile_rows = T;
+    b.mid_deg = M;
     build_tiles(b);
     if ((e = upload_tiles(b)) != cudaSuccess) break;
     for (int G : Gs) {
@@ -685,6 +762,7 @@ cudaError_t autotune(Batch& b) {
         best = tot;
         bestG = G;
         bestT = T;
+        bestM = M;
       }
     }
     if (e != cudaSuccess) break;
@@ -694,6 +772,7 @@ cudaError_t autotune(Batch& b) {
   if (e != cudaSuccess) return e;
   b.G = bestG;
   b.tile_rows = bestT;
+  b.mid_deg = bestM;
   build_tiles(b);
   e = upload_tiles(b);
   if (e == cudaSuccess) e = cudaMemset(b.S, 0, sizeof(PcgState) * b.count);
@@ -747,6 +826,14 @@ pirmcut_status pirmcut_batch_create(int count, const int64_t* n, const int64_t* 
     return bfail(nullptr, PIRMCUT_EINVAL, "batches run the FP64 solver");
   if (!(o.pcg_tol > 0.0) || o.pcg_max_iter < 0)
     return bfail(nullptr, PIRMCUT_EINVAL, "bad pcg_tol or pcg_max_iter");
+  {
+    const int g = o.batch_threads_per_row, tr = o.batch_tile_rows, md = o.batch_medium_deg;
+    if (!(g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32) ||
+        !(tr == 0 || (tr >= 64 && tr <= 65536)) || md < 0 || md > kHubDeg)
+      return bfail(nullptr, PIRMCUT_EINVAL,
+                   "batch_threads_per_row must be 0, 1, 2, 4, 8, 16 or 32, batch_tile_rows 0 or "
+                   "64..65536, batch_medium_deg 0..512");
+  }
   pirmcut_batch* h = new (std::nothrow) pirmcut_batch();
   if (!h) return bfail(nullptr, PIRMCUT_ENOMEM, "out of host memory");
   Batch& b = h->b;
@@ -814,8 +901,8 @@ pirmcut_status pirmcut_batch_create(int count, const int64_t* n, const int64_t* 
   if (e == cudaSuccess) e = cudaMemset(b.C, 0, sizeof(StepCounters));
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&b.h_ctr, sizeof(StepCounters), cudaHostAllocDefault);
   if (e != cudaSuccess) return bail(e, "upload");
-  // heavy rows: more entries than 32 threads can cover in 16 passes
-  b.heavy_deg = 512;
+  // hub rows: more entries than 32 threads can cover in 16 passes
+  b.heavy_deg = kHubDeg;
   e = autotune(b);
   if (e != cudaSuccess) return bail(e, "autotune");
   *out = h;
@@ -940,7 +1027,7 @@ pirmcut_status pirmcut_batch_cut(pirmcut_batch* h, int index, uint8_t* side, dou
     BCK(h, sweep_alloc(v), "sweep buffers");
     v.nt = keep;
   }
-  BCK(h, sweep_set_heavy(v, b.hg[index].rp.data()), "sweep rows");  // this instance's hubs
+  BCK(h, set_heavy_rows(v, b.hg[index].rp.data()), "sweep rows");  // this instance's hubs
   int kernels = 0;
   BCK(h, enqueue_sweep(v, b.stream, false, &kernels), "sweep");
   b.launches += kernels;
@@ -982,7 +1069,8 @@ pirmcut_status pirmcut_batch_get_x(pirmcut_batch* h, int index, double* x) {
 }
 
 pirmcut_status pirmcut_batch_info(const pirmcut_batch* h, int64_t* total_rows, int64_t* total_nnz,
-                                  int* threads_per_row, int* tile_rows, int* tiles) {
+                                  int* threads_per_row, int* tile_rows, int* tiles,
+                                  int64_t* medium_deg) {
   if (!h) return PIRMCUT_EINVAL;
   const pirmcut::Batch& b = h->b;
   if (total_rows) *total_rows = b.N;
@@ -990,6 +1078,7 @@ pirmcut_status pirmcut_batch_info(const pirmcut_batch* h, int64_t* total_rows, i
   if (threads_per_row) *threads_per_row = b.G;
   if (tile_rows) *tile_rows = b.tile_rows;
   if (tiles) *tiles = int(b.h_tiles.size());
+  if (medium_deg) *medium_deg = b.mid_deg;
   return PIRMCUT_OK;
 }
 

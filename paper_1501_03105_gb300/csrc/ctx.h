@@ -64,12 +64,9 @@ struct SweepBuf {
   double* result = nullptr;   // [value_prefix, value_exact, tau, k]
   int nblocks_sort = 0;
   int ntiles = 0;
-  // CSR rows of high degree, one block each in the per-row sweep kernels
-  int32_t* heavy = nullptr;   // row ids (at most kSweepHeavyMax), ascending
-  int n_heavy = 0;
-  int64_t heavy_deg = INT64_MAX;  // rows with more entries than this are heavy
 };
-constexpr int kSweepHeavyMax = 1024;
+// Most CSR rows that get a block of their own in the per-row kernels.
+constexpr int kHeavyRowsMax = 1024;
 
 // Learned warm start (per-node MLP, 6 -> 64 -> 64 -> 1).
 constexpr int kMlpFeatures = 6;
@@ -140,7 +137,13 @@ struct Ctx {
   double* p = nullptr;
   double* q = nullptr;
   double* diag = nullptr;
-  double* partials = nullptr;   // 4 * kMaxBlocks
+  double* partials = nullptr;   // 4 * (kMaxBlocks + kHeavyRowsMax)
+  // CSR rows far longer than the mean (more than max(512, 16 x mean) entries,
+  // at most kHeavyRowsMax of them, ascending): the per-row PCG and sweep
+  // kernels give each a block of its own, appended to their grids
+  int32_t* heavy = nullptr;
+  int n_heavy = 0;
+  int64_t heavy_deg = INT64_MAX;  // rows with more entries than this are heavy
   // FP64 path: CG on the Jacobi-scaled system D^-1/2 L~ D^-1/2 (unit
   // diagonal), allocated for precision FP64 only
   double* rsd = nullptr;        // d_v^-1/2
@@ -242,7 +245,7 @@ cudaError_t build_cut_graph(Ctx& c, cudaGraphExec_t* out, int* nodes);
 cudaError_t launch_side_full(Ctx& c, uint8_t* side_full);
 // The heavy rows of a CSR problem from its host row pointers (global entry
 // offsets for a batch instance's view).
-cudaError_t sweep_set_heavy(Ctx& c, const int64_t* host_rp);
+cudaError_t set_heavy_rows(Ctx& c, const int64_t* host_rp);
 void sweep_free(Ctx& c);
 
 }  // namespace pirmcut

@@ -73,17 +73,29 @@ k_reweight_dia(DiaDesc d, const double* __restrict__ c, const double* __restrict
   }
 }
 
+// CSR row kernels: blocks [0, light_blocks) take the rows with at most
+// heavy_deg entries, G threads per row; each later block takes one of the
+// heavy rows (a power-law hub) with all of its threads.
 template <int G>
 __global__ void __launch_bounds__(kThreads)
 k_reweight_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                const double* __restrict__ c, const double* __restrict__ x,
                const double* __restrict__ eps_list, const StepCounters* __restrict__ C,
-               int form, double* __restrict__ g) {
+               int form, double* __restrict__ g, int64_t heavy_deg,
+               const int32_t* __restrict__ heavy, int light_blocks) {
   const double eps = eps_list[C->eps_idx];
   const double eps2 = eps * eps;
+  if (int(blockIdx.x) >= light_blocks) {
+    const int64_t i = heavy[blockIdx.x - light_blocks];
+    const double xi = x[i];
+    for (int64_t e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x)
+      g[e] = conductance(c[e], xi - x[col[e]], eps2, form);
+    return;
+  }
   const int lane = threadIdx.x % G;
-  const int64_t ng = gstride() / G;
+  const int64_t ng = int64_t(light_blocks) * blockDim.x / G;
   for (int64_t i = gtid() / G; i < nt; i += ng) {
+    if (rp[i + 1] - rp[i] > heavy_deg) continue;  // the group agrees: same row
     const double xi = x[i];
     for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G)
       g[e] = conductance(c[e], xi - x[col[e]], eps2, form);
@@ -227,15 +239,41 @@ k_assemble_dia(DiaDesc d, const double* __restrict__ g, AssembleArgs a) {
 template <int G>
 __global__ void __launch_bounds__(kThreads, 4)
 k_assemble_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-               const double* __restrict__ g, AssembleArgs a) {
+               const double* __restrict__ g, AssembleArgs a, int64_t heavy_deg,
+               const int32_t* __restrict__ heavy, int light_blocks) {
   const double eps = a.initial ? 0.0 : a.eps_list[a.C->eps_idx];
   const double eps2 = eps * eps;
   const double* __restrict__ x = a.x;
+  double rz = 0.0, rr = 0.0, bb = 0.0, nbad = 0.0;
+  if (int(blockIdx.x) >= light_blocks) {
+    const int64_t i = heavy[blockIdx.x - light_blocks];
+    double v[2] = {0.0, 0.0};  // sum of g, (g, x) over the row
+    for (int64_t e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x) {
+      const double gg = g[e];
+      v[0] += gg;
+      v[1] = fma(gg, x[col[e]], v[1]);
+    }
+    block_sum<2>(v);
+    if (threadIdx.x == 0) {
+      const double xi = x[i];
+      double gs = a.cs[i], gt = a.ct[i];
+      if (!a.initial) {
+        const double wi = a.xw[i];
+        gs = conductance(gs, 1.0 - wi, eps2, a.form);
+        gt = conductance(gt, wi, eps2, a.form);
+      }
+      const double sum = v[0] + (gs + gt);
+      const double ri = a.zero_start ? gs : gs - fma(sum, xi, -v[1]);
+      assemble_store(a, i, sum, ri, xi, gs, rz, rr, bb, nbad);
+    }
+    assemble_finish(a, rz, rr, bb, nbad);
+    return;
+  }
   const int lane = threadIdx.x % G;
   const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
-  const int64_t ng = gstride() / G;
-  double rz = 0.0, rr = 0.0, bb = 0.0, nbad = 0.0;
+  const int64_t ng = int64_t(light_blocks) * blockDim.x / G;
   for (int64_t i = gtid() / G; i < nt; i += ng) {
+    if (rp[i + 1] - rp[i] > heavy_deg) continue;  // the group agrees: same row
     double sum = 0.0, ax = 0.0;
     for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) {
       const double gg = g[e];
@@ -285,10 +323,18 @@ template <int G>
 __global__ void __launch_bounds__(kThreads)
 k_scale_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
             const double* __restrict__ g, const double* __restrict__ rsd,
-            double* __restrict__ gh) {
+            double* __restrict__ gh, int64_t heavy_deg, const int32_t* __restrict__ heavy,
+            int light_blocks) {
+  if (int(blockIdx.x) >= light_blocks) {
+    const int64_t i = heavy[blockIdx.x - light_blocks];
+    const double si = rsd[i];
+    for (int64_t e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x) gh[e] = g[e] * (si * rsd[col[e]]);
+    return;
+  }
   const int lane = threadIdx.x % G;
-  const int64_t ng = gstride() / G;
+  const int64_t ng = int64_t(light_blocks) * blockDim.x / G;
   for (int64_t i = gtid() / G; i < nt; i += ng) {
+    if (rp[i + 1] - rp[i] > heavy_deg) continue;  // the group agrees: same row
     const double si = rsd[i];
     for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) gh[e] = g[e] * (si * rsd[col[e]]);
   }
@@ -343,16 +389,33 @@ template <int G>
 __global__ void __launch_bounds__(kThreads)
 k_spmv_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
            const double* __restrict__ g, const double* __restrict__ p, double* __restrict__ q,
-           double* partials, PcgState* S) {
+           double* partials, PcgState* S, int64_t heavy_deg, const int32_t* __restrict__ heavy,
+           int light_blocks) {
   if (S->stop_req) {
     if (blockIdx.x == 0 && threadIdx.x == 0) S->stopped = 1;
     return;
   }
+  double pq = 0.0;
+  if (int(blockIdx.x) >= light_blocks) {
+    const int64_t i = heavy[blockIdx.x - light_blocks];
+    double v[1] = {0.0};
+    for (int64_t e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x)
+      v[0] = fma(-g[e], p[col[e]], v[0]);
+    block_sum<1>(v);
+    if (threadIdx.x == 0) {
+      const double pi = p[i];
+      const double acc = v[0] + pi;
+      q[i] = acc;
+      pq = pi * acc;
+    }
+    spmv_finish(pq, partials, S);
+    return;
+  }
   const int lane = threadIdx.x % G;
   const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
-  const int64_t ng = gstride() / G;
-  double pq = 0.0;
+  const int64_t ng = int64_t(light_blocks) * blockDim.x / G;
   for (int64_t i = gtid() / G; i < nt; i += ng) {
+    if (rp[i + 1] - rp[i] > heavy_deg) continue;  // the group agrees: same row
     double acc = 0.0;
     for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) acc = fma(-g[e], p[col[e]], acc);
 #pragma unroll
@@ -589,8 +652,9 @@ cudaError_t launch_spmv_once(Ctx& c) {
     PIRMCUT_DISPATCH_K(c.K, (k_spmv_dia<KK><<<grid, kThreads, 0, c.stream>>>(
                                 c.dd, c.ghat, c.p, c.q, c.partials, c.S)));
   } else {
-    PIRMCUT_DISPATCH_G(c.group, (k_spmv_csr<GG><<<grid, kThreads, 0, c.stream>>>(
-                                    c.nt, c.rp, c.col, c.ghat, c.p, c.q, c.partials, c.S)));
+    PIRMCUT_DISPATCH_G(c.group, (k_spmv_csr<GG><<<grid + c.n_heavy, kThreads, 0, c.stream>>>(
+                                    c.nt, c.rp, c.col, c.ghat, c.p, c.q, c.partials, c.S,
+                                    c.heavy_deg, c.heavy, grid)));
   }
   c.launches += 1;
   return cudaGetLastError();
@@ -617,9 +681,9 @@ int enqueue_reweight(Ctx& c, cudaStream_t st, bool initial) {
     PIRMCUT_DISPATCH_K(c.K, (k_reweight_dia<KK><<<grid, kThreads, 0, st>>>(
                                 c.dd, c.cdia, c.x, c.eps_list, c.C, c.opt.reweight_form, c.gdia)));
   } else {
-    PIRMCUT_DISPATCH_G(c.group, (k_reweight_csr<GG><<<grid, kThreads, 0, st>>>(
+    PIRMCUT_DISPATCH_G(c.group, (k_reweight_csr<GG><<<grid + c.n_heavy, kThreads, 0, st>>>(
                                     c.nt, c.rp, c.col, c.cval, c.x, c.eps_list, c.C,
-                                    c.opt.reweight_form, c.gval)));
+                                    c.opt.reweight_form, c.gval, c.heavy_deg, c.heavy, grid)));
   }
   return 1;
 }
@@ -674,9 +738,10 @@ int enqueue_prologue(Ctx& c, cudaStream_t st, bool initial, cudaGraphConditional
     PIRMCUT_DISPATCH_K(c.K, (k_assemble_dia<KK><<<grid, kThreads, 0, st>>>(c.dd, g, a)));
     PIRMCUT_DISPATCH_K(c.K, (k_scale_dia<KK><<<grid, kThreads, 0, st>>>(c.dd, g, c.rsd, c.ghat)));
   } else {
-    PIRMCUT_DISPATCH_G(c.group, (k_assemble_csr<GG><<<grid, kThreads, 0, st>>>(c.nt, c.rp, c.col, g, a)));
-    PIRMCUT_DISPATCH_G(c.group, (k_scale_csr<GG><<<grid, kThreads, 0, st>>>(
-                                    c.nt, c.rp, c.col, g, c.rsd, c.ghat)));
+    PIRMCUT_DISPATCH_G(c.group, (k_assemble_csr<GG><<<grid + c.n_heavy, kThreads, 0, st>>>(
+                                    c.nt, c.rp, c.col, g, a, c.heavy_deg, c.heavy, grid)));
+    PIRMCUT_DISPATCH_G(c.group, (k_scale_csr<GG><<<grid + c.n_heavy, kThreads, 0, st>>>(
+                                    c.nt, c.rp, c.col, g, c.rsd, c.ghat, c.heavy_deg, c.heavy, grid)));
   }
   return kernels + 2;
 }
@@ -693,8 +758,9 @@ int enqueue_iteration(Ctx& c, cudaStream_t st, cudaGraphConditionalHandle h, int
     PIRMCUT_DISPATCH_K(c.K, (k_spmv_dia<KK><<<grid, kThreads, 0, st>>>(
                                 c.dd, c.ghat, c.p, c.q, c.partials, c.S)));
   } else {
-    PIRMCUT_DISPATCH_G(c.group, (k_spmv_csr<GG><<<grid, kThreads, 0, st>>>(
-                                    c.nt, c.rp, c.col, c.ghat, c.p, c.q, c.partials, c.S)));
+    PIRMCUT_DISPATCH_G(c.group, (k_spmv_csr<GG><<<grid + c.n_heavy, kThreads, 0, st>>>(
+                                    c.nt, c.rp, c.col, c.ghat, c.p, c.q, c.partials, c.S,
+                                    c.heavy_deg, c.heavy, grid)));
   }
   if (e1) cudaEventRecord(e1, st);
   k_update_r<<<vgrid, kThreads, 0, st>>>(c.nt, c.q, c.sq32, c.diag, c.r, c.partials, c.S);

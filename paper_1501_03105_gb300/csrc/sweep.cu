@@ -550,8 +550,7 @@ cudaError_t sweep_alloc(Ctx& c) {
   A((void**)&b.digit_tot, sizeof(uint32_t) * 256);
   A((void**)&b.rank, sizeof(int32_t) * nt);
   A((void**)&b.delta, sizeof(double) * nt);
-  A((void**)&b.blk, sizeof(double) * ((size_t(b.ntiles) + kMaxBlocks) * 2 + kSweepHeavyMax));
-  A((void**)&b.heavy, sizeof(int32_t) * kSweepHeavyMax);
+  A((void**)&b.blk, sizeof(double) * ((size_t(b.ntiles) + kMaxBlocks) * 2 + kHeavyRowsMax));
   A((void**)&b.blk_k, sizeof(int64_t) * (size_t(b.ntiles) + 1));
   A((void**)&b.side_red, nt);
   A((void**)&b.result, sizeof(double) * 4 + sizeof(unsigned int) * 8);
@@ -561,21 +560,12 @@ cudaError_t sweep_alloc(Ctx& c) {
     return e;
   }
   b.cap = nt;
-  b.n_heavy = 0;
-  b.heavy_deg = INT64_MAX;
-  if (c.format == PIRMCUT_FORMAT_CSR && c.rp && !c.hg.rp.empty()) e = sweep_set_heavy(c, c.hg.rp.data());
-  else if (c.format == PIRMCUT_FORMAT_CSR && c.rp && c.hg.nnz > 0) {
-    hvec<int64_t> hrp(size_t(nt) + 1);  // problem built on the device: its row pointers
-    e = cudaMemcpy(hrp.data(), c.rp, sizeof(int64_t) * (size_t(nt) + 1), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = sweep_set_heavy(c, hrp.data());
-  }
   return e;
 }
 
-// Rows with more than max(512, 16 x mean) entries, at most kSweepHeavyMax of
+// Rows with more than max(512, 16 x mean) entries, at most kHeavyRowsMax of
 // them (the longest), listed in ascending order.
-cudaError_t sweep_set_heavy(Ctx& c, const int64_t* rp) {
-  SweepBuf& b = c.sw;
+cudaError_t set_heavy_rows(Ctx& c, const int64_t* rp) {
   const int64_t nt = c.nt;
   const int64_t mean = nt ? (rp[nt] - rp[0]) / nt : 0;
   int64_t thr = std::max<int64_t>(512, 16 * mean);
@@ -584,12 +574,12 @@ cudaError_t sweep_set_heavy(Ctx& c, const int64_t* rp) {
     const int64_t d = rp[i + 1] - rp[i];
     if (d > thr) rows.push_back({d, int32_t(i)});
   }
-  if (int64_t(rows.size()) > kSweepHeavyMax) {
-    std::nth_element(rows.begin(), rows.begin() + kSweepHeavyMax, rows.end(),
+  if (int64_t(rows.size()) > kHeavyRowsMax) {
+    std::nth_element(rows.begin(), rows.begin() + kHeavyRowsMax, rows.end(),
                      [](const std::pair<int64_t, int32_t>& x, const std::pair<int64_t, int32_t>& y) {
                        return x.first > y.first;
                      });
-    thr = rows[kSweepHeavyMax].first;  // heavy: strictly longer than the first one left out
+    thr = rows[kHeavyRowsMax].first;  // heavy: strictly longer than the first one left out
     std::vector<std::pair<int64_t, int32_t>> keep;
     for (const auto& r : rows)
       if (r.first > thr) keep.push_back(r);
@@ -598,15 +588,19 @@ cudaError_t sweep_set_heavy(Ctx& c, const int64_t* rp) {
   std::vector<int32_t> ids;
   for (const auto& r : rows) ids.push_back(r.second);
   std::sort(ids.begin(), ids.end());
-  b.n_heavy = int(ids.size());
-  b.heavy_deg = thr;
+  if (!c.heavy) {
+    cudaError_t e = cudaMalloc((void**)&c.heavy, sizeof(int32_t) * kHeavyRowsMax);
+    if (e != cudaSuccess) return e;
+  }
+  c.n_heavy = int(ids.size());
+  c.heavy_deg = thr;
   if (ids.empty()) return cudaSuccess;
-  return cudaMemcpy(b.heavy, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice);
+  return cudaMemcpy(c.heavy, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice);
 }
 
 void sweep_free(Ctx& c) {
   SweepBuf& b = c.sw;
-  void* ps[] = {b.heavy, b.keys[0], b.keys[1], b.vals[0], b.vals[1], b.hist, b.digit_tot, b.rank,
+  void* ps[] = {b.keys[0], b.keys[1], b.vals[0], b.vals[1], b.hist, b.digit_tot, b.rank,
                 b.delta, b.blk, b.blk_k, b.side_red, b.result};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -643,9 +637,9 @@ cudaError_t enqueue_sweep(Ctx& c, cudaStream_t st, bool record, int* nodes) {
   if (c.format == PIRMCUT_FORMAT_DIA) {
     SW_DISPATCH_K(c.K, (k_delta_dia<KK><<<rgrid, kThreads, 0, st>>>(c.dd, c.cdia, c.cs, c.ct, b.rank, b.delta)));
   } else {
-    SW_DISPATCH_G(c.group, (k_delta_csr<GG><<<rgrid + b.n_heavy, kThreads, 0, st>>>(
-                                c.nt, c.rp, c.col, c.cval, c.cs, c.ct, b.rank, b.delta, b.heavy_deg,
-                                b.heavy, rgrid)));
+    SW_DISPATCH_G(c.group, (k_delta_csr<GG><<<rgrid + c.n_heavy, kThreads, 0, st>>>(
+                                c.nt, c.rp, c.col, c.cval, c.cs, c.ct, b.rank, b.delta, c.heavy_deg,
+                                c.heavy, rgrid)));
   }
   ++n_nodes;
   k_tile_sum<<<ntiles, kThreads, 0, st>>>(nt, order, b.delta, b.blk);
@@ -668,8 +662,8 @@ cudaError_t enqueue_sweep(Ctx& c, cudaStream_t st, bool record, int* nodes) {
   if (c.format == PIRMCUT_FORMAT_DIA) {
     SW_DISPATCH_K(c.K, (k_cut_dia<KK><<<rgrid, kThreads, 0, st>>>(c.dd, c.cdia, a)));
   } else {
-    SW_DISPATCH_G(c.group, (k_cut_csr<GG><<<rgrid + b.n_heavy, kThreads, 0, st>>>(
-                                c.nt, c.rp, c.col, c.cval, a, b.heavy_deg, b.heavy, rgrid)));
+    SW_DISPATCH_G(c.group, (k_cut_csr<GG><<<rgrid + c.n_heavy, kThreads, 0, st>>>(
+                                c.nt, c.rp, c.col, c.cval, a, c.heavy_deg, c.heavy, rgrid)));
   }
   ++n_nodes;
   if (nodes) *nodes = n_nodes;
@@ -697,8 +691,8 @@ cudaError_t enqueue_cut_value(Ctx& c, cudaStream_t st, const uint8_t* side_red) 
   if (c.format == PIRMCUT_FORMAT_DIA) {
     SW_DISPATCH_K(c.K, (k_cut_dia<KK><<<rgrid, kThreads, 0, st>>>(c.dd, c.cdia, a)));
   } else {
-    SW_DISPATCH_G(c.group, (k_cut_csr<GG><<<rgrid + b.n_heavy, kThreads, 0, st>>>(
-                                c.nt, c.rp, c.col, c.cval, a, b.heavy_deg, b.heavy, rgrid)));
+    SW_DISPATCH_G(c.group, (k_cut_csr<GG><<<rgrid + c.n_heavy, kThreads, 0, st>>>(
+                                c.nt, c.rp, c.col, c.cval, a, c.heavy_deg, c.heavy, rgrid)));
   }
   return cudaGetLastError();
 }

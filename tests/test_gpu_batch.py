@@ -45,14 +45,27 @@ def batch_graphs():
             gen.Graph(3, *gen.csr_from_edges(3, [0, 1], [1, 2], [2.0, 1.0]), 0, 2)]
 
 
-def test_batch_matches_single_contexts_and_oracle(P):
+# (threads per short row, rows per range tile, warp-row threshold); None:
+# the autotuner's choice.  The star's hub (1500 entries) is a block row in
+# every case; thresholds 4 and 16 send many Chung-Lu rows to the warp tier,
+# 512 turns it off.
+TILINGS = [None, (2, 512, 16), (1, 64, 4), (4, 2048, 512), (32, 512, 32)]
+
+
+@pytest.mark.parametrize("tiling", TILINGS, ids=lambda t: "auto" if t is None else "g%d-t%d-m%d" % t)
+def test_batch_matches_single_contexts_and_oracle(P, tiling):
     graphs = batch_graphs()
     T = 15
     eps = O.eps_schedule(T)
-    with P.Batch(graphs, pcg_tol=1e-13) as b:
+    kw = {} if tiling is None else dict(batch_threads_per_row=tiling[0], batch_tile_rows=tiling[1],
+                                        batch_medium_deg=tiling[2])
+    with P.Batch(graphs, pcg_tol=1e-13, **kw) as b:
         info = b.info()
         assert info["rows"] == sum(g.n - 2 for g in graphs)
-        assert info["threads_per_row"] in (2, 4, 8, 16, 32)
+        assert info["threads_per_row"] in (1, 2, 4, 8, 16, 32)
+        assert 1 <= info["medium_deg"] <= 512
+        if tiling is not None:
+            assert (info["threads_per_row"], info["tile_rows"], info["medium_deg"]) == tiling
         infos = b.solve(T, eps)
         xs_b = [b.get_x(i) for i in range(len(graphs))]
         cuts_b = [b.cut(i) for i in range(len(graphs))]
@@ -86,6 +99,16 @@ def test_batch_single_instance_and_repeat(P):
         x2 = b.get_x(0)
     assert np.array_equal(x1, x2)                      # deterministic
     assert [i.pcg_iters for i in a1[0]] == [i.pcg_iters for i in a2[0]]
+
+
+def test_batch_rejects_bad_tiling_options(P):
+    from paper_1501_03105_gb300 import binding as B
+    g = gen.random_graph(10, 0.3, 1)
+    for kw in (dict(batch_threads_per_row=3), dict(batch_tile_rows=32), dict(batch_medium_deg=513),
+               dict(batch_medium_deg=-1)):
+        with pytest.raises(B.PirmcutError) as e:
+            P.Batch([g], **kw)
+        assert e.value.status == B.EINVAL, kw
 
 
 def test_batch_reports_bad_instance(P):
