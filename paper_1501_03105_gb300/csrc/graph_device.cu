@@ -273,18 +273,25 @@ k_pack_dia(int64_t nt, int K, Offsets os, const int64_t* __restrict__ rrp,
   }
 }
 
-// sum of cs in kSumChunks fixed chunks, then the chunks in order (the order
-// the host reduction uses)
-__global__ void __launch_bounds__(kSumChunks)
+// sum of cs in the order the host reduction uses: kSumChunks fixed chunks, a
+// warp per chunk whose lane j runs over the elements a + j, a + j + 32, ...;
+// the lane sums in lane order, then the chunk sums in order.  One block of
+// kSumThreads threads.
+constexpr int kSumThreads = 1024;
+__global__ void __launch_bounds__(kSumThreads)
 k_sum_chunks(const double* __restrict__ v, int64_t n, double* __restrict__ out) {
   __shared__ double part[kSumChunks];
-  const int ch = threadIdx.x;
-  const int64_t a = n * ch / kSumChunks, b = n * (ch + 1) / kSumChunks;
-  double acc = 0.0;
-  for (int64_t i = a; i < b; ++i) acc += v[i];
-  part[ch] = acc;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int ch = w; ch < kSumChunks; ch += kSumThreads / 32) {
+    const int64_t a = n * ch / kSumChunks, b = n * (ch + 1) / kSumChunks;
+    double acc = 0.0;
+    for (int64_t i = a + lane; i < b; i += 32) acc += v[i];
+    double s = 0.0;
+    for (int j = 0; j < 32; ++j) s += __shfl_sync(0xffffffffu, acc, j);
+    if (lane == 0) part[ch] = s;
+  }
   __syncthreads();
-  if (ch == 0) {
+  if (threadIdx.x == 0) {
     double s = 0.0;
     for (int k = 0; k < kSumChunks; ++k) s += part[k];
     *out = s;
@@ -429,7 +436,7 @@ pirmcut_status reduce_graph_device(int64_t n, const int64_t* row_ptr, const int3
                                                       d_ct_t, d_small, d_flags);
   k_check<<<grid_for(nt), kThreads, 0, st>>>(nt, out.rp, out.col, out.cval, out.cs, out.ct, d_cs_s,
                                              d_ct_t, d_flags);
-  k_sum_chunks<<<1, kSumChunks, 0, st>>>(out.cs, nt, d_small + 2);
+  k_sum_chunks<<<1, kSumThreads, 0, st>>>(out.cs, nt, d_small + 2);
   double small[4] = {0, 0, 0, 0};
   if ((e = cudaGetLastError()) != cudaSuccess ||
       (e = cudaMemcpyAsync(&flags, d_flags, sizeof(flags), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||

@@ -121,16 +121,23 @@ void parallel_scan_shifted(const T* in, int64_t n, T* out) {
   }, 1);
 }
 
-// Sum of v[0, n) in a fixed order (256 chunk sums, then the chunks in order),
-// independent of the thread count.
+// Sum of v[0, n) in a fixed order, independent of the thread count (and the
+// order the device reduction of the input uses): 256 chunks; in a chunk
+// [a, b), 32 running sums over the elements a + j, a + j + 32, ... (j < 32),
+// added in order of j; then the chunk sums in order.
 inline double chunked_sum(const double* v, int64_t n) {
-  constexpr int kChunks = 256;
+  constexpr int kChunks = 256, kLanes = 32;
   double part[kChunks];
   parallel_for(kChunks, [&](int64_t lo, int64_t hi) {
     for (int64_t ch = lo; ch < hi; ++ch) {
       const int64_t a = n * ch / kChunks, b = n * (ch + 1) / kChunks;
+      double lane[kLanes] = {0.0};
+      for (int64_t base = a; base < b; base += kLanes) {
+        const int m = int(std::min<int64_t>(kLanes, b - base));
+        for (int j = 0; j < m; ++j) lane[j] += v[base + j];
+      }
       double acc = 0.0;
-      for (int64_t i = a; i < b; ++i) acc += v[i];
+      for (int j = 0; j < kLanes; ++j) acc += lane[j];
       part[ch] = acc;
     }
   }, 1);
