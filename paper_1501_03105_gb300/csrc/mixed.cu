@@ -261,17 +261,39 @@ k_massemble_dia(DiaDesc d, const double* __restrict__ g, MAssemble a) {
   massemble_finish(a, bb);
 }
 
+// CSR row kernels: blocks [0, light_blocks) take the rows with at most
+// heavy_deg entries, G threads per row; each later block takes one heavy row
+// (a power-law hub) with all of its threads.
 template <int G>
 __global__ void __launch_bounds__(kThreads)
 k_massemble_csr(int64_t nt, const int64_t* __restrict__ rp, const double* __restrict__ g,
-                MAssemble a) {
+                MAssemble a, int64_t heavy_deg, const int32_t* __restrict__ heavy,
+                int light_blocks) {
   const double eps = a.initial ? 0.0 : a.eps_list[a.C->eps_idx];
   const double eps2 = eps * eps;
+  double bb = 0.0;
+  if (int(blockIdx.x) >= light_blocks) {
+    const int64_t i = heavy[blockIdx.x - light_blocks];
+    double v[1] = {0.0};
+    for (int64_t e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x) v[0] += g[e];
+    block_sum<1>(v);
+    if (threadIdx.x == 0) {
+      const double xi = a.x[i];
+      double gs = a.cs[i], gt = a.ct[i];
+      if (!a.initial) {
+        gs = conductance(gs, 1.0 - xi, eps2, a.form);
+        gt = conductance(gt, xi, eps2, a.form);
+      }
+      massemble_row(a, i, v[0] + gs + gt, gs, bb);
+    }
+    massemble_finish(a, bb);
+    return;
+  }
   const int lane = threadIdx.x % G;
   const unsigned mask = group_mask<G>();
-  const int64_t ng = gstride() / G;
-  double bb = 0.0;
+  const int64_t ng = int64_t(light_blocks) * blockDim.x / G;
   for (int64_t i = gtid() / G; i < nt; i += ng) {
+    if (rp[i + 1] - rp[i] > heavy_deg) continue;  // the group agrees: same row
     double sum = 0.0;
     for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) sum += g[e];
 #pragma unroll
@@ -305,15 +327,26 @@ k_mscale_dia(DiaDesc d, const double* __restrict__ g, const float* __restrict__ 
   }
 }
 
+// (the product of the two scale factors is formed first, so both directions of
+// an edge get the same bits)
 template <int G>
 __global__ void __launch_bounds__(kThreads)
 k_mscale_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-             const double* __restrict__ g, const float* __restrict__ s32, float* __restrict__ g32) {
-  const int lane = threadIdx.x % G;
-  const int64_t ng = gstride() / G;
-  for (int64_t i = gtid() / G; i < nt; i += ng) {
+             const double* __restrict__ g, const float* __restrict__ s32, float* __restrict__ g32,
+             int64_t heavy_deg, const int32_t* __restrict__ heavy, int light_blocks) {
+  if (int(blockIdx.x) >= light_blocks) {
+    const int64_t i = heavy[blockIdx.x - light_blocks];
     const float si = s32[i];
-    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) g32[e] = float(g[e]) * si * s32[col[e]];
+    for (int64_t e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x)
+      g32[e] = float(g[e]) * (si * s32[col[e]]);
+    return;
+  }
+  const int lane = threadIdx.x % G;
+  const int64_t ng = int64_t(light_blocks) * blockDim.x / G;
+  for (int64_t i = gtid() / G; i < nt; i += ng) {
+    if (rp[i + 1] - rp[i] > heavy_deg) continue;  // the group agrees: same row
+    const float si = s32[i];
+    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) g32[e] = float(g[e]) * (si * s32[col[e]]);
   }
 }
 
@@ -419,13 +452,25 @@ k_resid_dia(DiaDesc d, const double* __restrict__ g, Resid a) {
 template <int G>
 __global__ void __launch_bounds__(kThreads)
 k_resid_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-            const double* __restrict__ g, Resid a) {
+            const double* __restrict__ g, Resid a, int64_t heavy_deg,
+            const int32_t* __restrict__ heavy, int light_blocks) {
   if (a.O->outer_stop) return;
+  FF rr{0.f, 0.f}, ss{0.f, 0.f};
+  if (int(blockIdx.x) >= light_blocks) {
+    const int64_t i = heavy[blockIdx.x - light_blocks];
+    double v[1] = {0.0};
+    for (int64_t e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x)
+      v[0] = fma(-g[e], a.x[col[e]], v[0]);
+    block_sum<1>(v);
+    if (threadIdx.x == 0) resid_row(a, i, fma(a.diag64[i], a.x[i], v[0]), rr, ss);
+    resid_finish(a, rr, ss);
+    return;
+  }
   const int lane = threadIdx.x % G;
   const unsigned mask = group_mask<G>();
-  const int64_t ng = gstride() / G;
-  FF rr{0.f, 0.f}, ss{0.f, 0.f};
+  const int64_t ng = int64_t(light_blocks) * blockDim.x / G;
   for (int64_t i = gtid() / G; i < nt; i += ng) {
+    if (rp[i + 1] - rp[i] > heavy_deg) continue;  // the group agrees: same row
     double acc = 0.0;
     for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) acc = fma(-g[e], a.x[col[e]], acc);
 #pragma unroll
@@ -626,16 +671,34 @@ template <int G>
 __global__ void __launch_bounds__(kThreads)
 k_spmv32_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
              const float* __restrict__ g, const float* __restrict__ p, float* __restrict__ q,
-             double* partials, PcgState* S) {
+             double* partials, PcgState* S, int64_t heavy_deg, const int32_t* __restrict__ heavy,
+             int light_blocks) {
   if (S->stop_req) {
     if (blockIdx.x == 0 && threadIdx.x == 0) S->stopped = 1;
     return;
   }
+  FF pq{0.f, 0.f};
+  if (int(blockIdx.x) >= light_blocks) {
+    const int64_t i = heavy[blockIdx.x - light_blocks];
+    float acc = 0.f;
+    for (int64_t e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x)
+      acc = fmaf(-g[e], p[col[e]], acc);
+    double v[1] = {double(acc)};
+    block_sum<1>(v);
+    if (threadIdx.x == 0) {
+      const float pi = p[i];
+      const float qi = float(v[0]) + pi;
+      q[i] = qi;
+      ff_fma(pq, pi, qi);
+    }
+    spmv32_finish(pq, partials, S);
+    return;
+  }
   const int lane = threadIdx.x % G;
   const unsigned mask = group_mask<G>();
-  const int64_t ng = gstride() / G;
-  FF pq{0.f, 0.f};
+  const int64_t ng = int64_t(light_blocks) * blockDim.x / G;
   for (int64_t i = gtid() / G; i < nt; i += ng) {
+    if (rp[i + 1] - rp[i] > heavy_deg) continue;  // the group agrees: same row
     float acc = 0.f;
     for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) acc = fmaf(-g[e], p[col[e]], acc);
 #pragma unroll
@@ -790,9 +853,11 @@ int enqueue_massemble(Ctx& c, cudaStream_t st, bool initial) {
     PIRMCUT_DISPATCH_K(c.K, (k_massemble_dia<KK><<<grid, kThreads, 0, st>>>(c.dd, c.gdia, a)));
     PIRMCUT_DISPATCH_K(c.K, (k_mscale_dia<KK><<<grid, kThreads, 0, st>>>(c.dd, c.gdia, c.s32, c.g32)));
   } else {
-    PIRMCUT_DISPATCH_G(c.group, (k_massemble_csr<GG><<<grid, kThreads, 0, st>>>(c.nt, c.rp, c.gval, a)));
-    PIRMCUT_DISPATCH_G(c.group, (k_mscale_csr<GG><<<grid, kThreads, 0, st>>>(c.nt, c.rp, c.col, c.gval,
-                                                                             c.s32, c.g32)));
+    PIRMCUT_DISPATCH_G(c.group, (k_massemble_csr<GG><<<grid + c.n_heavy, kThreads, 0, st>>>(
+                                    c.nt, c.rp, c.gval, a, c.heavy_deg, c.heavy, grid)));
+    PIRMCUT_DISPATCH_G(c.group, (k_mscale_csr<GG><<<grid + c.n_heavy, kThreads, 0, st>>>(
+                                    c.nt, c.rp, c.col, c.gval, c.s32, c.g32, c.heavy_deg, c.heavy,
+                                    grid)));
   }
   return 2;
 }
@@ -817,7 +882,8 @@ int enqueue_resid(Ctx& c, cudaStream_t st, cudaGraphConditionalHandle ho,
   if (c.format == PIRMCUT_FORMAT_DIA) {
     PIRMCUT_DISPATCH_K(c.K, (k_resid_dia<KK><<<grid, kThreads, 0, st>>>(c.dd, c.gdia, a)));
   } else {
-    PIRMCUT_DISPATCH_G(c.group, (k_resid_csr<GG><<<grid, kThreads, 0, st>>>(c.nt, c.rp, c.col, c.gval, a)));
+    PIRMCUT_DISPATCH_G(c.group, (k_resid_csr<GG><<<grid + c.n_heavy, kThreads, 0, st>>>(
+                                    c.nt, c.rp, c.col, c.gval, a, c.heavy_deg, c.heavy, grid)));
   }
   return 1;
 }
@@ -830,8 +896,9 @@ int enqueue_spmv32(Ctx& c, cudaStream_t st) {
     PIRMCUT_DISPATCH_K(c.K, (k_spmv32_dia<KK><<<row_grid(c), kThreads, 0, st>>>(
                                 c.dd, c.g32, c.p32, c.q32, c.partials, c.S)));
   } else {
-    PIRMCUT_DISPATCH_G(c.group, (k_spmv32_csr<GG><<<row_grid(c), kThreads, 0, st>>>(
-                                    c.nt, c.rp, c.col, c.g32, c.p32, c.q32, c.partials, c.S)));
+    PIRMCUT_DISPATCH_G(c.group, (k_spmv32_csr<GG><<<row_grid(c) + c.n_heavy, kThreads, 0, st>>>(
+                                    c.nt, c.rp, c.col, c.g32, c.p32, c.q32, c.partials, c.S,
+                                    c.heavy_deg, c.heavy, row_grid(c))));
   }
   return 1;
 }

@@ -145,11 +145,30 @@ k_features_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __rest
                const double* __restrict__ g, const double* __restrict__ gprev,
                const double* __restrict__ cs, const double* __restrict__ ct,
                const double* __restrict__ x, const double* __restrict__ eps_list,
-               const StepCounters* __restrict__ C, int form, float* __restrict__ f) {
+               const StepCounters* __restrict__ C, int form, float* __restrict__ f,
+               int64_t heavy_deg, const int32_t* __restrict__ heavy, int light_blocks) {
   const double eps = eps_list[C->eps_idx];
   const double eps2 = eps * eps;
+  if (int(blockIdx.x) >= light_blocks) {  // one heavy row (a hub) for the whole block
+    const int64_t i = heavy[blockIdx.x - light_blocks];
+    double wsum = 0.0, wx = 0.0, wxx = 0.0;
+    float lr = 0.0f;
+    int nlr = 0;
+    for (int64_t e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x)
+      edge_feature(g[e], gprev[e], x[col[e]], wsum, wx, wxx, lr, nlr);
+    double v[5] = {wsum, wx, wxx, double(lr), double(nlr)};
+    block_sum<5>(v);
+    if (threadIdx.x == 0) {
+      const double xi = x[i];
+      const double gs = conductance(cs[i], 1.0 - xi, eps2, form);
+      const double gt = conductance(ct[i], xi, eps2, form);
+      finish_features(f, i, xi, v[0], v[1], v[2], float(v[3]), int(v[4]), gs, gt, eps);
+    }
+    return;
+  }
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nt;
-       i += int64_t(gridDim.x) * blockDim.x) {
+       i += int64_t(light_blocks) * blockDim.x) {
+    if (rp[i + 1] - rp[i] > heavy_deg) continue;
     const double xi = x[i];
     double wsum = 0.0, wx = 0.0, wxx = 0.0;
     float lr = 0.0f;
@@ -268,12 +287,37 @@ k_linesearch_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __re
                  const double* __restrict__ g, const double* __restrict__ cs,
                  const double* __restrict__ ct, const double* __restrict__ x,
                  const double* __restrict__ dir, const double* __restrict__ eps_list,
-                 const StepCounters* __restrict__ C, int form, double* partials, MlpState* M) {
+                 const StepCounters* __restrict__ C, int form, double* partials, MlpState* M,
+                 int64_t heavy_deg, const int32_t* __restrict__ heavy, int light_blocks) {
   const double eps = eps_list[C->eps_idx];
   const double eps2 = eps * eps;
   double dr = 0.0, dad = 0.0, rr = 0.0;
+  if (int(blockIdx.x) >= light_blocks) {  // one heavy row (a hub) for the whole block
+    const int64_t i = heavy[blockIdx.x - light_blocks];
+    double v[3] = {0.0, 0.0, 0.0};  // sum of g, (g, x), (g, d) over the row
+    for (int64_t e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x) {
+      const double w = g[e];
+      v[0] += w;
+      v[1] = fma(w, x[col[e]], v[1]);
+      v[2] = fma(w, dir[col[e]], v[2]);
+    }
+    block_sum<3>(v);
+    if (threadIdx.x == 0) {
+      const double xi = x[i], di = dir[i];
+      const double gs = conductance(cs[i], 1.0 - xi, eps2, form);
+      const double gt = conductance(ct[i], xi, eps2, form);
+      const double sum = v[0] + (gs + gt);
+      const double r = gs - fma(sum, xi, -v[1]);
+      dr = di * r;
+      dad = di * fma(sum, di, -v[2]);
+      rr = r * r;
+    }
+    linesearch_finish(dr, dad, rr, partials, M);
+    return;
+  }
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nt;
-       i += int64_t(gridDim.x) * blockDim.x) {
+       i += int64_t(light_blocks) * blockDim.x) {
+    if (rp[i + 1] - rp[i] > heavy_deg) continue;
     const double xi = x[i], di = dir[i];
     const double gs = conductance(cs[i], 1.0 - xi, eps2, form);
     const double gt = conductance(ct[i], xi, eps2, form);
@@ -523,8 +567,9 @@ int enqueue_mlp_post(Ctx& c, cudaStream_t st) {
     PIRMCUT_DISPATCH_K(c.K, (k_features_dia<KK><<<grid, kThreads, 0, st>>>(
                                 c.dd, c.gdia, b.gprev, c.cs, c.ct, c.x, c.eps_list, c.C, form, b.feat)));
   } else {
-    k_features_csr<<<grid, kThreads, 0, st>>>(c.nt, c.rp, c.col, c.gval, b.gprev, c.cs, c.ct, c.x,
-                                              c.eps_list, c.C, form, b.feat);
+    k_features_csr<<<grid + c.n_heavy, kThreads, 0, st>>>(c.nt, c.rp, c.col, c.gval, b.gprev, c.cs,
+                                                          c.ct, c.x, c.eps_list, c.C, form, b.feat,
+                                                          c.heavy_deg, c.heavy, grid);
   }
   if (!(c.mlp_mode & PIRMCUT_MLP_PREDICT)) return 1;
   k_mlp_predict<false><<<grid, kThreads, sizeof(float) * NPARAM, st>>>(c.nt, b.feat, b.w16, b.dir,
@@ -534,8 +579,10 @@ int enqueue_mlp_post(Ctx& c, cudaStream_t st) {
                                 c.dd, c.gdia, c.cs, c.ct, c.x, b.dir, c.eps_list, c.C, form,
                                 c.partials, b.state)));
   } else {
-    k_linesearch_csr<<<grid, kThreads, 0, st>>>(c.nt, c.rp, c.col, c.gval, c.cs, c.ct, c.x, b.dir,
-                                                c.eps_list, c.C, form, c.partials, b.state);
+    k_linesearch_csr<<<grid + c.n_heavy, kThreads, 0, st>>>(c.nt, c.rp, c.col, c.gval, c.cs, c.ct,
+                                                            c.x, b.dir, c.eps_list, c.C, form,
+                                                            c.partials, b.state, c.heavy_deg,
+                                                            c.heavy, grid);
   }
   k_mlp_commit<<<grid, kThreads, 0, st>>>(c.nt, b.state, b.dir, c.x);
   return 4;

@@ -334,16 +334,18 @@ def test_sweep_with_a_hub_row(P):
             assert abs(value_b - O.sweep_cut(prob, b.get_x(i))["value"]) <= 1e-9 * value_b
 
 
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("form", [0, 1])
-def test_steps_with_a_hub_row(P, form):
-    """Teacher-forced IRLS steps on CSR with a hub row: the reweighting,
-    assembly, scaling and SpMV kernels give the hub a block of its own."""
+def test_steps_with_a_hub_row(P, form, precision):
+    """Teacher-forced IRLS steps on CSR with a hub row, FP64 and mixed: the
+    reweighting, assembly, scaling, residual and SpMV kernels give the hub a
+    block of its own."""
     g = _hub_graph()
     prob = O.Problem.from_graph(g)
     T = 8
     eps = O.eps_schedule(T)
     xs, _ = O.irls(prob, T, eps, form=form)
-    with solver(P, g, format=2, reweight_form=form) as s:
+    with solver(P, g, format=2, reweight_form=form, precision=precision) as s:
         for l in range(1, T + 1):
             s.set_x(xs[l - 1])
             info = s.irls_step(eps[l - 1])

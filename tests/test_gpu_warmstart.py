@@ -37,11 +37,27 @@ def P():
     return pkg
 
 
+def hub_graph(n_nt=1500, seed=17):
+    """A sparse random graph plus one hub joined to every other non-terminal:
+    a CSR row longer than max(512, 16 x mean), processed by a block of its own."""
+    g = gen.random_graph(n_nt, 4.0 / n_nt, seed)
+    rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    m = rows < g.col
+    u, v, c = rows[m], g.col[m].astype(np.int64), g.c[m]
+    others = np.setdiff1d(np.arange(1, n_nt), np.r_[v[u == 0], u[v == 0]])
+    u = np.r_[u, np.zeros(others.shape, dtype=np.int64)]
+    v = np.r_[v, others]
+    c = np.r_[c, np.random.default_rng(seed).uniform(0.01, 0.05, others.shape[0])]
+    rp, col, cc = gen.csr_from_edges(g.n, u, v, c)
+    return gen.Graph(g.n, rp, col, cc, g.s, g.t)
+
+
 GRAPHS = [
     ("grid16", lambda: gen.config_graph(1, scale=16)),
     ("vol8", lambda: gen.config_graph(3, scale=8)),
     ("random40", lambda: gen.random_graph(40, 0.1, 12)),
     ("chunglu", lambda: gen.chung_lu_instance(600, 5)),
+    ("hub1500", hub_graph),
 ]
 
 
@@ -160,10 +176,11 @@ def test_untrained_model_is_bit_identical_to_the_plain_start(P, fmt):
 
 @pytest.mark.parametrize("fmt", [0, 2])
 @pytest.mark.parametrize("delta", [-1 / 32, 1 / 64])
-def test_constant_direction_line_search(P, fmt, delta):
+@pytest.mark.parametrize("name", ["grid24", "hub1500"])
+def test_constant_direction_line_search(P, fmt, delta, name):
     """d = const (only b3 set): the line search is exact on both sides; alpha,
     the energy change, the plain residual and the solution follow the oracle."""
-    g = gen.config_graph(1, scale=24)
+    g = gen.config_graph(1, scale=24) if name == "grid24" else hub_graph()
     prob = O.Problem.from_graph(g)
     T = 6
     eps = O.eps_schedule(T)
