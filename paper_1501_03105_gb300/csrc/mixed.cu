@@ -296,8 +296,7 @@ k_massemble_csr(int64_t nt, const int64_t* __restrict__ rp, const double* __rest
     if (rp[i + 1] - rp[i] > heavy_deg) continue;  // the group agrees: same row
     double sum = 0.0;
     for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) sum += g[e];
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_down_sync(mask, sum, o, G);
+    sum = group_sum<G>(sum, mask);
     if (lane == 0) {
       const double xi = a.x[i];
       double gs = a.cs[i], gt = a.ct[i];
@@ -473,8 +472,7 @@ k_resid_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restric
     if (rp[i + 1] - rp[i] > heavy_deg) continue;  // the group agrees: same row
     double acc = 0.0;
     for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) acc = fma(-g[e], a.x[col[e]], acc);
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(mask, acc, o, G);
+    acc = group_sum<G>(acc, mask);
     if (lane == 0) resid_row(a, i, fma(a.diag64[i], a.x[i], acc), rr, ss);
   }
   resid_finish(a, rr, ss);

@@ -282,8 +282,12 @@ k_assemble_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __rest
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
-      sum += __shfl_down_sync(mask, sum, o, G);
-      ax += __shfl_down_sync(mask, ax, o, G);
+      const double s2 = __shfl_down_sync(mask, sum, o, G);
+      const double a2 = __shfl_down_sync(mask, ax, o, G);
+      if (lane < o) {
+        sum += s2;
+        ax += a2;
+      }
     }
     if (lane == 0) {
       const double xi = x[i];
@@ -419,7 +423,10 @@ k_spmv_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict
     double acc = 0.0;
     for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) acc = fma(-g[e], p[col[e]], acc);
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(mask, acc, o, G);
+    for (int o = G / 2; o > 0; o >>= 1) {
+      const double w = __shfl_down_sync(mask, acc, o, G);
+      if (lane < o) acc += w;
+    }
     if (lane == 0) {
       const double pi = p[i];
       acc += pi;
@@ -503,12 +510,18 @@ k_update_xp(int64_t nt, double* __restrict__ x, double* __restrict__ p,
 
 __device__ __forceinline__ double warp_min(double v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    const double w = __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) < o) v = fmin(v, w);
+  }
   return v;
 }
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    const double w = __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) < o) v = fmax(v, w);
+  }
   return v;
 }
 

@@ -288,8 +288,7 @@ k_delta_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restric
       const double w = c[e];
       acc += (ri < rank[col[e]]) ? w : -w;
     }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(mask, acc, o, G);
+    acc = group_sum<G>(acc, mask);
     if (lane == 0) delta[i] = (ct[i] - cs[i]) + acc;
   }
 }
@@ -485,8 +484,7 @@ k_cut_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict_
         const int32_t j = col[e];
         if (j > i && a.side[j] != si) t += c[e];
       }
-#pragma unroll
-      for (int o = G / 2; o > 0; o >>= 1) t += __shfl_down_sync(mask, t, o, G);
+      t = group_sum<G>(t, mask);
       if (lane == 0) acc += t + (si ? a.ct[i] : a.cs[i]);
     }
   }
