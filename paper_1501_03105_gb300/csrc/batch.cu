@@ -109,10 +109,7 @@ __device__ __forceinline__ bool inst_sum(const BArgs& a, const Tile& tl, double 
 template <int G>
 __device__ __forceinline__ double group_reduce(double v, unsigned mask) {
 #pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-    const double w = __shfl_down_sync(mask, v, o, G);
-    if (int(threadIdx.x % G) < o) v += w;
-  }
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_down_sync(mask, v, o, G);
   return v;
 }
 
@@ -415,12 +412,8 @@ kb_step_end(BArgs a, const double* __restrict__ x, StepRec* recs, int rec_cap,
   __shared__ unsigned int s_last;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double a = __shfl_down_sync(0xffffffffu, mn, o);
-    const double b = __shfl_down_sync(0xffffffffu, mx, o);
-    if (int(threadIdx.x & 31) < o) {
-      mn = fmin(mn, a);
-      mx = fmax(mx, b);
-    }
+    mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+    mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {

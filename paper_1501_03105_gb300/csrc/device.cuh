@@ -44,28 +44,23 @@ struct DiaDesc {
 };
 
 // Tree sums into the first lane of a warp or of a G-lane group (G divides
-// 32).  Every lane takes part in the shuffles, but only the lanes whose sum is
-// still needed add: GB300 spends its narrow FP64 pipe per active lane, and a
-// full butterfly would spend five adds per lane where one suffices.  The first
-// lane's result is the same tree either way.
+// 32), in a fixed order.
 __device__ __forceinline__ double warp_sum(double v) {
-  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double w = __shfl_down_sync(0xffffffffu, v, o);
-    if (lane < o) v += w;
-  }
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
 
 template <int G>
 __device__ __forceinline__ double group_sum(double v, unsigned mask) {
-  const int lane = threadIdx.x % G;
 #pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-    const double w = __shfl_down_sync(mask, v, o, G);
-    if (lane < o) v += w;
-  }
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_down_sync(mask, v, o, G);
   return v;
 }
 

@@ -32,10 +32,12 @@
 #include "ctx.h"
 
 // Resident blocks per SM the FP64 PCG-iteration kernels are launched with
-// (the grid is capped at 152 times this); fewer, longer-running blocks spend
-// less of GB300's FP64 pipe on the per-block reduction trees.
+// (the grid is capped at 152 times this): fewer, longer-running blocks spend
+// less of GB300's FP64 pipe on the per-block reduction trees, more keep more
+// loads in flight.  On the 2048x2048 grid (x^(0) + 50 steps) 4, 5, 6, 7 and 8
+// blocks gave 151, 141, 137-138, 146 and 148 ms.
 #ifndef PIRMCUT_FP64_BLOCKS_PER_SM
-#define PIRMCUT_FP64_BLOCKS_PER_SM 8
+#define PIRMCUT_FP64_BLOCKS_PER_SM 6
 #endif
 
 namespace pirmcut {
@@ -282,12 +284,8 @@ k_assemble_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __rest
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
-      const double s2 = __shfl_down_sync(mask, sum, o, G);
-      const double a2 = __shfl_down_sync(mask, ax, o, G);
-      if (lane < o) {
-        sum += s2;
-        ax += a2;
-      }
+      sum += __shfl_down_sync(mask, sum, o, G);
+      ax += __shfl_down_sync(mask, ax, o, G);
     }
     if (lane == 0) {
       const double xi = x[i];
@@ -422,11 +420,7 @@ k_spmv_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict
     if (rp[i + 1] - rp[i] > heavy_deg) continue;  // the group agrees: same row
     double acc = 0.0;
     for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) acc = fma(-g[e], p[col[e]], acc);
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-      const double w = __shfl_down_sync(mask, acc, o, G);
-      if (lane < o) acc += w;
-    }
+    acc = group_sum<G>(acc, mask);
     if (lane == 0) {
       const double pi = p[i];
       acc += pi;
@@ -435,6 +429,50 @@ k_spmv_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict
     }
   }
   spmv_finish(pq, partials, S);
+}
+
+// grid_sum<2> for an FP64 sum a and an FP32 sum b: within a block b takes an
+// FP32 tree (its FP64 adds would be a third of the residual update's FP64
+// work), the last block adds the block partials of both in FP64.
+__device__ __forceinline__ bool grid_sum_df(double a, float b, double* partials,
+                                            unsigned int* counter, double (&tot)[2]) {
+  __shared__ double sa[32];
+  __shared__ float sb[32];
+  __shared__ unsigned int s_last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  a = warp_sum(a);
+  b = warp_sum_f(b);
+  if (lane == 0) {
+    sa[wid] = a;
+    sb[wid] = b;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    a = warp_sum(lane < nw ? sa[lane] : 0.0);
+    b = warp_sum_f(lane < nw ? sb[lane] : 0.0f);
+  }
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = a;
+    partials[gridDim.x + blockIdx.x] = double(b);
+    __threadfence();
+    s_last = (atomicAdd(counter, 1u) == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  double acc[2] = {0.0, 0.0};
+  for (unsigned int k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
+    acc[0] += __ldcg(partials + k);
+    acc[1] += __ldcg(partials + gridDim.x + k);
+  }
+  block_sum<2>(acc);
+  if (threadIdx.x == 0) {
+    tot[0] = acc[0];
+    tot[1] = acc[1];
+    *counter = 0u;
+  }
+  return true;
 }
 
 // r^ -= alpha q; (r^, r^) and ||r||^2 = sum_v d_v r^_v^2 -> beta, stop.  The
@@ -457,8 +495,9 @@ k_update_r(int64_t nt, const double* __restrict__ q, const float* __restrict__ s
       rz = fma(ri, ri, rz);
       rr = fma(diag[i] * ri, ri, rr);
     }
-  } else {
-    float rr32 = 0.0f;
+  }
+  float rr32 = 0.0f;
+  if (!fp64_norm) {
     for (int64_t i = gtid(); i < nt; i += gstride()) {
       const double ri = fma(-alpha, q[i], r[i]);
       r[i] = ri;
@@ -466,10 +505,16 @@ k_update_r(int64_t nt, const double* __restrict__ q, const float* __restrict__ s
       const float ui = sq32[i] * abs_f32_scaled(ri, sh);
       rr32 = fmaf(ui, ui, rr32);
     }
-    rr = double(rr32);
   }
-  double v[2] = {rz, rr}, tot[2];
-  if (grid_sum<2>(v, partials, &S->counter[2], tot) && threadIdx.x == 0) {
+  double tot[2];
+  bool last;
+  if (fp64_norm) {
+    double v[2] = {rz, rr};
+    last = grid_sum<2>(v, partials, &S->counter[2], tot);
+  } else {
+    last = grid_sum_df(rz, rr32, partials, &S->counter[2], tot);
+  }
+  if (last && threadIdx.x == 0) {
     const int it = S->iters + 1;
     S->iters = it;
     const double beta = tot[0] / S->rz;
@@ -510,18 +555,12 @@ k_update_xp(int64_t nt, double* __restrict__ x, double* __restrict__ p,
 
 __device__ __forceinline__ double warp_min(double v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double w = __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) < o) v = fmin(v, w);
-  }
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
   return v;
 }
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double w = __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) < o) v = fmax(v, w);
-  }
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
   return v;
 }
 
