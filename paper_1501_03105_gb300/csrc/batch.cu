@@ -300,7 +300,7 @@ kb_spmv(BArgs a, const double* __restrict__ g, const double* __restrict__ diag,
     for (int64_t m = tl.r0 + threadIdx.x / 32; m < tl.r1; m += kBT / 32) {
       const int64_t r = a.med[m];
       double acc = 0.0;
-      for (int64_t e = a.rp[r] + lane; e < a.rp[r + 1]; e += 32) acc = fma(-g[e], p[base + a.col[e]], acc);
+      acc = row_dot_neg(g, a.col, p + base, a.rp[r] + lane, a.rp[r + 1], 32, acc);
       acc = group_reduce<32>(acc, 0xffffffffu);
       if (lane == 0) {
         const double pr = p[r];
@@ -315,7 +315,7 @@ kb_spmv(BArgs a, const double* __restrict__ g, const double* __restrict__ diag,
     for (int64_t r = tl.r0 + threadIdx.x / G; r < tl.r1; r += kBT / G) {
       if (deg_of(a, r) > a.mid_deg) continue;
       double acc = 0.0;
-      for (int64_t e = a.rp[r] + lane; e < a.rp[r + 1]; e += G) acc = fma(-g[e], p[base + a.col[e]], acc);
+      acc = row_dot_neg(g, a.col, p + base, a.rp[r] + lane, a.rp[r + 1], G, acc);
       acc = group_reduce<G>(acc, mask);
       if (lane == 0) {
         const double pr = p[r];

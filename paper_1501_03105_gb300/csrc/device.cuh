@@ -64,6 +64,27 @@ __device__ __forceinline__ double group_sum(double v, unsigned mask) {
   return v;
 }
 
+// acc - sum of g[e] p[col[e]] over e = e, e + S, ... < e1, added in that
+// order; the column indices and gathers of four entries are issued before
+// their FMAs, so that each thread keeps several loads in flight (CSR rows are
+// short and their gathers dependent on the index loads).
+__device__ __forceinline__ double row_dot_neg(const double* __restrict__ g,
+                                              const int32_t* __restrict__ col,
+                                              const double* __restrict__ p, int64_t e, int64_t e1,
+                                              int S, double acc) {
+  for (; e + 3 * S < e1; e += 4 * S) {
+    const int32_t c0 = col[e], c1 = col[e + S], c2 = col[e + 2 * S], c3 = col[e + 3 * S];
+    const double g0 = g[e], g1 = g[e + S], g2 = g[e + 2 * S], g3 = g[e + 3 * S];
+    const double p0 = p[c0], p1 = p[c1], p2 = p[c2], p3 = p[c3];
+    acc = fma(-g0, p0, acc);
+    acc = fma(-g1, p1, acc);
+    acc = fma(-g2, p2, acc);
+    acc = fma(-g3, p3, acc);
+  }
+  for (; e < e1; e += S) acc = fma(-g[e], p[col[e]], acc);
+  return acc;
+}
+
 // Sum NV doubles over the block; the result is valid in thread 0.
 // Fixed tree: the sum is bit-identical from run to run.
 template <int NV>

@@ -46,6 +46,14 @@ namespace {
 
 constexpr int kFp64MaxBlocks = 152 * PIRMCUT_FP64_BLOCKS_PER_SM;
 
+// Grid of the SpMV: the cap above on DIA (bound by the FP64 pipe); on CSR,
+// whose gathers are latency-bound, every resident block.
+inline int spmv_grid(const Ctx& c) {
+  const int rg = row_grid(c);
+  const int cap = c.format == PIRMCUT_FORMAT_DIA ? kFp64MaxBlocks : kMaxBlocks;
+  return rg < cap ? rg : cap;
+}
+
 __device__ __forceinline__ int64_t gtid() {
   return int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
 }
@@ -419,7 +427,7 @@ k_spmv_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict
   for (int64_t i = gtid() / G; i < nt; i += ng) {
     if (rp[i + 1] - rp[i] > heavy_deg) continue;  // the group agrees: same row
     double acc = 0.0;
-    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) acc = fma(-g[e], p[col[e]], acc);
+    acc = row_dot_neg(g, col, p, rp[i] + lane, rp[i + 1], G, acc);
     acc = group_sum<G>(acc, mask);
     if (lane == 0) {
       const double pi = p[i];
@@ -698,8 +706,7 @@ cudaError_t launch_gather_x(Ctx& c, const double* xfull) {
 }
 
 cudaError_t launch_spmv_once(Ctx& c) {
-  const int rg = row_grid(c);
-  const int grid = rg < kFp64MaxBlocks ? rg : kFp64MaxBlocks;
+  const int grid = spmv_grid(c);
   if (c.format == PIRMCUT_FORMAT_DIA) {
     PIRMCUT_DISPATCH_K(c.K, (k_spmv_dia<KK><<<grid, kThreads, 0, c.stream>>>(
                                 c.dd, c.ghat, c.p, c.q, c.partials, c.S)));
@@ -802,8 +809,8 @@ int enqueue_prologue(Ctx& c, cudaStream_t st, bool initial, cudaGraphConditional
 // bracket the spmv launch).
 int enqueue_iteration(Ctx& c, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond,
                       cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
-  const int rg = row_grid(c), vg = grid_for(c.nt);
-  const int grid = rg < kFp64MaxBlocks ? rg : kFp64MaxBlocks;
+  const int vg = grid_for(c.nt);
+  const int grid = spmv_grid(c);
   const int vgrid = vg < kFp64MaxBlocks ? vg : kFp64MaxBlocks;
   if (e0) cudaEventRecord(e0, st);
   if (c.format == PIRMCUT_FORMAT_DIA) {
