@@ -713,7 +713,11 @@ void free_batch(Batch& b) {
 // Autotuner: time the batched SpMV (capacities as conductances) for each
 // (threads per row, tile height, medium-row threshold) candidate and keep the
 // fastest.  A medium threshold equal to the hub threshold disables that tier.
-// A value fixed in the options replaces its list of candidates.
+// A value fixed in the options replaces its list of candidates.  The timing
+// runs with every instance active, but most PCG iterations of a step run with
+// few instances left, where each tile costs a block launch that finds nothing
+// to do; so a taller tile height (fewer tiles) is kept unless a shorter one
+// is more than 10 % faster.
 cudaError_t autotune(Batch& b) {
   std::vector<int> Gs = {1, 2, 4, 8, 16, 32}, Ts = {512, 2048};
   std::vector<int64_t> Ms = {16, 32, 64, b.heavy_deg};
@@ -758,7 +762,9 @@ cudaError_t autotune(Batch& b) {
       }
       if (e == cudaSuccess) e = cudaGetLastError();
       if (e != cudaSuccess) break;
-      if (tot < best) {
+      const bool taller = T > bestT, shorter = T < bestT;
+      if ((taller && tot < best * 1.1f) || (shorter && tot < best * 0.9f) ||
+          (!taller && !shorter && tot < best)) {
         best = tot;
         bestG = G;
         bestT = T;
