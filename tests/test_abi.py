@@ -51,6 +51,17 @@ def test_default_options(lib):
     o = B.pirmcut_default_options()
     assert o.reweight_form == B.REWEIGHT_WEIGHTED_L1 and o.precision == B.PREC_FP64
     assert o.pcg_tol == 1e-10 and o.pcg_max_iter == 20000 and o.warm_start == 1
+    assert o.track_cut == 0 and o.graph_launch == 1 and o.inner_tol == 1e-5
+    assert o.time_spmv == 0 and o.reduce_on_host == 0
+    assert (o.batch_threads_per_row, o.batch_tile_rows, o.batch_medium_deg) == (0, 0, 0)
+
+
+def test_batch_options_are_checked_before_any_gpu_work(lib):
+    from paper_1501_03105_gb300 import binding as B
+    g = gen.random_graph(10, 0.3, 1)
+    for kw in (dict(precision=B.PREC_MIXED), dict(batch_threads_per_row=3),
+               dict(batch_tile_rows=32), dict(batch_tile_rows=70000), dict(batch_medium_deg=513)):
+        _expect(B.EINVAL, B.Batch, [g], **kw)
 
 
 def _expect(status, fn, *a, **k):
