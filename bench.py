@@ -259,7 +259,7 @@ def run_batch(args):
     T = 50
     eps = eps_list(T)
     stream = torch.cuda.current_stream()
-    opt = B.pirmcut_default_options(pcg_tol=PCG_TOL)
+    opt = B.pirmcut_default_options(pcg_tol=PCG_TOL, graph_launch=0 if args.launch == "stream" else 1)
     e_inst = []
     for g in graphs:
         rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))

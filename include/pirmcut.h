@@ -85,9 +85,10 @@ typedef struct {
   int graph_launch;    /* 1: each step is one CUDA graph whose PCG loop is a
                           device-side WHILE node (no host sync inside a solve);
                           0: the same kernels launched one by one from the host,
-                          PCG iterations in chunks of 8 with the stop flag read
-                          back between chunks (for profilers that cannot see
-                          into conditional graph nodes)                       */
+                          PCG iterations in chunks of 8 with the stop flag (for
+                          batches: the number of active instances) read back
+                          between chunks (for profilers that cannot see into
+                          conditional graph nodes); the results are identical */
   double inner_tol;    /* MIXED only: each FP32 inner solve reduces its residual
                           by this factor (or just enough for the FP64 test)   */
   int time_spmv;       /* 1 (with graph_launch 0): bracket every PCG

@@ -518,7 +518,7 @@ struct Batch {
   double* partials = nullptr;
   int* active = nullptr;
   StepCounters* C = nullptr;
-  StepCounters* h_ctr = nullptr;
+  StepCounters* h_ctr = nullptr;  // pinned; followed by one int, the active-instance count read back in stream mode
   double* eps_list = nullptr;
   int eps_cap = 0;
   StepRec* recs = nullptr;
@@ -905,7 +905,8 @@ pirmcut_status pirmcut_batch_create(int count, const int64_t* n, const int64_t* 
   if (e == cudaSuccess) e = cudaMemcpy(b.ct, ctv.data(), sizeof(double) * b.N, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(b.S, 0, sizeof(PcgState) * count);
   if (e == cudaSuccess) e = cudaMemset(b.C, 0, sizeof(StepCounters));
-  if (e == cudaSuccess) e = cudaHostAlloc((void**)&b.h_ctr, sizeof(StepCounters), cudaHostAllocDefault);
+  if (e == cudaSuccess)
+    e = cudaHostAlloc((void**)&b.h_ctr, sizeof(StepCounters) + sizeof(int), cudaHostAllocDefault);
   if (e != cudaSuccess) return bail(e, "upload");
   // hub rows: more entries than 32 threads can cover in 16 passes
   b.heavy_deg = kHubDeg;
@@ -940,8 +941,9 @@ pirmcut_status pirmcut_batch_solve(pirmcut_batch* h, int T, const double* eps, p
     if (b.g_step) cudaGraphExecDestroy(b.g_step);
     b.g_init = b.g_step = nullptr;
   }
-  if (!b.g_init) BCK(h, build_bgraph(b, true, &b.g_init), "building the batch x0 graph");
-  if (!b.g_step) BCK(h, build_bgraph(b, false, &b.g_step), "building the batch step graph");
+  const bool graphs = b.opt.graph_launch != 0;
+  if (graphs && !b.g_init) BCK(h, build_bgraph(b, true, &b.g_init), "building the batch x0 graph");
+  if (graphs && !b.g_step) BCK(h, build_bgraph(b, false, &b.g_step), "building the batch step graph");
   if (T > 0) BCK(h, cudaMemcpyAsync(b.eps_list, eps, sizeof(double) * T, cudaMemcpyHostToDevice, b.stream), "eps");
   std::memset(b.h_ctr, 0, sizeof(StepCounters));
   BCK(h, cudaMemcpyAsync(b.C, b.h_ctr, sizeof(StepCounters), cudaMemcpyHostToDevice, b.stream), "counters");
@@ -951,10 +953,29 @@ pirmcut_status pirmcut_batch_solve(pirmcut_batch* h, int T, const double* eps, p
     b.events.push_back(ev);
   }
   BCK(h, cudaEventRecord(b.events[0], b.stream), "event");
+  int64_t stream_kernels = 0;
   for (int k = 0; k <= T; ++k) {
-    BCK(h, cudaGraphLaunch(k == 0 ? b.g_init : b.g_step, b.stream), "graph launch");
+    if (graphs) {
+      BCK(h, cudaGraphLaunch(k == 0 ? b.g_init : b.g_step, b.stream), "graph launch");
+    } else {
+      // the same kernels from the host: PCG iterations in chunks of 8, the
+      // number of active instances read back between chunks; iterations queued
+      // after the last instance stopped are no-ops (the kernels test the flags)
+      cudaGraphConditionalHandle none{};
+      int* h_active = reinterpret_cast<int*>(b.h_ctr + 1);
+      stream_kernels += enqueue_bstep(b, b.stream, k == 0, none, 0, 0);
+      for (int guard = 0;; ++guard) {
+        for (int j = 0; j < 8; ++j) stream_kernels += enqueue_bstep(b, b.stream, k == 0, none, 0, 1);
+        BCK(h, cudaMemcpyAsync(h_active, b.active, sizeof(int), cudaMemcpyDeviceToHost, b.stream), "active");
+        BCK(h, cudaStreamSynchronize(b.stream), "batch step");
+        if (*h_active == 0 || guard > b.opt.pcg_max_iter / 8 + 2) break;
+      }
+      stream_kernels += enqueue_bstep(b, b.stream, k == 0, none, 0, 2);
+      BCK(h, cudaGetLastError(), "batch step launch");
+    }
     BCK(h, cudaEventRecord(b.events[k + 1], b.stream), "event");
   }
+  b.launches += stream_kernels;
   BCK(h, cudaMemcpyAsync(b.h_recs, b.recs, sizeof(StepRec) * b.rec_cap * b.count, cudaMemcpyDeviceToHost, b.stream), "records");
   BCK(h, cudaStreamSynchronize(b.stream), "batch solve");
   b.x_set = true;
@@ -983,7 +1004,7 @@ pirmcut_status pirmcut_batch_solve(pirmcut_batch* h, int T, const double* eps, p
       if (st == PIRMCUT_ENUMERIC) worst = PIRMCUT_ENUMERIC;
       else if (st == PIRMCUT_ENOCONV && worst == PIRMCUT_OK) worst = PIRMCUT_ENOCONV;
     }
-    b.launches += 8 + 3 * (it_total + 1);
+    if (graphs) b.launches += 8 + 3 * (it_total + 1);
   }
   if (worst != PIRMCUT_OK) return bfail(h, worst, "an instance did not converge or broke down");
   return PIRMCUT_OK;

@@ -101,6 +101,26 @@ def test_batch_single_instance_and_repeat(P):
     assert [i.pcg_iters for i in a1[0]] == [i.pcg_iters for i in a2[0]]
 
 
+def test_batch_stream_launch_matches_graph_launch(P):
+    """graph_launch = 0 runs the same kernels from the host (chunks of 8
+    iterations): bit-identical iterates, iteration counts and cuts."""
+    graphs = [gen.chung_lu_instance(1500, 31, float32_caps=True), gen.config_graph(1, scale=18),
+              gen.random_graph(30, 0.2, 4)]
+    T = 6
+    eps = O.eps_schedule(T)
+    out = []
+    for mode in (1, 0):
+        with P.Batch(graphs, pcg_tol=1e-12, graph_launch=mode, batch_threads_per_row=2,
+                     batch_tile_rows=512, batch_medium_deg=16) as b:
+            infos = b.solve(T, eps)
+            out.append(([b.get_x(i) for i in range(len(graphs))],
+                        [[x.pcg_iters for x in inf] for inf in infos],
+                        [b.cut(i)[1] for i in range(len(graphs))]))
+    for xa, xb in zip(out[0][0], out[1][0]):
+        assert np.array_equal(xa, xb)
+    assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
+
+
 def test_batch_rejects_bad_tiling_options(P):
     from paper_1501_03105_gb300 import binding as B
     g = gen.random_graph(10, 0.3, 1)
