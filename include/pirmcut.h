@@ -105,6 +105,9 @@ typedef struct {
                           warp tier off); 0 = chosen by the autotuner          */
   int batch_tile_rows;
   int batch_medium_deg;
+  int step_stats;      /* 1: every step also records its objective and flow
+                          value in pirmcut_step_info (one more pass over the
+                          edges per step); batches leave them NaN             */
 } pirmcut_options;
 
 typedef struct {
@@ -118,11 +121,18 @@ typedef struct {
   int status;          /* pirmcut_status of the step                          */
   int refinements;     /* MIXED: FP64 refinement cycles (FP64 residuals that
                           started an inner solve); 0 for FP64                 */
+  double objective;    /* with options.step_stats: the smoothed objective
+                          S_eps(x^(l)) of the reweighting form (Eq.
+                          l1-min-smooth-version; eps = 0 for step 0), over the
+                          edges of positive capacity; else NaN               */
+  double flow_value;   /* with options.step_stats: x^T L(g^(l)) x, the value of
+                          the electrical flow of the step's system (Prop.
+                          wls-equal-electrical-flow); else NaN               */
 } pirmcut_step_info;
 
 /* Fill *opt with the defaults: WEIGHTED_L1, FP64, pcg_tol 1e-10,
  * pcg_max_iter 20000, warm_start 1, FORMAT_AUTO, track_cut 0, graph_launch 1,
- * inner_tol 1e-5, time_spmv 0, reduce_on_host 0, batch_* 0.  With MIXED,
+ * inner_tol 1e-5, time_spmv 0, reduce_on_host 0, batch_* 0, step_stats 0.  With MIXED,
  * pcg_iters counts FP32 inner iterations, at most
  * min(pcg_max_iter, 2000) per refinement cycle and 64 cycles per system. */
 void pirmcut_default_options(pirmcut_options* opt);

@@ -36,14 +36,16 @@ class Options(ctypes.Structure):
                 ("track_cut", ctypes.c_int), ("graph_launch", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("time_spmv", ctypes.c_int),
                 ("reduce_on_host", ctypes.c_int), ("batch_threads_per_row", ctypes.c_int),
-                ("batch_tile_rows", ctypes.c_int), ("batch_medium_deg", ctypes.c_int)]
+                ("batch_tile_rows", ctypes.c_int), ("batch_medium_deg", ctypes.c_int),
+                ("step_stats", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int), ("pcg_iters", ctypes.c_int), ("eps", ctypes.c_double),
                 ("rel_residual", ctypes.c_double), ("x_min", ctypes.c_double),
                 ("x_max", ctypes.c_double), ("cut_value", ctypes.c_double),
-                ("ms", ctypes.c_double), ("status", ctypes.c_int), ("refinements", ctypes.c_int)]
+                ("ms", ctypes.c_double), ("status", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("objective", ctypes.c_double), ("flow_value", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -43,7 +43,8 @@ cudaError_t dalloc(T** p, size_t count) {
 
 void free_device(Ctx& c) {
   void* ps[] = {c.cdia, c.gdia, c.rp, c.col, c.cval, c.gval, c.cs, c.ct, c.x, c.r, c.p,
-                c.q, c.diag, c.rsd, c.sq32, c.xs, c.ghat, c.heavy, c.partials, c.S, c.C, c.eps_list,
+                c.q, c.diag, c.rsd, c.sq32, c.xs, c.ghat, c.xstats, c.heavy, c.partials, c.S, c.C,
+                c.eps_list,
                 c.recs, c.xfull, c.side_full, c.d_in_rp, c.d_in_col};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -86,6 +87,10 @@ pirmcut_status check_options(const pirmcut_options& o, std::string* msg) {
   }
   if (o.format < PIRMCUT_FORMAT_AUTO || o.format > PIRMCUT_FORMAT_CSR) {
     *msg = "unknown format";
+    return PIRMCUT_EINVAL;
+  }
+  if (o.step_stats != 0 && o.step_stats != 1) {
+    *msg = "step_stats must be 0 or 1";
     return PIRMCUT_EINVAL;
   }
   return PIRMCUT_OK;
@@ -203,6 +208,8 @@ void fill_info(const Ctx& c, const pirmcut::StepRec& r, float ms, pirmcut_step_i
     st = PIRMCUT_ENOCONV;
   info->status = st;
   info->refinements = r.refine;
+  info->objective = r.obj;
+  info->flow_value = r.flow;
 }
 
 // Run x^(0) (when with_initial) and the eps steps already in eps_list[0..T).
@@ -333,6 +340,7 @@ pirmcut_status finish_create(pirmcut_ctx* h, const pirmcut_options& o, void* str
   double** vecs[] = {&cx.x, &cx.r, &cx.p, &cx.q, &cx.diag};
   for (double** v : vecs)
     if ((e = dalloc(v, nt)) != cudaSuccess) return bail(e, "cudaMalloc");
+  if (o.step_stats && (e = dalloc(&cx.xstats, nt)) != cudaSuccess) return bail(e, "cudaMalloc");
   if (o.precision == PIRMCUT_PREC_FP64) {
     if ((e = dalloc(&cx.rsd, nt)) != cudaSuccess) return bail(e, "cudaMalloc");
     if ((e = dalloc(&cx.xs, nt)) != cudaSuccess) return bail(e, "cudaMalloc");
@@ -444,6 +452,7 @@ void pirmcut_default_options(pirmcut_options* opt) {
   opt->batch_threads_per_row = 0;
   opt->batch_tile_rows = 0;
   opt->batch_medium_deg = 0;
+  opt->step_stats = 0;
 }
 
 pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* col,

@@ -454,6 +454,8 @@ kb_step_end(BArgs a, const double* __restrict__ x, StepRec* recs, int rec_cap,
   rec.cut = NAN;
   rec.status = S->status;
   rec.refine = 0;
+  rec.obj = NAN;
+  rec.flow = NAN;
   recs[size_t(tl.inst) * rec_cap + C->rec_idx] = rec;
 }
 
@@ -999,6 +1001,8 @@ pirmcut_status pirmcut_batch_solve(pirmcut_batch* h, int T, const double* eps, p
       if (st == PIRMCUT_OK && r.bb > 0.0 && !(r.rr <= b.opt.pcg_tol * b.opt.pcg_tol * r.bb)) st = PIRMCUT_ENOCONV;
       info.status = st;
       info.refinements = 0;
+      info.objective = r.obj;
+      info.flow_value = r.flow;
       if (infos) infos[size_t(i) * (T + 1) + k] = info;
       it_total = std::max<int64_t>(it_total, r.iters);
       if (st == PIRMCUT_ENUMERIC) worst = PIRMCUT_ENUMERIC;

@@ -24,6 +24,8 @@ struct StepRec {
   double cut;
   int status;
   int refine;   // FP64 refinement cycles (mixed precision), 0 otherwise
+  double obj;   // S_eps(x^(l)) and x^T L(g^(l)) x with options.step_stats, else NaN
+  double flow;
 };
 
 // State of the FP64 iterative-refinement loop around the FP32 inner PCG.
@@ -150,6 +152,7 @@ struct Ctx {
   float* sq32 = nullptr;        // d_v^1/2 in FP32 (norm of the stopping test)
   double* xs = nullptr;         // scaled iterate D^1/2 x
   double* ghat = nullptr;       // scaled conductances g_uv d_u^-1/2 d_v^-1/2 (DIA K*nt or CSR nnz)
+  double* xstats = nullptr;     // x at the start of a step (options.step_stats)
   PcgState* S = nullptr;
   // mixed precision: FP32 CG on the Jacobi-scaled system D^-1/2 L~ D^-1/2
   // (unit diagonal) inside FP64 iterative refinement
@@ -212,6 +215,8 @@ struct PcgProgress {
   int iters, maxit, stop_req;
 };
 int enqueue_step_end(Ctx& c, cudaStream_t st, bool initial, const OuterState* O);
+// options.step_stats: keep x^(l-1) at the start of a step (a copy, no kernel)
+void enqueue_stats_pre(Ctx& c, cudaStream_t st);
 cudaError_t build_step_graph(Ctx& c, bool initial, cudaGraphExec_t* out, int* nodes);
 cudaError_t run_step_stream(Ctx& c, bool initial, int* stop_flag_host, int64_t* kernels);
 cudaError_t launch_scatter_x(Ctx& c, double* xfull);           // reduced x -> full n

@@ -1034,6 +1034,7 @@ cudaError_t build_step_graph_mixed(Ctx& c, bool initial, cudaGraphExec_t* out, i
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&ho, graph, 1, cudaGraphCondAssignDefault);
   if (e == cudaSuccess) {
     const bool mlp = mlp_active(c, initial);
+    enqueue_stats_pre(c, st);
     if (mlp) n_nodes += enqueue_mlp_pre(c, st);
     n_nodes += enqueue_reweight(c, st, initial);
     if (mlp) n_nodes += enqueue_mlp_post(c, st);
@@ -1090,6 +1091,7 @@ cudaError_t run_step_stream_mixed(Ctx& c, bool initial, int* flag_host, int64_t*
   cudaStream_t st = c.stream;
   cudaGraphConditionalHandle none{};
   const bool mlp = mlp_active(c, initial);
+  enqueue_stats_pre(c, st);
   int64_t k = mlp ? enqueue_mlp_pre(c, st) : 0;
   k += enqueue_reweight(c, st, initial);
   if (mlp) k += enqueue_mlp_post(c, st);

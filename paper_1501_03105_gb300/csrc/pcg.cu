@@ -650,10 +650,135 @@ k_step_end(int64_t nt, double* __restrict__ x, const double* __restrict__ xs,
   rec.cut = NAN;
   rec.status = S->status;
   rec.refine = O ? O->outer_iters : 0;
+  rec.obj = NAN;
+  rec.flow = NAN;
   recs[C->rec_idx] = rec;
   C->rec_idx += 1;
   C->step += 1;
   if (consumes_eps) C->eps_idx += 1;
+}
+
+// ---------------------------------------------------------------------------
+// per-step objective and flow value (options.step_stats)
+// ---------------------------------------------------------------------------
+
+// Term of edge e in S_eps (Eq. l1-min-smooth-version): weighted-l1 form
+// c sqrt(d^2 + eps^2), the paper's form sqrt((c d)^2 + eps^2); edges of zero
+// capacity are not told apart from absent ones in the packed storage and
+// count 0 in both forms.
+__device__ __forceinline__ double edge_objective(double c, double d, double eps2, int form) {
+  if (form == PIRMCUT_REWEIGHT_PAPER) {
+    const double cd = c * d;
+    return c > 0.0 ? sqrt(fma(cd, cd, eps2)) : 0.0;
+  }
+  return c * sqrt(fma(d, d, eps2));
+}
+
+struct StatsArgs {
+  const double* cs;
+  const double* ct;
+  const double* x;   // x^(l), after the step
+  const double* xw;  // x^(l-1): the point the step's conductances came from
+  const double* eps_list;
+  const StepCounters* C;
+  StepRec* recs;
+  double* partials;
+  unsigned int* counter;
+  double c_st;       // the direct s-t edge (d = 1)
+  int form;
+  int initial;       // x^(0): g = c and eps = 0
+};
+
+// the terminal edges of row i: objective and flow terms (x_s = 1, x_t = 0)
+__device__ __forceinline__ void stats_terminals(const StatsArgs& a, int64_t i, double xi,
+                                                double eps2, double& obj, double& flow) {
+  const double cs = a.cs[i], ct = a.ct[i];
+  double gs = cs, gt = ct;
+  if (!a.initial) {
+    const double wi = a.xw[i];
+    gs = conductance(cs, 1.0 - wi, eps2, a.form);
+    gt = conductance(ct, wi, eps2, a.form);
+  }
+  const double ds = 1.0 - xi;
+  obj += edge_objective(cs, ds, eps2, a.form) + edge_objective(ct, xi, eps2, a.form);
+  flow = fma(gs * ds, ds, flow);
+  flow = fma(gt * xi, xi, flow);
+}
+
+__device__ __forceinline__ double stats_eps2(const StatsArgs& a) {
+  const double eps = a.initial ? 0.0 : a.eps_list[a.C->eps_idx - 1];  // the step end advanced it
+  return eps * eps;
+}
+
+__device__ __forceinline__ void stats_finish(const StatsArgs& a, double obj, double flow) {
+  double v[2] = {obj, flow}, tot[2];
+  if (grid_sum<2>(v, a.partials, a.counter, tot) && threadIdx.x == 0) {
+    const double eps2 = stats_eps2(a);
+    double o = tot[0], f = tot[1];
+    if (a.c_st > 0.0) {
+      o += edge_objective(a.c_st, 1.0, eps2, a.form);
+      f += a.initial ? a.c_st : conductance(a.c_st, 1.0, eps2, a.form);
+    }
+    StepRec& r = a.recs[a.C->rec_idx - 1];
+    r.obj = o;
+    r.flow = f;
+  }
+}
+
+// each undirected edge once: DIA rows own their upper diagonals
+template <int K>
+__global__ void __launch_bounds__(kThreads)
+k_step_stats_dia(DiaDesc d, const double* __restrict__ c, const double* __restrict__ g,
+                 StatsArgs a) {
+  const int64_t nt = d.nt;
+  const double eps2 = stats_eps2(a);
+  double obj = 0.0, flow = 0.0;
+  for (int64_t i = gtid(); i < nt; i += gstride()) {
+    const double xi = a.x[i];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int64_t j = i + d.off[k];
+      if (j < nt) {
+        const double dd = xi - a.x[j];
+        obj += edge_objective(c[k * nt + i], dd, eps2, a.form);
+        flow = fma(g[k * nt + i] * dd, dd, flow);
+      }
+    }
+    stats_terminals(a, i, xi, eps2, obj, flow);
+  }
+  stats_finish(a, obj, flow);
+}
+
+// each undirected edge once: the entry (i, j) with j > i
+template <int G>
+__global__ void __launch_bounds__(kThreads)
+k_step_stats_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                 const double* __restrict__ c, const double* __restrict__ g, StatsArgs a) {
+  const double eps2 = stats_eps2(a);
+  const int lane = threadIdx.x % G;
+  const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
+  const int64_t ng = gstride() / G;
+  double obj = 0.0, flow = 0.0;
+  for (int64_t i = gtid() / G; i < nt; i += ng) {
+    const double xi = a.x[i];
+    double o = 0.0, f = 0.0;
+    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) {
+      const int32_t j = col[e];
+      if (j > i) {
+        const double dd = xi - a.x[j];
+        o += edge_objective(c[e], dd, eps2, a.form);
+        f = fma(g[e] * dd, dd, f);
+      }
+    }
+    o = group_sum<G>(o, mask);
+    f = group_sum<G>(f, mask);
+    if (lane == 0) {
+      obj += o;
+      flow += f;
+      stats_terminals(a, i, xi, eps2, obj, flow);
+    }
+  }
+  stats_finish(a, obj, flow);
 }
 
 // ---------------------------------------------------------------------------
@@ -748,13 +873,41 @@ int enqueue_reweight(Ctx& c, cudaStream_t st, bool initial) {
 }
 
 // Epilogue of a step: x from the scaled iterate (FP64 path), range of x and
-// the step record.
+// the step record; with options.step_stats, the objective and flow value.
 int enqueue_step_end(Ctx& c, cudaStream_t st, bool initial, const OuterState* O) {
   const bool scaled = c.opt.precision == PIRMCUT_PREC_FP64;
   k_step_end<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.x, scaled ? c.xs : nullptr,
                                                   scaled ? c.rsd : nullptr, c.S, c.C, c.recs,
                                                   c.eps_list, initial ? 0 : 1, c.partials, O);
-  return 1;
+  if (!c.opt.step_stats) return 1;
+  StatsArgs a;
+  a.cs = c.cs;
+  a.ct = c.ct;
+  a.x = c.x;
+  a.xw = c.xstats;
+  a.eps_list = c.eps_list;
+  a.C = c.C;
+  a.recs = c.recs;
+  a.partials = c.partials;
+  // the step end's last-block counter, released by that block before this launch
+  a.counter = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(c.S) +
+                                              offsetof(PcgState, counter) + 3 * sizeof(unsigned int));
+  a.c_st = c.hg.c_st;
+  a.form = c.opt.reweight_form;
+  a.initial = initial ? 1 : 0;
+  if (c.format == PIRMCUT_FORMAT_DIA) {
+    PIRMCUT_DISPATCH_K(c.K, (k_step_stats_dia<KK><<<grid_for(c.nt), kThreads, 0, st>>>(
+                                c.dd, c.cdia, c.gdia, a)));
+  } else {
+    PIRMCUT_DISPATCH_G(c.group, (k_step_stats_csr<GG><<<row_grid(c), kThreads, 0, st>>>(
+                                    c.nt, c.rp, c.col, c.cval, c.gval, a)));
+  }
+  return 2;
+}
+
+void enqueue_stats_pre(Ctx& c, cudaStream_t st) {
+  if (c.opt.step_stats)
+    cudaMemcpyAsync(c.xstats, c.x, sizeof(double) * size_t(c.nt), cudaMemcpyDeviceToDevice, st);
 }
 
 namespace {
@@ -768,6 +921,7 @@ int enqueue_prologue(Ctx& c, cudaStream_t st, bool initial, cudaGraphConditional
   const bool zero_start = initial || !c.opt.warm_start;
   const bool mlp = mlp_active(c, initial);
   double* g = c.format == PIRMCUT_FORMAT_DIA ? c.gdia : c.gval;
+  enqueue_stats_pre(c, st);
   int kernels = mlp ? enqueue_mlp_pre(c, st) : 0;
   kernels += enqueue_reweight(c, st, initial);
   if (mlp) kernels += enqueue_mlp_post(c, st);

@@ -99,6 +99,38 @@ def test_teacher_forced_steps_grid64(P, form, fmt):
             assert info.x_min >= -1e-12 and info.x_max <= 1 + 1e-12
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("fmt", [0, 2])
+def test_step_objective_and_flow_value(P, fmt, form, precision):
+    """options.step_stats: each step's record holds S_eps(x^(l)) and the flow
+    value x^T L(g^(l)) x of the returned iterate, as the oracle computes them
+    from that iterate (Eq. l1-min-smooth-version, Prop.
+    wls-equal-electrical-flow); step 0 uses eps = 0 and g = c.  Off: NaN."""
+    g = gen.config_graph(1)
+    prob = O.Problem.from_graph(g)
+    T = 10
+    eps = O.eps_schedule(T)
+    xs, _ = O.irls(prob, T, eps, form=form)
+    with solver(P, g, format=fmt, reweight_form=form, precision=precision, step_stats=1) as s:
+        info = s.initial()
+        x = s.get_x()
+        assert info.objective == pytest.approx(O.smoothed_objective(prob, x, 0.0, form), rel=1e-12)
+        assert info.flow_value == pytest.approx(O.flow_value(prob, x, O.initial_conductance(prob)), rel=1e-12)
+        for l in range(1, T + 1):
+            s.set_x(xs[l - 1])
+            info = s.irls_step(eps[l - 1])
+            x = s.get_x()
+            gl = O.reweight(prob, xs[l - 1], eps[l - 1], form)
+            assert info.objective == pytest.approx(O.smoothed_objective(prob, x, eps[l - 1], form), rel=1e-12), l
+            assert info.flow_value == pytest.approx(O.flow_value(prob, x, gl), rel=1e-11), l
+            # the MM step: the objective does not rise along the step (reading c12)
+            assert info.objective <= O.smoothed_objective(prob, xs[l - 1], eps[l - 1], form) * (1 + 1e-12)
+    with solver(P, g, format=fmt) as s:
+        info = s.initial()
+        assert np.isnan(info.objective) and np.isnan(info.flow_value)
+
+
 @pytest.mark.parametrize("name,make", GRAPHS)
 def test_teacher_forced_steps_small(P, name, make):
     g = make()
