@@ -623,6 +623,29 @@ pirmcut_status pirmcut_set_x(pirmcut_ctx* h, const double* x, int mem_kind) {
   return PIRMCUT_OK;
 }
 
+namespace {
+// After new capacities: the sweep graph bakes c(s,t) and cut(0), and with
+// options.step_stats the step graphs bake c(s,t) into the statistics kernel's
+// arguments; drop the graphs that hold a stale value (they are rebuilt on
+// the next use).
+void drop_graphs_baking_cst(Ctx& c, double old_cst) {
+  if (c.g_cut) {
+    cudaGraphExecDestroy(c.g_cut);
+    c.g_cut = nullptr;
+  }
+  if (c.opt.step_stats && !(c.hg.c_st == old_cst)) {
+    if (c.g_init) {
+      cudaGraphExecDestroy(c.g_init);
+      c.g_init = nullptr;
+    }
+    if (c.g_step) {
+      cudaGraphExecDestroy(c.g_step);
+      c.g_step = nullptr;
+    }
+  }
+}
+}  // namespace
+
 pirmcut_status pirmcut_update_weights(pirmcut_ctx* h, const double* cnew, int mem_kind) {
   if (!h) return fail(nullptr, PIRMCUT_EINVAL, "ctx is NULL");
   Ctx& c = h->c;
@@ -661,11 +684,9 @@ pirmcut_status pirmcut_update_weights(pirmcut_ctx* h, const double* cnew, int me
       if (ce == cudaSuccess) ce = cudaStreamSynchronize(c.stream);
       dg.release();
       if (ce != cudaSuccess) return cuda_fail(h, ce, "updating the capacities");
+      const double old_cst = c.hg.c_st;
       c.hg = std::move(ng);
-      if (c.g_cut) {
-        cudaGraphExecDestroy(c.g_cut);
-        c.g_cut = nullptr;
-      }
+      drop_graphs_baking_cst(c, old_cst);
       return PIRMCUT_OK;
     }
     // host reduction of the device-resident structure
@@ -688,6 +709,7 @@ pirmcut_status pirmcut_update_weights(pirmcut_ctx* h, const double* cnew, int me
   bool same = ng.format == c.format && ng.nt == c.nt && ng.K == c.K && ng.nnz == c.hg.nnz;
   for (int k = 0; same && k < c.K; ++k) same = ng.off[k] == c.hg.off[k];
   if (!same) return fail(h, PIRMCUT_EINVAL, "the new capacities change the stored structure");
+  const double old_cst = c.hg.c_st;
   c.hg = std::move(ng);
   if (c.format == PIRMCUT_FORMAT_CSR) {
     CK(h, cudaMemcpyAsync(c.cval, c.hg.cval.data(), sizeof(double) * c.hg.cval.size(), cudaMemcpyHostToDevice, c.stream), "upload");
@@ -697,11 +719,7 @@ pirmcut_status pirmcut_update_weights(pirmcut_ctx* h, const double* cnew, int me
   CK(h, cudaMemcpyAsync(c.cs, c.hg.cs.data(), sizeof(double) * c.nt, cudaMemcpyHostToDevice, c.stream), "upload");
   CK(h, cudaMemcpyAsync(c.ct, c.hg.ct.data(), sizeof(double) * c.nt, cudaMemcpyHostToDevice, c.stream), "upload");
   CK(h, cudaStreamSynchronize(c.stream), "upload");
-  // the sweep graph bakes c(s,t) and cut(0)
-  if (c.g_cut) {
-    cudaGraphExecDestroy(c.g_cut);
-    c.g_cut = nullptr;
-  }
+  drop_graphs_baking_cst(c, old_cst);
   return PIRMCUT_OK;
 }
 

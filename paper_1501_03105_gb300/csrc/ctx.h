@@ -216,7 +216,7 @@ struct PcgProgress {
 };
 int enqueue_step_end(Ctx& c, cudaStream_t st, bool initial, const OuterState* O);
 // options.step_stats: keep x^(l-1) at the start of a step (a copy, no kernel)
-void enqueue_stats_pre(Ctx& c, cudaStream_t st);
+cudaError_t enqueue_stats_pre(Ctx& c, cudaStream_t st);
 cudaError_t build_step_graph(Ctx& c, bool initial, cudaGraphExec_t* out, int* nodes);
 cudaError_t run_step_stream(Ctx& c, bool initial, int* stop_flag_host, int64_t* kernels);
 cudaError_t launch_scatter_x(Ctx& c, double* xfull);           // reduced x -> full n

@@ -1034,13 +1034,13 @@ cudaError_t build_step_graph_mixed(Ctx& c, bool initial, cudaGraphExec_t* out, i
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&ho, graph, 1, cudaGraphCondAssignDefault);
   if (e == cudaSuccess) {
     const bool mlp = mlp_active(c, initial);
-    enqueue_stats_pre(c, st);
+    e = enqueue_stats_pre(c, st);
     if (mlp) n_nodes += enqueue_mlp_pre(c, st);
     n_nodes += enqueue_reweight(c, st, initial);
     if (mlp) n_nodes += enqueue_mlp_post(c, st);
     n_nodes += enqueue_massemble(c, st, initial);
     if (initial || !c.opt.warm_start) cudaMemsetAsync(c.x, 0, sizeof(double) * c.nt, st);
-    e = add_while(st, ho, &out_node, &out_body);
+    if (e == cudaSuccess) e = add_while(st, ho, &out_node, &out_body);
   }
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hi, out_body, 0, cudaGraphCondAssignDefault);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
@@ -1091,13 +1091,14 @@ cudaError_t run_step_stream_mixed(Ctx& c, bool initial, int* flag_host, int64_t*
   cudaStream_t st = c.stream;
   cudaGraphConditionalHandle none{};
   const bool mlp = mlp_active(c, initial);
-  enqueue_stats_pre(c, st);
+  const cudaError_t ep = enqueue_stats_pre(c, st);
   int64_t k = mlp ? enqueue_mlp_pre(c, st) : 0;
   k += enqueue_reweight(c, st, initial);
   if (mlp) k += enqueue_mlp_post(c, st);
   k += enqueue_massemble(c, st, initial);
   if (initial || !c.opt.warm_start) cudaMemsetAsync(c.x, 0, sizeof(double) * c.nt, st);
   cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = ep;
   const size_t off_o = offsetof(OuterState, outer_stop);
   const size_t off_s = offsetof(PcgState, iters);
   PcgProgress* prog = reinterpret_cast<PcgProgress*>(flag_host);

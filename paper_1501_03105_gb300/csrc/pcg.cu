@@ -749,17 +749,42 @@ k_step_stats_dia(DiaDesc d, const double* __restrict__ c, const double* __restri
   stats_finish(a, obj, flow);
 }
 
-// each undirected edge once: the entry (i, j) with j > i
+// each undirected edge once: the entry (i, j) with j > i.  Blocks
+// [0, light_blocks) take the rows with at most heavy_deg entries, G threads
+// per row; each later block takes one heavy row (a hub) with all its threads.
 template <int G>
 __global__ void __launch_bounds__(kThreads)
 k_step_stats_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                 const double* __restrict__ c, const double* __restrict__ g, StatsArgs a) {
+                 const double* __restrict__ c, const double* __restrict__ g, StatsArgs a,
+                 int64_t heavy_deg, const int32_t* __restrict__ heavy, int light_blocks) {
   const double eps2 = stats_eps2(a);
-  const int lane = threadIdx.x % G;
-  const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
-  const int64_t ng = gstride() / G;
   double obj = 0.0, flow = 0.0;
+  if (int(blockIdx.x) >= light_blocks) {
+    const int64_t i = heavy[blockIdx.x - light_blocks];
+    const double xi = a.x[i];
+    double v[2] = {0.0, 0.0};
+    for (int64_t e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x) {
+      const int32_t j = col[e];
+      if (j > i) {
+        const double dd = xi - a.x[j];
+        v[0] += edge_objective(c[e], dd, eps2, a.form);
+        v[1] = fma(g[e] * dd, dd, v[1]);
+      }
+    }
+    block_sum<2>(v);
+    if (threadIdx.x == 0) {
+      obj = v[0];
+      flow = v[1];
+      stats_terminals(a, i, xi, eps2, obj, flow);
+    }
+    stats_finish(a, obj, flow);
+    return;
+  }
+  const int lane = threadIdx.x % G;
+  const unsigned mask = group_mask<G>();
+  const int64_t ng = int64_t(light_blocks) * blockDim.x / G;
   for (int64_t i = gtid() / G; i < nt; i += ng) {
+    if (rp[i + 1] - rp[i] > heavy_deg) continue;  // the group agrees: same row
     const double xi = a.x[i];
     double o = 0.0, f = 0.0;
     for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) {
@@ -899,15 +924,17 @@ int enqueue_step_end(Ctx& c, cudaStream_t st, bool initial, const OuterState* O)
     PIRMCUT_DISPATCH_K(c.K, (k_step_stats_dia<KK><<<grid_for(c.nt), kThreads, 0, st>>>(
                                 c.dd, c.cdia, c.gdia, a)));
   } else {
-    PIRMCUT_DISPATCH_G(c.group, (k_step_stats_csr<GG><<<row_grid(c), kThreads, 0, st>>>(
-                                    c.nt, c.rp, c.col, c.cval, c.gval, a)));
+    const int grid = row_grid(c);
+    PIRMCUT_DISPATCH_G(c.group, (k_step_stats_csr<GG><<<grid + c.n_heavy, kThreads, 0, st>>>(
+                                    c.nt, c.rp, c.col, c.cval, c.gval, a, c.heavy_deg, c.heavy,
+                                    grid)));
   }
   return 2;
 }
 
-void enqueue_stats_pre(Ctx& c, cudaStream_t st) {
-  if (c.opt.step_stats)
-    cudaMemcpyAsync(c.xstats, c.x, sizeof(double) * size_t(c.nt), cudaMemcpyDeviceToDevice, st);
+cudaError_t enqueue_stats_pre(Ctx& c, cudaStream_t st) {
+  if (!c.opt.step_stats) return cudaSuccess;
+  return cudaMemcpyAsync(c.xstats, c.x, sizeof(double) * size_t(c.nt), cudaMemcpyDeviceToDevice, st);
 }
 
 namespace {
@@ -916,12 +943,12 @@ namespace {
 //   [keep x^(l-1), g^(l-1)] -> [c -> g | reweight] -> [features, learned start]
 //   -> assemble -> scale.
 int enqueue_prologue(Ctx& c, cudaStream_t st, bool initial, cudaGraphConditionalHandle h,
-                     int use_cond) {
+                     int use_cond, cudaError_t* err) {
   const int grid = row_grid(c);
   const bool zero_start = initial || !c.opt.warm_start;
   const bool mlp = mlp_active(c, initial);
   double* g = c.format == PIRMCUT_FORMAT_DIA ? c.gdia : c.gval;
-  enqueue_stats_pre(c, st);
+  *err = enqueue_stats_pre(c, st);
   int kernels = mlp ? enqueue_mlp_pre(c, st) : 0;
   kernels += enqueue_reweight(c, st, initial);
   if (mlp) kernels += enqueue_mlp_post(c, st);
@@ -1004,9 +1031,10 @@ cudaError_t build_step_graph(Ctx& c, bool initial, cudaGraphExec_t* out, int* no
     if (dummy) cudaGraphDestroy(dummy);
     return e;
   }
-  n_nodes += enqueue_prologue(c, st, initial, h, 1);
+  cudaError_t ep = cudaSuccess;
+  n_nodes += enqueue_prologue(c, st, initial, h, 1, &ep);
   // WHILE node holding one PCG iteration
-  e = cudaStreamGetCaptureInfo(st, &cst, nullptr, &graph, &deps, nullptr, &ndeps);
+  e = ep != cudaSuccess ? ep : cudaStreamGetCaptureInfo(st, &cst, nullptr, &graph, &deps, nullptr, &ndeps);
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = h;
@@ -1047,8 +1075,10 @@ cudaError_t build_step_graph(Ctx& c, bool initial, cudaGraphExec_t* out, int* no
 cudaError_t run_step_stream(Ctx& c, bool initial, int* stop_flag_host, int64_t* kernels) {
   cudaStream_t st = c.stream;
   cudaGraphConditionalHandle none{};
-  int64_t k = enqueue_prologue(c, st, initial, none, 0);
+  cudaError_t ep = cudaSuccess;
+  int64_t k = enqueue_prologue(c, st, initial, none, 0, &ep);
   cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = ep;
   static_assert(offsetof(PcgState, maxit) == offsetof(PcgState, iters) + sizeof(int) &&
                     offsetof(PcgState, stop_req) == offsetof(PcgState, iters) + 2 * sizeof(int),
                 "iters, maxit, stop_req are read back together");

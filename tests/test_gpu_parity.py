@@ -131,6 +131,71 @@ def test_step_objective_and_flow_value(P, fmt, form, precision):
         assert np.isnan(info.objective) and np.isnan(info.flow_value)
 
 
+def objective_positive(prob, x, eps, form):
+    """S_eps(x) over the edges of positive capacity: the form the library
+    records.  The packed storage does not tell a listed edge of capacity 0
+    from an absent one, so such an edge counts 0; in the paper's form the
+    oracle's sum gives each of them sqrt((0 d)^2 + eps^2) = eps, which is
+    taken out here (the weighted-l1 form gives them 0 already)."""
+    m0 = int(np.count_nonzero(prob.cap == 0.0))
+    s = O.smoothed_objective(prob, x, eps, form)
+    return s - m0 * eps if form == O.PAPER else s
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("name,make", GRAPHS)
+def test_step_objective_and_flow_value_graphs(P, name, make, form, precision):
+    """The step statistics on every small graph: zero capacities
+    (random12), a direct s-t edge (random12), CSR rows of every length and a
+    hub row (chunglu), DIA grids and volumes; teacher-forced steps."""
+    g = make()
+    prob = O.Problem.from_graph(g)
+    T = 8
+    eps = O.eps_schedule(T)
+    xs, _ = O.irls(prob, T, eps, form=form)
+    with solver(P, g, reweight_form=form, precision=precision, step_stats=1) as s:
+        info = s.initial()
+        x = s.get_x()
+        assert info.objective == pytest.approx(objective_positive(prob, x, 0.0, form), rel=1e-12)
+        assert info.flow_value == pytest.approx(O.flow_value(prob, x, O.initial_conductance(prob)), rel=1e-11)
+        for l in range(1, T + 1):
+            s.set_x(xs[l - 1])
+            info = s.irls_step(eps[l - 1])
+            x = s.get_x()
+            gl = O.reweight(prob, xs[l - 1], eps[l - 1], form)
+            assert info.objective == pytest.approx(objective_positive(prob, x, eps[l - 1], form), rel=1e-12), l
+            assert info.flow_value == pytest.approx(O.flow_value(prob, x, gl), rel=1e-11), l
+
+
+@pytest.mark.parametrize("graph_launch", [1, 0])
+def test_step_stats_after_update_weights_st_edge(P, graph_launch):
+    """A sequence on one structure (Section 6) with a direct s-t edge whose
+    capacity changes: after pirmcut_update_weights every step's objective and
+    flow value use the new c(s,t) (the step graphs are rebuilt)."""
+    g = gen.random_graph(30, 0.15, 21, st_edge=True)
+    T = 4
+    eps = O.eps_schedule(T)
+    with solver(P, g, step_stats=1, graph_launch=graph_launch) as s:
+        for k, scale in enumerate([1.0, 3.0, 0.25]):
+            c = g.c.copy()
+            rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+            st = ((rows == g.s) & (g.col == g.t)) | ((rows == g.t) & (g.col == g.s))
+            assert st.sum() == 2
+            c[st] *= scale
+            prob = O.Problem(g.n, g.row_ptr, g.col, c, g.s, g.t)
+            if k:
+                s.update_weights(c)
+            infos = s.solve(T, eps)
+            xs, _ = O.irls(prob, T, eps)
+            for l in range(T + 1):
+                e = eps[l - 1] if l else 0.0
+                gl = O.initial_conductance(prob) if l == 0 else O.reweight(prob, xs[l - 1], e)
+                # free-running: the GPU and the oracle iterates agree to the solver tolerance
+                assert infos[l].objective == pytest.approx(objective_positive(prob, xs[l], e, 0), rel=1e-9), (k, l)
+                assert infos[l].flow_value == pytest.approx(O.flow_value(prob, xs[l], gl), rel=1e-9), (k, l)
+
+
 @pytest.mark.parametrize("name,make", GRAPHS)
 def test_teacher_forced_steps_small(P, name, make):
     g = make()

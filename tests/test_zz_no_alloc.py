@@ -1,4 +1,5 @@
-"""The allocation-free sweep cut (pirmcut_sweep_cut_static) against pirmcut_cut.
+"""The allocation-free sweep cut (pirmcut_sweep_cut_static) against pirmcut_cut
+and against the oracle's sweep cut (Section 3.3).
 
 Some callers cannot call cudaMalloc: code running while a stream is captured
 into a CUDA graph, frameworks that own all device memory through their own
@@ -7,13 +8,16 @@ library offers one sweep-cut entry point whose scratch is a fixed array in the
 library's device memory.  These tests call it through the C ABI on device
 buffers, twice in a row (the scratch array keeps the previous call's contents),
 and compare its cut value, threshold and side with the context-based
-pirmcut_cut on the same graph and voltages, to the tolerance the other parity
-tests use (1e-9 relative on the value).  This file is collected last.
+pirmcut_cut on the same graph and voltages, and with the FP64 oracle's sweep
+cut of those voltages, to the tolerances the other parity tests use (1e-9
+relative on the value; the side identical on every vertex at least 1e-6 from
+the threshold).  This file is collected last.
 """
 import numpy as np
 import pytest
 
 import gen
+import oracle as O
 
 pytestmark = pytest.mark.gpu
 
@@ -57,6 +61,7 @@ def test_static_sweep_matches_pirmcut_cut(env, name, g, x_kind):
             x[g.s], x[g.t] = 1.0, 0.0
             s.set_x(x)
         ref_side, ref_value, ref_tau = s.cut()
+    prob = O.Problem.from_graph(g)
     rp = torch.from_numpy(g.row_ptr).to(dev)
     col = torch.from_numpy(g.col).to(dev)
     c = torch.from_numpy(g.c).to(dev)
@@ -72,6 +77,14 @@ def test_static_sweep_matches_pirmcut_cut(env, name, g, x_kind):
         assert abs(value - ref_value) <= CUT_RTOL * ref_value, (call, value, ref_value)
         assert abs(tau - ref_tau) <= 1e-15, (call, tau, ref_tau)
         assert np.array_equal(side.cpu().numpy(), ref_side), call
+        # the oracle's sweep of the same voltages (prefix sums, vertex-id ties)
+        ora = O.sweep_cut(prob, x)
+        assert abs(value - ora["value"]) <= CUT_RTOL * ora["value"], (call, value, ora["value"])
+        assert abs(tau - ora["tau"]) <= 1e-15, (call, tau, ora["tau"])
+        assert int(k) == ora["k"], (call, k, ora["k"])
+        far = np.abs(x - ora["tau"]) >= 1e-6
+        far[[g.s, g.t]] = True
+        assert np.array_equal(side.cpu().numpy().astype(bool)[far], ora["side"][far]), call
 
 
 def test_static_sweep_rejects_oversized_input(env):
