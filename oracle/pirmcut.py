@@ -235,6 +235,11 @@ def wls_step(prob: Problem, g: np.ndarray, solver: str = "direct", v0=None,
     elif solver == "pcg":
         v, it, rel = pcg_jacobi(Lt, b, v0, tol, maxit)
         info.update(pcg_iters=it, rel_residual=rel)
+    elif solver == "pcg_omp":
+        # the same recurrence written out in C, over every host core
+        from .pcg_omp import pcg_jacobi as pcg_jacobi_omp
+        v, it, rel = pcg_jacobi_omp(Lt, b, v0, tol, maxit)
+        info.update(pcg_iters=it, rel_residual=rel)
     else:
         raise ValueError(solver)
     x = prob.full_x(v)

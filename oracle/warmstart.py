@@ -16,6 +16,8 @@ writes every piece of that out plainly:
 * ``mlp_forward``     the network evaluated exactly (FP64) on BF16 weights
                       and FP32 inputs, with a rigorous bound on the error of
                       an FP32 evaluation (fused multiply-add per term);
+* ``mlp_forward_bf16`` the same exact value with a bound for the tensor-core
+                      data path (BF16 operands, FP32 accumulation);
 * ``mlp_gradient``    the exact gradient of the minibatch mean squared error;
 * ``splitmix64``      the SplitMix64 generator (Steele, Lea & Flood, 2014),
                       ``sample_nodes`` the minibatch it draws;
@@ -153,6 +155,43 @@ def mlp_forward(w, F):
     e1 = gamma(NF) * (np.abs(F) @ np.abs(W1).T + np.abs(b1))
     e2 = gamma(H) * (np.abs(b2) + (np.abs(h1) + e1) @ np.abs(W2).T) + e1 @ np.abs(W2).T
     eo = gamma(H) * (abs(b3) + (np.abs(h2) + e2) @ np.abs(w3)) + e2 @ np.abs(w3)
+    return out, eo
+
+
+def mlp_forward_bf16(w, F, u_acc: float = 2.0 ** -22):
+    """The network on feature rows F with the BF16 rounding of the weights w,
+    evaluated exactly in FP64, and a bound on |result of the tensor-core data
+    path - exact| for the evaluation that:
+
+    * enters each feature as a BF16 head plus a BF16 tail, f ~ hi + lo with
+      |f - hi - lo| <= 2^-18 |f| (each rounding to nearest BF16 is within
+      2^-9 relative);
+    * accumulates layer 1 (six features, the bias as a seventh term) and
+      layer 2 (64 terms, starting from b2) in FP32 with any order of
+      additions, each within u_acc relative (2^-22: round to nearest would
+      give 2^-24; the model also covers truncated partial sums);
+    * rounds ReLU(layer 1) to BF16 (2^-9 relative) before layer 2;
+    * evaluates layer 3 in FP32 with fused multiply-adds (2^-24).
+
+    The bound follows the forward error analysis of dot products
+    (Higham, Accuracy and Stability of Numerical Algorithms, Section 3.1:
+    gamma_n = n u / (1 - n u) times the sum of the absolute terms); ReLU is
+    1-Lipschitz; an input error reaches the output through |weights|.
+    """
+    p = bf16_round(w).astype(np.float64)
+    F = np.asarray(F, dtype=np.float32).astype(np.float64)
+    out, (F, z1, h1, z2, h2) = forward64(p, F)
+    W1, b1, W2, b2, w3, b3 = unpack(p)
+
+    def gamma(k, u):
+        return k * u / (1 - k * u)
+
+    aW1, aW2, aw3 = np.abs(W1), np.abs(W2), np.abs(w3)
+    eF = 2.0 ** -18 * np.abs(F)
+    e1 = eF @ aW1.T + gamma(NF + 1, u_acc) * ((np.abs(F) + eF) @ aW1.T + np.abs(b1))
+    eh1 = e1 + 2.0 ** -9 * (np.abs(h1) + e1)
+    e2 = eh1 @ aW2.T + gamma(H + 1, u_acc) * (np.abs(b2) + (np.abs(h1) + eh1) @ aW2.T)
+    eo = e2 @ aw3 + gamma(H + 1, 2.0 ** -24) * (abs(b3) + (np.abs(h2) + e2) @ aw3)
     return out, eo
 
 

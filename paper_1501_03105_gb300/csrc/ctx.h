@@ -85,6 +85,7 @@ struct MlpState {
   int used;              // steps that started from it
   int train_steps;       // Adam steps taken
   unsigned int counter;  // last-block counter of the residual reductions
+  unsigned int adam_ticket;  // last-block counter of the Adam step
 };
 
 struct MlpBuf {

@@ -43,10 +43,8 @@ constexpr int OFF_W3 = OFF_B2 + H;        // [H]
 constexpr int OFF_B3 = OFF_W3 + H;        // [1]
 constexpr int NPARAM = OFF_B3 + 1;
 static_assert(NPARAM == kMlpParams, "parameter layout");
-constexpr int TRAIN_THREADS = 128;
 constexpr int TRAIN_BLOCKS = 32;
 constexpr int SAMPLES_PER_BLOCK = 64;
-constexpr size_t TRAIN_SMEM = sizeof(float) * (2 * NPARAM + NF + 4 * H + 2);
 
 // SplitMix64 finaliser (Steele, Lea, Flood 2014): a counter-based generator.
 __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
@@ -113,33 +111,6 @@ __device__ __forceinline__ void edge_feature(double w, double w0, double xj, dou
   }
 }
 
-template <int K>
-__global__ void __launch_bounds__(kThreads)
-k_features_dia(DiaDesc d, const double* __restrict__ g, const double* __restrict__ gprev,
-               const double* __restrict__ cs, const double* __restrict__ ct,
-               const double* __restrict__ x, const double* __restrict__ eps_list,
-               const StepCounters* __restrict__ C, int form, float* __restrict__ f) {
-  const int64_t nt = d.nt;
-  const double eps = eps_list[C->eps_idx];
-  const double eps2 = eps * eps;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nt;
-       i += int64_t(gridDim.x) * blockDim.x) {
-    const double xi = x[i];
-    double wsum = 0.0, wx = 0.0, wxx = 0.0;
-    float lr = 0.0f;
-    int nlr = 0;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int64_t o = d.off[k];
-      if (i + o < nt) edge_feature(g[k * nt + i], gprev[k * nt + i], x[i + o], wsum, wx, wxx, lr, nlr);
-      if (i >= o) edge_feature(g[k * nt + i - o], gprev[k * nt + i - o], x[i - o], wsum, wx, wxx, lr, nlr);
-    }
-    const double gs = conductance(cs[i], 1.0 - xi, eps2, form);
-    const double gt = conductance(ct[i], xi, eps2, form);
-    finish_features(f, i, xi, wsum, wx, wxx, lr, nlr, gs, gt, eps);
-  }
-}
-
 __global__ void __launch_bounds__(kThreads)
 k_features_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                const double* __restrict__ g, const double* __restrict__ gprev,
@@ -181,49 +152,329 @@ k_features_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __rest
   }
 }
 
-// delta = MLP(f), one node per thread.  The BF16 weights are
-// widened to FP32 in shared memory with W2 transposed, so that the 64 layer-2
-// accumulators of a thread take one hidden unit k at a time from consecutive
-// (vectorisable, broadcast) shared-memory words; FP32 accumulation.
-// delta -> dir (FP64, the search direction) or out32 (FP32, inference API)
+// ---------------------------------------------------------------------------
+// Inference on the tensor cores: mma.sync.m16n8k16 with BF16 operands and
+// FP32 accumulation.  A warp evaluates 32 rows at a time as two 16-row tiles:
+//   layer 1  [16 x 16] x [16 x 64]: the 16-wide K slot holds the six
+//            features split into a BF16 head and a BF16 tail (f = hi + lo to
+//            about 2^-17 relative, so that differences such as f1 - f0 keep
+//            their digits), a constant 1 for the bias b1, and zeros;
+//   layer 2  [16 x 64] x [64 x 64]: the layer-1 accumulators, after ReLU and
+//            rounding to BF16, are already laid out as the A fragments of
+//            this product (no shared-memory round trip); the accumulators
+//            start from b2;
+//   layer 3  64 -> 1 on the CUDA cores in FP32 from the layer-2
+//            accumulators (ReLU, dot with w3, a reduction over the four
+//            threads that hold a row, + b3).
+// Each thread keeps its B fragments of W1 and W2 (BF16) in registers.
+// ---------------------------------------------------------------------------
+
+struct MlpFrags {
+  uint32_t w1[8][2];     // layer 1, per 8-unit output tile: K pairs (2t, 2t+1) and (8+2t, 9+2t)
+  uint32_t w2[8][4][2];  // layer 2, [output tile][16-wide K chunk]
+  uint32_t b2[8];        // (b2[8j+2t], b2[8j+2t+1]) as BF16 pairs
+  uint32_t w3[8];        // (w3[8j+2t], w3[8j+2t+1])
+  float b3;
+};
+
+__device__ __forceinline__ uint32_t bf16_bits(const __nv_bfloat16* p) {
+  return uint32_t(__bfloat16_as_ushort(*p));
+}
+// BF16 pair (p[0] in the low half = the lower K index, p[1] in the high half)
+__device__ __forceinline__ uint32_t bf16_pair(const __nv_bfloat16* p) {
+  return bf16_bits(p) | (bf16_bits(p + 1) << 16);
+}
+__device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
+
+// round two FP32 values to BF16 (nearest even) and pack them: lo in the low half
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+// the same after ReLU
+__device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                               uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// This thread's fragments of the BF16 weights (lane = 4 g + t).
+__device__ __forceinline__ void load_frags(const __nv_bfloat16* __restrict__ w16, MlpFrags& F) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int u = 8 * j + g;  // the output unit of this thread's B column
+    const uint32_t head = t < 3 ? bf16_pair(w16 + OFF_W1 + u * NF + 2 * t)  // (W1[u][2t], W1[u][2t+1])
+                                : bf16_bits(w16 + OFF_B1 + u);              // (b1[u], 0)
+    F.w1[j][0] = head;
+    F.w1[j][1] = t < 3 ? head : 0u;  // the tails of the features meet the same weights
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      F.w2[j][c][0] = bf16_pair(w16 + OFF_W2 + u * H + 16 * c + 2 * t);
+      F.w2[j][c][1] = bf16_pair(w16 + OFF_W2 + u * H + 16 * c + 8 + 2 * t);
+    }
+    F.b2[j] = bf16_pair(w16 + OFF_B2 + 8 * j + 2 * t);
+    F.w3[j] = bf16_pair(w16 + OFF_W3 + 8 * j + 2 * t);
+  }
+  F.b3 = bf16_lo(bf16_bits(w16 + OFF_B3));
+}
+
+constexpr int kStage = 9;  // words per row of a warp's A-fragment staging area (8 + 1 pad)
+
+// The network on 32 rows: lane L supplies the features f of row L (any
+// values when the row does not exist) and gets that row's output back.
+// stage: 32 * kStage words of shared memory owned by this warp.
+__device__ __forceinline__ float mlp_warp32(const MlpFrags& W, const float (&f)[NF],
+                                            uint32_t* stage) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  // this row's K slot: words 0-3 = (f0,f1) (f2,f3) (f4,f5) (1,0) rounded to
+  // BF16, words 4-6 = the tails f - BF16(f), word 7 = 0
+  uint32_t* my = stage + lane * kStage;
+  const uint32_t h0 = pack_bf16(f[0], f[1]), h1 = pack_bf16(f[2], f[3]), h2 = pack_bf16(f[4], f[5]);
+  my[0] = h0;
+  my[1] = h1;
+  my[2] = h2;
+  my[3] = pack_bf16(1.0f, 0.0f);
+  my[4] = pack_bf16(f[0] - bf16_lo(h0), f[1] - bf16_hi(h0));
+  my[5] = pack_bf16(f[2] - bf16_lo(h1), f[3] - bf16_hi(h1));
+  my[6] = pack_bf16(f[4] - bf16_lo(h2), f[5] - bf16_hi(h2));
+  my[7] = 0u;
+  __syncwarp();
+  float out_g[2], out_g8[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int r0 = 16 * h + g, r1 = r0 + 8;
+    uint32_t a[4];
+    a[0] = stage[r0 * kStage + t];
+    a[1] = stage[r1 * kStage + t];
+    a[2] = stage[r0 * kStage + 4 + t];
+    a[3] = stage[r1 * kStage + 4 + t];
+    // layer 1 (bias through the constant-1 column), ReLU, BF16: the A
+    // fragments of layer 2 (K chunk c = hidden units 16c .. 16c + 15)
+    uint32_t a2[4][4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+      mma_bf16_16816(d0, a, W.w1[2 * c][0], W.w1[2 * c][1]);
+      mma_bf16_16816(d1, a, W.w1[2 * c + 1][0], W.w1[2 * c + 1][1]);
+      a2[c][0] = pack_relu_bf16(d0[0], d0[1]);
+      a2[c][1] = pack_relu_bf16(d0[2], d0[3]);
+      a2[c][2] = pack_relu_bf16(d1[0], d1[1]);
+      a2[c][3] = pack_relu_bf16(d1[2], d1[3]);
+    }
+    // layer 2 from b2, then ReLU and the dot with w3 (FP32)
+    float pg = 0.f, pg8 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float bl = bf16_lo(W.b2[j]), bh = bf16_hi(W.b2[j]);
+      float d[4] = {bl, bh, bl, bh};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) mma_bf16_16816(d, a2[c], W.w2[j][c][0], W.w2[j][c][1]);
+      const float wl = bf16_lo(W.w3[j]), wh = bf16_hi(W.w3[j]);
+      pg = fmaf(fmaxf(d[0], 0.f), wl, pg);
+      pg = fmaf(fmaxf(d[1], 0.f), wh, pg);
+      pg8 = fmaf(fmaxf(d[2], 0.f), wl, pg8);
+      pg8 = fmaf(fmaxf(d[3], 0.f), wh, pg8);
+    }
+    pg += __shfl_xor_sync(0xffffffffu, pg, 1);
+    pg += __shfl_xor_sync(0xffffffffu, pg, 2);
+    pg8 += __shfl_xor_sync(0xffffffffu, pg8, 1);
+    pg8 += __shfl_xor_sync(0xffffffffu, pg8, 2);
+    out_g[h] = pg + W.b3;
+    out_g8[h] = pg8 + W.b3;
+  }
+  // back to one row per lane through the staging area
+  __syncwarp();
+  float* so = reinterpret_cast<float*>(stage);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (t == 0) so[16 * h + g] = out_g[h];
+    if (t == 1) so[16 * h + g + 8] = out_g8[h];
+  }
+  __syncwarp();
+  const float r = so[lane];
+  __syncwarp();
+  return r;
+}
+
+// FP32 value of a double by truncation of its significand, built with
+// integer instructions (GB300 runs FP64 <-> FP32 conversions on its narrow
+// FP64 pipe); relative error below 2^-23, magnitudes below the FP32 normal
+// range give a signed zero, above it an infinity.
+__device__ __forceinline__ float f32_trunc(double v) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  const unsigned hi = unsigned(b >> 32), lo = unsigned(b);
+  const int e = int((hi >> 20) & 0x7FFu) - 896;
+  const unsigned m = __funnelshift_r(lo, hi, 29) & 0x7FFFFFu;
+  const unsigned sgn = hi & 0x80000000u;
+  if (e <= 0) return __uint_as_float(sgn);
+  if (e >= 255) return __uint_as_float(sgn | 0x7f800000u);
+  return __uint_as_float(sgn | (unsigned(e) << 23) | m);
+}
+
+// Conductance in FP32 (a feature input only): the two reweighting forms.
+__device__ __forceinline__ float conductance32(float c, float d, float eps2, int form) {
+  if (form == PIRMCUT_REWEIGHT_PAPER) {
+    const float cd = c * d;
+    return c * c * rsqrtf(fmaf(cd, cd, eps2));
+  }
+  return c * rsqrtf(fmaf(d, d, eps2));
+}
+
+// The six features of DIA row i (< nt) in FP32: neighbour differences
+// x_u - x_i are formed in FP64 and then truncated, the weighted mean and
+// variance of the neighbours' voltages are taken about x_i in two passes
+// (no cancellation), logarithms in FP32.
+template <int K>
+__device__ __forceinline__ void features_dia32(const DiaDesc& d, const double* __restrict__ g,
+                                               const double* __restrict__ gprev,
+                                               const double* __restrict__ cs,
+                                               const double* __restrict__ ct,
+                                               const double* __restrict__ x, float eps2f,
+                                               float log_eps8, int form, int64_t i, float (&f)[NF]) {
+  const int64_t nt = d.nt;
+  const double xi = x[i];
+  float w[2 * K + 2], dx[2 * K + 2];
+  float lr = 0.f;
+  int nlr = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int64_t o = d.off[k];
+    w[2 * k] = 0.f;
+    dx[2 * k] = 0.f;
+    w[2 * k + 1] = 0.f;
+    dx[2 * k + 1] = 0.f;
+    if (i + o < nt) {
+      const float wu = f32_trunc(g[k * nt + i]), wp = f32_trunc(gprev[k * nt + i]);
+      w[2 * k] = wu;
+      dx[2 * k] = f32_trunc(x[i + o] - xi);
+      if (wu > 0.f && wp > 0.f) {
+        lr += __log2f(wu) - __log2f(wp);
+        ++nlr;
+      }
+    }
+    if (i >= o) {
+      const float wu = f32_trunc(g[k * nt + i - o]), wp = f32_trunc(gprev[k * nt + i - o]);
+      w[2 * k + 1] = wu;
+      dx[2 * k + 1] = f32_trunc(x[i - o] - xi);
+      if (wu > 0.f && wp > 0.f) {
+        lr += __log2f(wu) - __log2f(wp);
+        ++nlr;
+      }
+    }
+  }
+  // terminals: x_s = 1, x_t = 0, conductances of step l from x^(l-1)
+  const float ds = f32_trunc(1.0 - xi), dt = -f32_trunc(xi);
+  w[2 * K] = conductance32(f32_trunc(cs[i]), ds, eps2f, form);
+  dx[2 * K] = ds;
+  w[2 * K + 1] = conductance32(f32_trunc(ct[i]), dt, eps2f, form);
+  dx[2 * K + 1] = dt;
+  float wsum = 0.f, wd = 0.f;
+#pragma unroll
+  for (int k = 0; k < 2 * K + 2; ++k) {
+    wsum += w[k];
+    wd = fmaf(w[k], dx[k], wd);
+  }
+  const float inv = 1.0f / wsum;
+  const float m = wd * inv;
+  float var = 0.f;
+#pragma unroll
+  for (int k = 0; k < 2 * K + 2; ++k) {
+    const float e = dx[k] - m;
+    var = fmaf(w[k] * e, e, var);
+  }
+  const float x32 = f32_trunc(xi);
+  f[0] = x32;
+  f[1] = x32 + m;
+  f[2] = sqrtf(var * inv);
+  f[3] = nlr ? lr * (0.69314718f * 0.125f) / float(nlr) : 0.f;
+  f[4] = logf(wsum) * 0.125f;
+  f[5] = log_eps8;
+}
+
+// Learned direction on a DIA grid: features (kept in feat when with_feat)
+// and, with kPredict, the network's output into dir (FP64).  A warp takes 32
+// consecutive rows at a time.
+template <int K, bool kPredict>
+__global__ void __launch_bounds__(128)
+k_mlp_fused_dia(DiaDesc d, const double* __restrict__ g, const double* __restrict__ gprev,
+                const double* __restrict__ cs, const double* __restrict__ ct,
+                const double* __restrict__ x, const double* __restrict__ eps_list,
+                const StepCounters* __restrict__ C, int form,
+                const __nv_bfloat16* __restrict__ w16, float* __restrict__ feat, int with_feat,
+                double* __restrict__ dir) {
+  __shared__ uint32_t stage_all[4][32 * kStage];
+  const int64_t nt = d.nt;
+  const double eps = eps_list[C->eps_idx];
+  const float eps2f = float(eps) * float(eps);
+  const float log_eps8 = logf(float(eps)) * 0.125f;
+  MlpFrags W;
+  if (kPredict) load_frags(w16, W);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* stage = stage_all[warp];
+  const int64_t tiles = (nt + 31) / 32;
+  for (int64_t tile = int64_t(blockIdx.x) * 4 + warp; tile < tiles; tile += int64_t(gridDim.x) * 4) {
+    const int64_t i = tile * 32 + lane;
+    float f[NF] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (i < nt) {
+      features_dia32<K>(d, g, gprev, cs, ct, x, eps2f, log_eps8, form, i, f);
+      if (with_feat) {
+#pragma unroll
+        for (int k = 0; k < NF; ++k) feat[i * NF + k] = f[k];
+      }
+    }
+    if (kPredict) {
+      const float out = mlp_warp32(W, f, stage);
+      if (i < nt) dir[i] = double(out);
+    }
+  }
+}
+
+// The network on stored feature rows (CSR problems, and the inference entry
+// point): delta -> dir (FP64) or out32 (FP32).
 template <bool kF32>
-__global__ void __launch_bounds__(kThreads)
-k_mlp_predict(int64_t nt, const float* __restrict__ f, const __nv_bfloat16* __restrict__ w16,
-              double* __restrict__ dir, float* __restrict__ out32) {
-  extern __shared__ __align__(16) float sw[];
-  for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) {
-    int dst = i;
-    if (i >= OFF_W2 && i < OFF_B2) {
-      const int j = (i - OFF_W2) / H, k = (i - OFF_W2) % H;
-      dst = OFF_W2 + k * H + j;
+__global__ void __launch_bounds__(128)
+k_mlp_predict_tc(int64_t nt, const float* __restrict__ f, const __nv_bfloat16* __restrict__ w16,
+                 double* __restrict__ dir, float* __restrict__ out32) {
+  __shared__ uint32_t stage_all[4][32 * kStage];
+  MlpFrags W;
+  load_frags(w16, W);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* stage = stage_all[warp];
+  const int64_t tiles = (nt + 31) / 32;
+  for (int64_t tile = int64_t(blockIdx.x) * 4 + warp; tile < tiles; tile += int64_t(gridDim.x) * 4) {
+    const int64_t i = tile * 32 + lane;
+    float in[NF] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (i < nt) {
+#pragma unroll
+      for (int k = 0; k < NF; ++k) in[k] = f[i * NF + k];
     }
-    sw[dst] = __bfloat162float(w16[i]);
-  }
-  __syncthreads();
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nt;
-       i += int64_t(gridDim.x) * blockDim.x) {
-    float in[NF];
-#pragma unroll
-    for (int k = 0; k < NF; ++k) in[k] = f[i * NF + k];
-    float z[H];
-#pragma unroll
-    for (int j = 0; j < H; ++j) z[j] = sw[OFF_B2 + j];
-#pragma unroll 1
-    for (int k = 0; k < H; ++k) {
-      float h = sw[OFF_B1 + k];
-#pragma unroll
-      for (int m = 0; m < NF; ++m) h = fmaf(sw[OFF_W1 + k * NF + m], in[m], h);
-      h = fmaxf(h, 0.0f);
-      const float* w2t = sw + OFF_W2 + k * H;
-#pragma unroll
-      for (int j = 0; j < H; ++j) z[j] = fmaf(w2t[j], h, z[j]);
+    const float out = mlp_warp32(W, in, stage);
+    if (i < nt) {
+      if (kF32) out32[i] = out;
+      else dir[i] = double(out);
     }
-    float out = sw[OFF_B3];
-#pragma unroll
-    for (int j = 0; j < H; ++j) out = fmaf(sw[OFF_W3 + j], fmaxf(z[j], 0.0f), out);
-    if (kF32) out32[i] = out;
-    else dir[i] = double(out);
   }
+}
+
+// Grid of the warp-tile kernels: 4 warps of 32 rows per block, at most three
+// blocks per SM (about 160 registers a thread).
+inline int mlp_tile_grid(int64_t rows) {
+  const int64_t tiles = (rows + 31) / 32;
+  int64_t b = (tiles + 3) / 4;
+  if (b > 152 * 3) b = 152 * 3;
+  return int(b < 1 ? 1 : b);
 }
 
 // Line search along the learned direction d from x = x^(l-1): with
@@ -352,93 +603,228 @@ k_mlp_commit(int64_t nt, MlpState* M, const double* __restrict__ dir, double* __
   }
 }
 
-// One minibatch: each block takes SAMPLES_PER_BLOCK sampled nodes in turn
-// and accumulates their gradients in shared memory (every parameter has one
-// owning thread); the block's sums go to grad_part[block].
-__global__ void __launch_bounds__(TRAIN_THREADS)
+// One minibatch as block-level GEMMs.  Block b takes the SAMPLES_PER_BLOCK
+// (64) nodes drawn for it and runs the forward and backward pass of its
+// samples together, FP32 arithmetic on the BF16 weights:
+//   Z1 = F W1^T + b1,  H1 = relu(Z1)                      [64 x 64]
+//   Z2 = H1 W2^T + b2, out = relu(Z2) w3 + b3             [64 x 64], [64]
+//   dZ2 = (2 (out - target) / batch) w3^T . [Z2 > 0]
+//   dW2 = dZ2^T H1,  dH1 = dZ2 W2,  dZ1 = dH1 . [Z1 > 0],  dW1 = dZ1^T F
+// Each of the 256 threads owns a 4 x 4 tile of every 64 x 64 product; the
+// sums over the samples of a block run in a fixed order, and grad_part[b]
+// receives the block's gradient (summed over blocks in block order by the
+// Adam step), so that training is reproducible.
+constexpr int GB_THREADS = 256;
+constexpr int LD = H + 1;  // padded row stride of the 64 x 64 tiles in shared memory
+constexpr size_t GRAD_SMEM =
+    sizeof(float) * (size_t(H) * LD * 3 + H * NF + 3 * H + 1 + SAMPLES_PER_BLOCK * (NF + 2) +
+                     GB_THREADS);
+
+__global__ void __launch_bounds__(GB_THREADS)
 k_mlp_grad(int64_t nt, const float* __restrict__ f, const double* __restrict__ x,
            const double* __restrict__ xprev, const __nv_bfloat16* __restrict__ w16,
            const MlpState* __restrict__ M, uint64_t seed, float* __restrict__ grad_part,
            float* __restrict__ loss_part) {
   extern __shared__ float sm[];
-  float* sw = sm;             // NPARAM weights
-  float* sg = sw + NPARAM;    // NPARAM gradient sums
-  float* in = sg + NPARAM;    // NF
-  float* z1 = in + NF;        // H pre-activations, layer 1
-  float* z2 = z1 + H;         // H pre-activations, layer 2
-  float* dz2 = z2 + H;        // H
-  float* dz1 = dz2 + H;       // H
-  float* red = dz1 + H;       // [output error]
+  float* W2s = sm;                          // [j][k], stride LD
+  float* Z1 = W2s + H * LD;                 // [s][k]: Z1, later dZ1
+  float* D2 = Z1 + H * LD;                  // [s][j]: dZ2
+  float* W1s = D2 + H * LD;                 // [k][m]
+  float* b1s = W1s + H * NF;
+  float* b2s = b1s + H;
+  float* w3s = b2s + H;
+  float* b3s = w3s + H;                     // [1]
+  float* Fs = b3s + 1;                      // [s][m]
+  float* tgt = Fs + SAMPLES_PER_BLOCK * NF; // [s]
+  float* dout = tgt + SAMPLES_PER_BLOCK;    // [s]
+  float* red = dout + SAMPLES_PER_BLOCK;    // [GB_THREADS] per-thread partials
   const int t = threadIdx.x;
-  for (int i = t; i < NPARAM; i += blockDim.x) {
-    sw[i] = __bfloat162float(w16[i]);
-    sg[i] = 0.0f;
+  for (int i = t; i < H * H; i += GB_THREADS) W2s[(i / H) * LD + i % H] = __bfloat162float(w16[OFF_W2 + i]);
+  for (int i = t; i < H * NF; i += GB_THREADS) W1s[i] = __bfloat162float(w16[OFF_W1 + i]);
+  if (t < H) {
+    b1s[t] = __bfloat162float(w16[OFF_B1 + t]);
+    b2s[t] = __bfloat162float(w16[OFF_B2 + t]);
+    w3s[t] = __bfloat162float(w16[OFF_W3 + t]);
   }
+  if (t == 0) b3s[0] = __bfloat162float(w16[OFF_B3]);
   const uint64_t stream = splitmix64(seed ^ (uint64_t(M->train_steps) << 20));
-  const float inv_batch = 1.0f / float(TRAIN_BLOCKS * SAMPLES_PER_BLOCK);
-  float sse = 0.0f;
-  __syncthreads();
-  for (int smp = 0; smp < SAMPLES_PER_BLOCK; ++smp) {
-    const uint64_t h = splitmix64(stream + uint64_t(blockIdx.x) * SAMPLES_PER_BLOCK + uint64_t(smp));
-    const int64_t node = int64_t(h % uint64_t(nt));
-    if (t < NF) in[t] = f[node * NF + t];
-    __syncthreads();
-    if (t < H) {
-      float z = sw[OFF_B1 + t];
+  if (t < SAMPLES_PER_BLOCK) {
+    const uint64_t hsh = splitmix64(stream + uint64_t(blockIdx.x) * SAMPLES_PER_BLOCK + uint64_t(t));
+    const int64_t node = int64_t(hsh % uint64_t(nt));
 #pragma unroll
-      for (int k = 0; k < NF; ++k) z = fmaf(sw[OFF_W1 + t * NF + k], in[k], z);
-      z1[t] = z;
-    }
-    __syncthreads();
-    if (t < H) {
-      float z = sw[OFF_B2 + t];
-      for (int k = 0; k < H; ++k) z = fmaf(sw[OFF_W2 + t * H + k], fmaxf(z1[k], 0.0f), z);
-      z2[t] = z;
-    }
-    __syncthreads();
-    if (t == 0) {
-      float out = sw[OFF_B3];
-      for (int j = 0; j < H; ++j) out = fmaf(sw[OFF_W3 + j], fmaxf(z2[j], 0.0f), out);
-      const float err = out - float(x[node] - xprev[node]);
-      red[0] = err;
+    for (int m = 0; m < NF; ++m) Fs[t * NF + m] = f[node * NF + m];
+    tgt[t] = float(x[node] - xprev[node]);
+  }
+  __syncthreads();
+  // Z1 (16 entries per thread)
+  for (int i = t; i < SAMPLES_PER_BLOCK * H; i += GB_THREADS) {
+    const int s = i / H, k = i % H;
+    float z = b1s[k];
+#pragma unroll
+    for (int m = 0; m < NF; ++m) z = fmaf(W1s[k * NF + m], Fs[s * NF + m], z);
+    Z1[s * LD + k] = z;
+  }
+  __syncthreads();
+  // Z2 tile (samples 4 ts .. 4 ts + 3, units 4 tj .. 4 tj + 3); a half-warp
+  // shares ts, so the output's reduction over j stays inside it
+  const int ts = t >> 4, tj = t & 15;
+  float z2[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b2 = 0; b2 < 4; ++b2) z2[a][b2] = b2s[4 * tj + b2];
+  for (int k = 0; k < H; ++k) {
+    float hv[4], wv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) hv[a] = fmaxf(Z1[(4 * ts + a) * LD + k], 0.f);
+#pragma unroll
+    for (int b2 = 0; b2 < 4; ++b2) wv[b2] = W2s[(4 * tj + b2) * LD + k];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) z2[a][b2] = fmaf(hv[a], wv[b2], z2[a][b2]);
+  }
+  float po[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    po[a] = 0.f;
+#pragma unroll
+    for (int b2 = 0; b2 < 4; ++b2) po[a] = fmaf(fmaxf(z2[a][b2], 0.f), w3s[4 * tj + b2], po[a]);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) po[a] += __shfl_xor_sync(0xffffffffu, po[a], o, 16);
+  }
+  const float inv_batch = 1.0f / float(TRAIN_BLOCKS * SAMPLES_PER_BLOCK);
+  float sse = 0.f;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int s = 4 * ts + a;
+    const float err = po[a] + b3s[0] - tgt[s];
+    const float dz = 2.0f * err * inv_batch;
+    if (tj == 0) {
+      dout[s] = dz;
       sse = fmaf(err, err, sse);
     }
-    __syncthreads();
-    const float dout = 2.0f * red[0] * inv_batch;  // d(mean squared error)/d(out)
-    if (t < H) {
-      sg[OFF_W3 + t] += dout * fmaxf(z2[t], 0.0f);
-      dz2[t] = z2[t] > 0.0f ? dout * sw[OFF_W3 + t] : 0.0f;
+#pragma unroll
+    for (int b2 = 0; b2 < 4; ++b2)
+      D2[s * LD + 4 * tj + b2] = z2[a][b2] > 0.f ? dz * w3s[4 * tj + b2] : 0.f;
+  }
+  // g(w3) partials: sum over this thread's samples
+  float gw3[4];
+#pragma unroll
+  for (int b2 = 0; b2 < 4; ++b2) {
+    gw3[b2] = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const float dzs = 2.0f * (po[a] + b3s[0] - tgt[4 * ts + a]) * inv_batch;
+      gw3[b2] = fmaf(dzs, fmaxf(z2[a][b2], 0.f), gw3[b2]);
     }
-    if (t == 0) sg[OFF_B3] += dout;
+  }
+  __syncthreads();
+  float* gout = grad_part + size_t(blockIdx.x) * NPARAM;
+  // g(w3)[j] = sum over ts of the partials (fixed order through shared memory)
+#pragma unroll
+  for (int b2 = 0; b2 < 4; ++b2) {
+    red[t] = gw3[b2];
     __syncthreads();
-    if (t < H) {
-      float a = 0.0f;
-      for (int k = 0; k < H; ++k) a = fmaf(sw[OFF_W2 + k * H + t], dz2[k], a);
-      dz1[t] = z1[t] > 0.0f ? a : 0.0f;
-      sg[OFF_B2 + t] += dz2[t];
+    if (t < 16) {
+      float acc = 0.f;
+      for (int q = 0; q < 16; ++q) acc += red[q * 16 + t];
+      gout[OFF_W3 + 4 * t + b2] = acc;
     }
-    __syncthreads();
-    for (int idx = t; idx < H * H; idx += TRAIN_THREADS)
-      sg[OFF_W2 + idx] += dz2[idx / H] * fmaxf(z1[idx % H], 0.0f);
-    for (int idx = t; idx < H * NF; idx += TRAIN_THREADS)
-      sg[OFF_W1 + idx] += dz1[idx / NF] * in[idx % NF];
-    if (t < H) sg[OFF_B1 + t] += dz1[t];
     __syncthreads();
   }
-  for (int i = t; i < NPARAM; i += blockDim.x) grad_part[size_t(blockIdx.x) * NPARAM + i] = sg[i];
-  if (t == 0) loss_part[blockIdx.x] = sse;
+  // dW2 = dZ2^T H1: tile (units 4 tj, inputs 4 ts); g(b2); g(b3)
+  {
+    const int tk = ts;
+    float acc[4][4] = {};
+    for (int s = 0; s < SAMPLES_PER_BLOCK; ++s) {
+      float dv[4], hv[4];
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) dv[b2] = D2[s * LD + 4 * tj + b2];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) hv[c] = fmaxf(Z1[s * LD + 4 * tk + c], 0.f);
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[b2][c] = fmaf(dv[b2], hv[c], acc[b2][c]);
+    }
+#pragma unroll
+    for (int b2 = 0; b2 < 4; ++b2)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) gout[OFF_W2 + (4 * tj + b2) * H + 4 * tk + c] = acc[b2][c];
+    if (t < H) {
+      float gb = 0.f;
+      for (int s = 0; s < SAMPLES_PER_BLOCK; ++s) gb += D2[s * LD + t];
+      gout[OFF_B2 + t] = gb;
+    }
+    if (t == 0) {
+      float gb = 0.f;
+      for (int s = 0; s < SAMPLES_PER_BLOCK; ++s) gb += dout[s];
+      gout[OFF_B3] = gb;
+    }
+  }
+  // dH1 = dZ2 W2: tile (samples 4 ts, inputs 4 tj); dZ1 = dH1 . [Z1 > 0] in place
+  {
+    float acc[4][4] = {};
+    for (int j = 0; j < H; ++j) {
+      float dv[4], wv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) dv[a] = D2[(4 * ts + a) * LD + j];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) wv[c] = W2s[j * LD + 4 * tj + c];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(dv[a], wv[c], acc[a][c]);
+    }
+    __syncthreads();  // every thread is done reading Z1 as H1
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float* zp = Z1 + (4 * ts + a) * LD + 4 * tj + c;
+        *zp = *zp > 0.f ? acc[a][c] : 0.f;
+      }
+  }
+  __syncthreads();
+  // dW1 = dZ1^T F, g(b1)
+  for (int i = t; i < H * NF; i += GB_THREADS) {
+    const int k = i / NF, m = i % NF;
+    float acc = 0.f;
+    for (int s = 0; s < SAMPLES_PER_BLOCK; ++s) acc = fmaf(Z1[s * LD + k], Fs[s * NF + m], acc);
+    gout[OFF_W1 + i] = acc;
+  }
+  if (t < H) {
+    float gb = 0.f;
+    for (int s = 0; s < SAMPLES_PER_BLOCK; ++s) gb += Z1[s * LD + t];
+    gout[OFF_B1 + t] = gb;
+  }
+  // the block's squared error (threads tj == 0 hold four samples each)
+  red[t] = sse;
+  __syncthreads();
+  if (t == 0) {
+    float acc = 0.f;
+    for (int q = 0; q < GB_THREADS; q += 16) acc += red[q];
+    loss_part[blockIdx.x] = acc;
+  }
 }
 
 // Block gradients summed in block order; one Adam step (Kingma & Ba) on the
-// FP32 master weights, BF16 copy refreshed.  One block, so the step counter
-// is read before and written after every update.
-__global__ void __launch_bounds__(1024)
+// FP32 master weights, BF16 copy refreshed.  Every block reads the step
+// count; the last block to finish (a ticket, no waiting) records the loss
+// and advances the count.
+constexpr int ADAM_THREADS = 256;
+constexpr int ADAM_BLOCKS = (NPARAM + ADAM_THREADS - 1) / ADAM_THREADS;
+
+__global__ void __launch_bounds__(ADAM_THREADS)
 k_mlp_adam(const float* __restrict__ grad_part, const float* __restrict__ loss_part,
            float* master, __nv_bfloat16* w16, float* m, float* v, MlpState* M, float lr) {
+  __shared__ unsigned int s_last;
   const int step = M->train_steps + 1;
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.0f - powf(b1, float(step)), c2 = 1.0f - powf(b2, float(step));
-  for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) {
+  const int i = blockIdx.x * ADAM_THREADS + threadIdx.x;
+  if (i < NPARAM) {
     float gsum = 0.0f;
     for (int b = 0; b < TRAIN_BLOCKS; ++b) gsum += grad_part[size_t(b) * NPARAM + i];
     const float mi = b1 * m[i] + (1.0f - b1) * gsum;
@@ -451,10 +837,16 @@ k_mlp_adam(const float* __restrict__ grad_part, const float* __restrict__ loss_p
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(&M->adam_ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
     float s = 0.0f;
     for (int b = 0; b < TRAIN_BLOCKS; ++b) s += loss_part[b];
     M->loss = s * (1.0f / float(TRAIN_BLOCKS * SAMPLES_PER_BLOCK));
     M->train_steps = step;
+    M->adam_ticket = 0u;
   }
 }
 
@@ -489,6 +881,9 @@ cudaError_t mlp_alloc(Ctx& c) {
   A((void**)&b.state, sizeof(MlpState));
   if (e == cudaSuccess) e = cudaMemsetAsync(b.state, 0, sizeof(MlpState), c.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b.feat, 0, sizeof(float) * NF * size_t(c.nt), c.stream);
+  // the gradient kernel's tiles take more than the default 48 KB of shared memory
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, int(GRAD_SMEM));
   if (e != cudaSuccess) mlp_free(c);
   return e;
 }
@@ -563,17 +958,27 @@ int enqueue_mlp_post(Ctx& c, cudaStream_t st) {
   MlpBuf& b = c.mlp;
   const int grid = grid_for(c.nt);
   const int form = c.opt.reweight_form;
+  const bool predict = (c.mlp_mode & PIRMCUT_MLP_PREDICT) != 0;
+  const int keep_feat = (c.mlp_mode & PIRMCUT_MLP_TRAIN) ? 1 : 0;
   if (c.format == PIRMCUT_FORMAT_DIA) {
-    PIRMCUT_DISPATCH_K(c.K, (k_features_dia<KK><<<grid, kThreads, 0, st>>>(
-                                c.dd, c.gdia, b.gprev, c.cs, c.ct, c.x, c.eps_list, c.C, form, b.feat)));
+    const int tg = mlp_tile_grid(c.nt);
+    if (predict) {
+      PIRMCUT_DISPATCH_K(c.K, (k_mlp_fused_dia<KK, true><<<tg, 128, 0, st>>>(
+                                  c.dd, c.gdia, b.gprev, c.cs, c.ct, c.x, c.eps_list, c.C, form,
+                                  b.w16, b.feat, keep_feat, b.dir)));
+    } else {
+      PIRMCUT_DISPATCH_K(c.K, (k_mlp_fused_dia<KK, false><<<tg, 128, 0, st>>>(
+                                  c.dd, c.gdia, b.gprev, c.cs, c.ct, c.x, c.eps_list, c.C, form,
+                                  b.w16, b.feat, 1, b.dir)));
+      return 1;
+    }
   } else {
     k_features_csr<<<grid + c.n_heavy, kThreads, 0, st>>>(c.nt, c.rp, c.col, c.gval, b.gprev, c.cs,
                                                           c.ct, c.x, c.eps_list, c.C, form, b.feat,
                                                           c.heavy_deg, c.heavy, grid);
+    if (!predict) return 1;
+    k_mlp_predict_tc<false><<<mlp_tile_grid(c.nt), 128, 0, st>>>(c.nt, b.feat, b.w16, b.dir, nullptr);
   }
-  if (!(c.mlp_mode & PIRMCUT_MLP_PREDICT)) return 1;
-  k_mlp_predict<false><<<grid, kThreads, sizeof(float) * NPARAM, st>>>(c.nt, b.feat, b.w16, b.dir,
-                                                                       nullptr);
   if (c.format == PIRMCUT_FORMAT_DIA) {
     PIRMCUT_DISPATCH_K(c.K, (k_linesearch_dia<KK><<<grid, kThreads, 0, st>>>(
                                 c.dd, c.gdia, c.cs, c.ct, c.x, b.dir, c.eps_list, c.C, form,
@@ -585,7 +990,7 @@ int enqueue_mlp_post(Ctx& c, cudaStream_t st) {
                                                             c.heavy, grid);
   }
   k_mlp_commit<<<grid, kThreads, 0, st>>>(c.nt, b.state, b.dir, c.x);
-  return 4;
+  return c.format == PIRMCUT_FORMAT_DIA ? 3 : 4;
 }
 
 // After the solve of a step, with training on: iters_per_step Adam steps on
@@ -594,18 +999,18 @@ int enqueue_mlp_train(Ctx& c, cudaStream_t st) {
   if (!(c.mlp_mode & PIRMCUT_MLP_TRAIN)) return 0;
   MlpBuf& b = c.mlp;
   for (int it = 0; it < b.iters_per_step; ++it) {
-    k_mlp_grad<<<TRAIN_BLOCKS, TRAIN_THREADS, TRAIN_SMEM, st>>>(
+    k_mlp_grad<<<TRAIN_BLOCKS, GB_THREADS, GRAD_SMEM, st>>>(
         c.nt, b.feat, c.x, b.xprev, b.w16, b.state, b.seed, b.grad_part, b.loss_part);
-    k_mlp_adam<<<1, 1024, 0, st>>>(b.grad_part, b.loss_part, b.master, b.w16, b.m, b.v, b.state,
-                                    b.lr);
+    k_mlp_adam<<<ADAM_BLOCKS, ADAM_THREADS, 0, st>>>(b.grad_part, b.loss_part, b.master, b.w16,
+                                                     b.m, b.v, b.state, b.lr);
   }
   return 2 * b.iters_per_step;
 }
 
 // Inference on caller-supplied features (count x kMlpFeatures, device) -> delta (device).
 cudaError_t mlp_predict_delta(Ctx& c, const float* feat, int64_t count, float* delta) {
-  k_mlp_predict<true><<<grid_for(count), kThreads, sizeof(float) * NPARAM, c.stream>>>(
-      count, feat, c.mlp.w16, nullptr, delta);
+  k_mlp_predict_tc<true><<<mlp_tile_grid(count), 128, 0, c.stream>>>(count, feat, c.mlp.w16, nullptr,
+                                                                     delta);
   c.launches += 1;
   return cudaGetLastError();
 }

@@ -1,0 +1,92 @@
+"""Write the oracle's reference cut values mu_ref of the benchmark workloads
+into tests/golden/mu_ref.json.
+
+Time-to-cut (the benchmark's second metric) is the time until the sweep cut
+after an IRLS step comes within 1e-6 relative of mu_ref, the value of the
+sweep cut (Section 3.3) of the FP64 oracle's last iterate of the same
+workload: x^(0) (W^(0) = C) and T IRLS steps (Section 2.1), eps_l =
+max(0.1 * 2^-(l-1), 1e-6), each reduced system (Eq. reduced-laplacian-system)
+solved by the oracle's Jacobi-PCG to ||r|| <= 1e-12 ||b||, warm-started from
+the previous iterate.  This script calls only the oracle and the seeded input
+generators; the PCG runs in the oracle's C restatement over every host core.
+
+    python tests/golden/make_mu_ref.py [grid2048] [vol256]
+"""
+from __future__ import annotations
+
+import datetime
+import json
+import os
+import platform
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+import oracle as O  # noqa: E402
+from oracle import pcg_omp  # noqa: E402
+
+OUT = os.path.join(HERE, "mu_ref.json")
+# workload -> (generator number, IRLS steps T)
+WORKLOADS = {"grid2048": (2, 50), "vol256": (3, 30)}
+TOL = 1e-12
+
+
+def run(name):
+    k, T = WORKLOADS[name]
+    t0 = time.time()
+    g = gen.config_graph(k)
+    prob = O.Problem.from_graph(g)
+    eps = O.eps_schedule(T)
+    nt = prob.nonterminals
+    steps = []
+    x = None
+    for l in range(T + 1):
+        gl = O.initial_conductance(prob) if l == 0 else O.reweight(prob, x, eps[l - 1])
+        Lt, b = O.reduced_system(prob, O.laplacian(prob, gl))
+        v, it, rel = pcg_omp.pcg_jacobi(Lt, b, None if x is None else x[nt], tol=TOL, maxit=10 ** 7)
+        if rel > TOL:
+            raise RuntimeError(f"{name} step {l}: PCG stopped at {rel:.3e}")
+        x = prob.full_x(v)
+        mu = O.sweep_cut(prob, x)["value"]
+        steps.append({"step": l, "eps": eps[l - 1] if l else 0.0, "pcg_iters": it,
+                      "rel_residual": rel, "sweep_value": mu})
+        print(f"{name} step {l}: {it} PCG iterations, sweep {mu:.12g} ({time.time() - t0:.0f} s)",
+              flush=True)
+    mu_ref = steps[-1]["sweep_value"]
+    first = next(s["step"] for s in steps
+                 if all(abs(t["sweep_value"] - mu_ref) <= 1e-6 * mu_ref for t in steps[s["step"]:]))
+    return {
+        "workload": g.name, "generator": f"gen.config_graph({k})", "T": T,
+        "eps": "max(0.1 * 2^-(l-1), 1e-6)", "pcg": f"oracle Jacobi-PCG, tol {TOL}, warm start",
+        "mu_ref": mu_ref,
+        "first_step_within_1e-6_for_good": first,
+        "steps": steps,
+        "seconds": time.time() - t0,
+        "host": f"{platform.machine()}, {pcg_omp.max_threads()} OpenMP threads",
+        "date": datetime.date.today().isoformat(),
+        "command": "python tests/golden/make_mu_ref.py " + name,
+    }
+
+
+def main(argv):
+    names = argv or list(WORKLOADS)
+    data = {}
+    if os.path.exists(OUT):
+        with open(OUT) as f:
+            data = json.load(f)
+    for name in names:
+        data[name] = run(name)
+        with open(OUT, "w") as f:
+            json.dump(data, f, indent=1)
+            f.write("\n")
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main(sys.argv[1:]))

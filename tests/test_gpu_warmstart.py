@@ -1,10 +1,13 @@
 """GPU parity of the learned warm start against ``oracle/warmstart.py``.
 
 Bars:
-* features: FP32 values computed in FP64 and rounded once (f0-f2, f4, f5:
-  within 2e-6 absolute), f3 from FP32 logarithms (within 1e-5 absolute);
-* inference: within the oracle's rigorous bound on an FP32 fused
-  multiply-add evaluation of the network;
+* features: f0-f2, f4, f5 within 2e-6 absolute of the oracle's FP64 values
+  (CSR: computed in FP64 and rounded once; DIA: computed in FP32 from
+  truncated FP64 inputs, differences formed in FP64, the variance in two
+  passes -- a few units of 2^-23 on values of size <= 1 and on logarithms
+  / 8), f3 from FP32 logarithms (within 1e-5 absolute);
+* inference (tensor cores, BF16 operands, FP32 accumulation): within the
+  oracle's bound for that data path (split-BF16 features, BF16 hidden layer);
 * line search: alpha and the energy change to relative 1e-9 (1e-7 for the
   change, a quotient of FP64 sums) where the direction is exact on both sides
   (a constant), to relative 1e-5 where it comes from the FP32 network;
@@ -78,23 +81,22 @@ def line_search_tolerance(prob, g, v0, d, e):
     return ta, tE
 
 
-def feature_ulps(F):
-    """One unit in the last place of each FP32 feature (both sides round
-    their FP64 values once, so they may differ by that much)."""
-    F = np.asarray(F, dtype=np.float32)
-    return np.abs(np.spacing(F)).astype(np.float64)
+FEATURE_ATOL = 2e-6
 
 
 def jacobi_weights(alpha):
     """Weights whose output is alpha * (f1 - f0): one damped Jacobi step,
-    since f1 - f0 = (sum_u g x_u) / d_v - x_v = r_v / d_v."""
+    since f1 - f0 = (sum_u g x_u) / d_v - x_v = r_v / d_v.  Two hidden units
+    carry the positive and the negative part (relu(f1 - f0), relu(f0 - f1)),
+    so that the BF16 hidden layer rounds the difference itself, relatively."""
     w = np.zeros(W.NPARAM, dtype=np.float32)
     W1 = w[W.OFF_W1:W.OFF_B1].reshape(64, 6)
     W1[0, 0], W1[0, 1] = -1.0, 1.0
-    w[W.OFF_B1] = 1.0                       # f1 - f0 + 1 >= 0: the ReLU passes it
-    w[W.OFF_W2] = 1.0                       # W2[0][0]
+    W1[1, 0], W1[1, 1] = 1.0, -1.0
+    W2 = w[W.OFF_W2:W.OFF_B2].reshape(64, 64)
+    W2[0, 0], W2[1, 1] = 1.0, 1.0
     w[W.OFF_W3] = alpha
-    w[W.OFF_B3] = -alpha
+    w[W.OFF_W3 + 1] = -alpha
     return w
 
 
@@ -118,14 +120,15 @@ def test_features_match_oracle(P, name, make, fmt):
             ref = W.features(prob, xs[l - 1], gl, gprev, eps[l - 1])
             got = s.mlp_features()
             cols = [0, 1, 2, 4, 5]
-            np.testing.assert_allclose(got[:, cols], ref[:, cols], rtol=0, atol=2e-6, err_msg=f"step {l}")
+            np.testing.assert_allclose(got[:, cols], ref[:, cols], rtol=0, atol=FEATURE_ATOL,
+                                       err_msg=f"step {l}")
             np.testing.assert_allclose(got[:, 3], ref[:, 3], rtol=0, atol=1e-5, err_msg=f"step {l}")
             assert np.max(np.abs(s.get_x() - xs[l])) <= XTOL
             gprev = gl
 
 
 @pytest.mark.parametrize("count", [1, 257, 5000])
-def test_inference_within_the_fp32_bound(P, count):
+def test_inference_within_the_bf16_bound(P, count):
     g = gen.config_graph(1, scale=8)
     rng = np.random.default_rng(count)
     w = rng.normal(0, 0.2, W.NPARAM).astype(np.float32)
@@ -136,7 +139,7 @@ def test_inference_within_the_fp32_bound(P, count):
         got = s.mlp_predict(F)
         back = s.mlp_weights()
     assert np.array_equal(back, w)
-    out, bound = W.mlp_forward(w, F)
+    out, bound = W.mlp_forward_bf16(w, F)
     assert np.all(np.abs(got.astype(np.float64) - out) <= bound)
 
 
@@ -153,7 +156,7 @@ def test_inference_device_buffers(P):
         dd = torch.empty(300, dtype=torch.float32, device="cuda")
         s.mlp_predict(dF, dd)
         got = dd.cpu().numpy()
-    out, bound = W.mlp_forward(w, F)
+    out, bound = W.mlp_forward_bf16(w, F)
     assert np.all(np.abs(got.astype(np.float64) - out) <= bound)
 
 
@@ -229,18 +232,17 @@ def test_jacobi_direction_and_the_solve_stays_exact(P, fmt, precision):
             assert info.status == 0
             gl = O.reweight(prob, xs[l - 1], eps[l - 1])
             F = W.features(prob, xs[l - 1], gl, gprev, eps[l - 1])
-            out, bound = W.mlp_forward(w, F)
+            out, bound = W.mlp_forward_bf16(w, F)
             v0 = reduced(prob, xs[l - 1])
             alpha, dE = W.line_search(prob, gl, v0, out)
-            # d = 0.5 (f1 - f0): the network's own bound plus one ulp of each
-            # input feature on either side
-            ul = feature_ulps(F)
-            e = bound + 0.5 * 2 * (ul[:, 0] + ul[:, 1])
+            # d = 0.5 (f1 - f0): the data path's bound plus the feature
+            # tolerance of f0 and f1 on the GPU's side
+            e = bound + 0.5 * 2 * FEATURE_ATOL
             ta, tE = line_search_tolerance(prob, gl, v0, out, e)
             st = s.mlp_stats()
             assert abs(st.alpha - alpha) <= 2 * ta + 1e-12 * abs(alpha), (st.alpha, alpha, ta)
             assert abs(st.energy_change - dE) <= 2 * tE + 1e-9 * abs(dE), (st.energy_change, dE, tE)
-            assert abs(st.alpha - alpha) <= 1e-3 * abs(alpha)
+            assert abs(st.alpha - alpha) <= 1e-2 * abs(alpha)
             assert st.energy_change < 0.0
             assert np.max(np.abs(s.get_x() - xs[l])) <= XTOL, l
             gprev = gl

@@ -185,6 +185,54 @@ def test_forward_error_bound_covers_float32_fma_evaluation():
         assert bound[r] < 2e-3 * (1 + abs(out[r]))  # not vacuous
 
 
+def _bf16(a):
+    return W.bf16_round(np.float32(a)).astype(np.float64)
+
+
+def _trunc32(v):
+    """Round toward zero to float32: a worse accumulator than round to nearest."""
+    f = np.float32(v)
+    if abs(float(f)) > abs(v):
+        f = np.nextafter(f, np.float32(0))
+    return f
+
+
+def test_forward_bf16_bound_covers_the_tensor_core_data_path():
+    """The tensor-core evaluation emulated step by step: split-BF16 features,
+    exact BF16 products, FP32 partial sums (rounded to nearest, or truncated)
+    in a shuffled order, ReLU rounded to BF16, an FP32 output layer.  Every
+    emulation lies within the bound, which is not vacuous."""
+    rng = np.random.default_rng(14)
+    w = _rand_params(15)
+    F = rng.normal(0, 1, (6, 6)).astype(np.float32)
+    F[:, 1] = F[:, 0] + np.float32(1e-3)          # a near-cancelling pair (f1 - f0)
+    out, bound = W.mlp_forward_bf16(w, F)
+    W1, b1, W2, b2, w3, b3 = (a.astype(np.float64) for a in W.unpack(W.bf16_round(w)))
+    for trunc in (False, True):
+        acc = _trunc32 if trunc else np.float32
+        for r in range(F.shape[0]):
+            hi = np.array([_bf16(v) for v in F[r]])
+            lo = np.array([_bf16(np.float64(F[r, m]) - hi[m]) for m in range(6)])
+            h1 = np.zeros(64)
+            for k in range(64):
+                terms = [W1[k, m] * hi[m] for m in range(6)] + [W1[k, m] * lo[m] for m in range(6)]
+                terms.append(b1[k])
+                z = np.float32(0)
+                for j in rng.permutation(len(terms)):
+                    z = acc(np.float64(z) + terms[j])
+                h1[k] = _bf16(max(float(z), 0.0))
+            o = np.float32(b3)
+            for j in range(64):
+                z = np.float32(b2[j])
+                for k in rng.permutation(64):
+                    z = acc(np.float64(z) + W2[j, k] * h1[k])
+                o = _fma32(np.float32(w3[j]), np.float32(max(float(z), 0.0)), o)
+            assert abs(float(o) - out[r]) <= bound[r], (trunc, r)
+            # not vacuous: the BF16 hidden layer costs about 2^-9 times the
+            # absolute path sums (64 x 64 weights of size ~0.2 here)
+            assert bound[r] < 0.2 * (1 + abs(out[r]))
+
+
 def test_forward_zero_output_layer_predicts_zero():
     w = _rand_params(6)
     w[W.OFF_W3:] = 0
