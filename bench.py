@@ -45,7 +45,8 @@ WORKLOADS = {
 }
 METRIC = "PCG edge-iters/s"
 UNIT = "edge-iters/s"
-PROFILE_NOTE = os.path.join(ROOT, "profiles", "spmv_dia_fp64_grid2048.md")
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic.json")
+MU_REF_JSON = os.path.join(ROOT, "tests", "golden", "mu_ref.json")
 NOMINAL_FP64_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x 2 flop x max clock
 
 
@@ -144,27 +145,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def profile_traffic(source_hash):
-    """Per-launch DRAM bytes of the SpMV from the committed ncu summary, when
-    the kernel source has not changed since it was captured."""
-    if not os.path.exists(PROFILE_NOTE):
+def profile_traffic(kernel, source_hash):
+    """Per-launch DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of
+    a kernel from the machine-readable ncu record in profiles/traffic.json,
+    when the kernel's source has not changed since it was captured."""
+    if not os.path.exists(TRAFFIC_JSON):
         return None
-    want = None
-    traffic = None
-    with open(PROFILE_NOTE) as f:
-        for line in f:
-            if line.startswith("source_sha256:"):
-                want = line.split(":", 1)[1].strip()
-            if line.startswith("traffic_bytes_per_launch:"):
-                traffic = float(line.split(":", 1)[1].strip())
-    if want != source_hash:
+    with open(TRAFFIC_JSON) as f:
+        rec = json.load(f).get(kernel)
+    if not rec or rec.get("source_sha256") != source_hash:
         return None
-    return traffic
+    return float(rec["traffic_bytes_per_launch"])
 
 
 def kernel_source_hash():
-    """Hash of the SpMV kernel's source (the PCG-iteration section of pcg.cu
-    up to the vector updates, plus the shared reduction helpers)."""
+    """Hash of the FP64 SpMV kernel's source (the PCG-iteration section of
+    pcg.cu up to the vector updates, plus the shared reduction helpers)."""
     csrc = os.path.join(ROOT, "paper_1501_03105_gb300", "csrc")
     with open(os.path.join(csrc, "pcg.cu")) as f:
         text = f.read()
@@ -173,6 +169,17 @@ def kernel_source_hash():
     h = hashlib.sha256(text[a:b].encode())
     with open(os.path.join(csrc, "device.cuh"), "rb") as f:
         h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def mixed_source_hash():
+    """Hash of the mixed-precision path's source (mixed.cu and the shared
+    device helpers): a traffic record of its fused SpMV holds while it holds."""
+    csrc = os.path.join(ROOT, "paper_1501_03105_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in ("mixed.cu", "device.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -199,34 +206,64 @@ def make_batch(count=64, seed=4):
         return pool.map(_chung_lu_one, jobs)
 
 
-def cpu_oracle_sample(g, budget_s=20.0):
-    """The FP64 oracle's Jacobi-PCG (as it stands) on the x^(0) system of the
-    workload, iterations bounded by a time budget.  Returns a dict."""
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_x0_system(g):
+    """The reduced x^(0) system (W^(0) = C) of the workload, by the oracle."""
     import oracle as O
     prob = O.Problem.from_graph(g)
-    L = O.laplacian(prob, O.initial_conductance(prob))
-    Lt, b = O.reduced_system(prob, L)
-    t0 = time.perf_counter()
-    _, it1, _ = O.pcg_jacobi(Lt, b, None, tol=PCG_TOL, maxit=2)
-    per = (time.perf_counter() - t0) / max(it1, 1)
-    maxit = max(2, min(200, int(budget_s / max(per, 1e-6))))
-    t0 = time.perf_counter()
-    _, it, rel = O.pcg_jacobi(Lt, b, None, tol=PCG_TOL, maxit=maxit)
-    dt = time.perf_counter() - t0
+    Lt, b = O.reduced_system(prob, O.laplacian(prob, O.initial_conductance(prob)))
     e = prob.m - int(np.sum((prob.eu == prob.s) | (prob.ev == prob.s) | (prob.eu == prob.t) | (prob.ev == prob.t)))
-    return {"value": e * it / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle Jacobi-PCG on the x^(0) system of grid2048: {it} iterations "
-                      f"({dt:.1f} s, numpy/scipy, single thread)", "seconds": dt, "iters": it}
+    return Lt, b, e
+
+
+def cpu_oracle_sample(g, budget_s=8.0, threads=0, system=None):
+    """The FP64 oracle's Jacobi-PCG as it stands (its C restatement, OpenMP)
+    on the x^(0) system of the workload, solved from zero to the benchmark's
+    tolerance, repeated until about budget_s seconds of CPU work.  threads 0
+    = every host core.  Returns a dict."""
+    from oracle import pcg_omp
+    Lt, b, e = system if system is not None else oracle_x0_system(g)
+    cores = threads if threads > 0 else pcg_omp.max_threads()
+    its = 0
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        _, it, _ = pcg_omp.pcg_jacobi(Lt, b, None, tol=PCG_TOL, maxit=100000, threads=cores)
+        its += it
+        reps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": e * its / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle Jacobi-PCG (C, OpenMP, FP64) on the x^(0) system of {g.name}, "
+                      f"solved {reps} times from zero to 1e-10 ({its} iterations, {dt:.1f} s, "
+                      f"{cores} thread(s), {cpu_model()})",
+            "seconds": dt, "iters": its}
 
 
 def run_reference(args):
+    """The reference arm: the oracle (FP64, the C restatement of its
+    Jacobi-PCG over every host core) on a bounded sample of the benchmark's
+    workload -- the PCG solves of its x^(0) system."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     g = make_graph()
+    system = oracle_x0_system(g)
     vals = []
     for k in range(args.warmup + args.steps):
-        r = cpu_oracle_sample(g, budget_s=args.ref_budget)
+        r = cpu_oracle_sample(g, budget_s=args.ref_budget, system=system)
         if k >= args.warmup:
             vals.append(r)
     v = sum(r["value"] for r in vals) / len(vals)
@@ -235,13 +272,84 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(vals),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "grid2048: 2048x2048 4-connected segmentation grid, 12 disks, seed 2",
-                       "sample": "Jacobi-PCG on the x^(0) system", "pcg_tol": PCG_TOL},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "config": {"workload": WORKLOADS["grid2048"][3],
+                       "sample": "Jacobi-PCG solves of the x^(0) system", "pcg_tol": PCG_TOL},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
                              "sample": vals[0]["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def golden_mu_ref(name):
+    """The oracle's final sweep-cut value of a workload (Section 3.3), written
+    by tests/golden/make_mu_ref.py; None when it has not been computed."""
+    if not os.path.exists(MU_REF_JSON):
+        return None
+    with open(MU_REF_JSON) as f:
+        rec = json.load(f).get(name)
+    return float(rec["mu_ref"]) if rec else None
+
+
+def time_to_cut(track, mu_ref, rel=1e-6):
+    """Device time from the start of a solve to the end of the first IRLS step
+    whose sweep value is within rel of mu_ref (the sweep after each step is
+    part of the step's time); the last step must be within it too, otherwise
+    not reached.  track: [(sweep value, step ms)] from x^(0) on."""
+    if not mu_ref or not track:
+        return {"ms": None, "step": None, "mu_ref": mu_ref, "reached": False}
+    acc, hit = 0.0, None
+    for l, (cv, ms_l) in enumerate(track):
+        acc += ms_l
+        if hit is None and abs(cv - mu_ref) <= rel * mu_ref:
+            hit = (acc, l)
+    final_err = abs(track[-1][0] - mu_ref) / mu_ref
+    reached = hit is not None and final_err <= rel
+    return {"ms": hit[0] if reached else None, "step": hit[1] if reached else None,
+            "solve_ms": acc, "final_rel_err": final_err, "mu_ref": mu_ref, "reached": reached}
+
+
+def ttc_volume(B, stream, args):
+    """Time to cut (1e-6 relative to the oracle's mu_ref) on the 256^3 volume,
+    T = 30, one solve per arm after a two-step warm-up solve on the same
+    context: plain FP64, mixed precision, and both with the learned warm start
+    (a model trained, untimed, on the IRLS trajectory of the 128^3 volume of
+    the sequence recipe, then frozen)."""
+    import gen
+    mu_ref = golden_mu_ref("vol256")
+    T = 30
+    eps = eps_list(T)
+    g = gen.config_graph(3)
+    gtrain = gen.config_graph(5)
+    opt = B.pirmcut_default_options(pcg_tol=PCG_TOL)
+    with B.Solver(gtrain, opt, stream=stream) as s:
+        s.mlp_enable(B.MLP_PREDICT | B.MLP_TRAIN, seed=5)
+        s.solve(T, eps)
+        w = s.mlp_weights()
+    arms = {}
+    for name, prec, learned in (("fp64", B.PREC_FP64, False), ("mixed", B.PREC_MIXED, False),
+                                ("learned_fp64", B.PREC_FP64, True),
+                                ("learned_mixed", B.PREC_MIXED, True)):
+        opt = B.pirmcut_default_options(pcg_tol=PCG_TOL, precision=prec, track_cut=1,
+                                        inner_tol=args.inner_tol)
+        with B.Solver(g, opt, stream=stream) as s:
+            if learned:
+                s.mlp_enable(B.MLP_PREDICT, seed=5)
+                s.mlp_weights(w)
+            s.solve(2, eps[:2])
+            infos = s.solve(T, eps)
+        r = time_to_cut([(i.cut_value, i.ms) for i in infos], mu_ref)
+        r["pcg_iters"] = int(sum(i.pcg_iters for i in infos))
+        arms[name] = r
+    base = arms["fp64"]["ms"]
+    for r in arms.values():
+        r["speedup_vs_fp64"] = (base / r["ms"]) if (base and r["ms"]) else None
+    return {"workload": "vol256: 256^3 6-connected segmentation volume, ellipsoid, float32 "
+                        "capacities, seed 3, T=30",
+            "mu_ref": mu_ref, "mu_ref_source": "tests/golden/mu_ref.json: the FP64 oracle, "
+                                                "Jacobi-PCG to 1e-12, same eps schedule",
+            "learned_model": "trained on the 128^3 volume (seed 5), 30 IRLS steps x 8 Adam steps",
+            "arms": arms}
 
 
 def run_batch(args):
@@ -466,7 +574,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--ref-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=10.0)
+    ap.add_argument("--no-ttc", action="store_true",
+                    help="skip the time-to-cut arms on the 256^3 volume")
     ap.add_argument("--workload", default="grid2048", choices=list(WORKLOADS) + ["chunglu64", "seq128"])
     ap.add_argument("--problems", type=int, default=200, help="seq128: problems in the sequence")
     ap.add_argument("--seq-scale", type=int, default=128, help="seq128: side of the volume")
@@ -572,70 +682,66 @@ def main():
                     track=[(i.cut_value, i.ms) for i in infos],
                     clocks=clk.summary() if clk else None)
 
-    if args.only == "mixed":
-        r64 = timed(B.PREC_MIXED, with_clocks=True)
-        rmx = r64
-    else:
-        r64 = timed(B.PREC_FP64, with_clocks=True)
-        rmx = timed(B.PREC_MIXED, with_clocks=False) if args.only is None else r64
-    nt, ne, fmt = r64["nt"], r64["ne"], r64["fmt"]
-    iters, ms, launches, cut_value = r64["iters"], r64["ms"], r64["launches"], r64["cut"]
+    r64 = timed(B.PREC_FP64, with_clocks=True) if args.only != "mixed" else None
+    rmx = timed(B.PREC_MIXED, with_clocks=args.only == "mixed") if args.only != "fp64" else None
+    head = r64 if r64 is not None else rmx
+    nt, ne, fmt = head["nt"], head["ne"], head["fmt"]
+    iters, ms, launches, cut_value = head["iters"], head["ms"], head["launches"], head["cut"]
     ms_step = ms / args.steps
-    value = r64["job_units"] / (ms / 1e3)
-    mu_ref = cut_value
+    value = head["job_units"] / (ms / 1e3)
+    mu_ref = golden_mu_ref(args.workload)
 
-    def time_to_cut(track):
-        acc = 0.0
-        for l, (cv, ms_l) in enumerate(track):
-            acc += ms_l
-            if abs(cv - mu_ref) <= 1e-6 * mu_ref:
-                return {"ms": acc, "step": l}
-        return {"ms": None, "step": None}
+    def fp64_roofline(r):
+        # the PCG matrix-vector kernel: its average launch inside a solve (CUDA
+        # events around every launch on the working stream); the isolated
+        # cold-L2 launch is reported beside it
+        cold_ms, spmv_bytes, spmv_flops = r["spmv"]
+        spmv_ms, live_n = r["spmv_live"]
+        gbs = spmv_bytes / (spmv_ms * 1e-3) / 1e9
+        tflops = spmv_flops / (spmv_ms * 1e-3) / 1e12
+        src = kernel_source_hash()
+        return {"bound": "alu", "achieved": tflops, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": tflops / NOMINAL_FP64_TFLOPS,
+                "traffic": profile_traffic(f"k_spmv_dia<2> fp64 {args.workload}", src),
+                "peak_kind": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)",
+                "kernel": "k_spmv_dia<2> FP64 (q = L~p, fused (p,q))",
+                "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak,
+                        "peak_kind": peak_kind},
+                "bytes_per_launch": spmv_bytes, "flops_per_launch": spmv_flops,
+                "launch_ms": spmv_ms, "launches_timed": live_n, "kernel_source": src,
+                "isolated_cold_l2": {"launch_ms": cold_ms,
+                                     "achieved_tflops": spmv_flops / (cold_ms * 1e-3) / 1e12}}
 
-    # roofline of the PCG matrix-vector kernel: its average launch inside a
-    # solve (CUDA events around every launch on the working stream); the
-    # isolated cold-L2 launch time is reported beside it
-    cold_ms, spmv_bytes, spmv_flops = r64["spmv"]
-    spmv_ms, live_n = r64["spmv_live"]
-    gbs = spmv_bytes / (spmv_ms * 1e-3) / 1e9
-    tflops = spmv_flops / (spmv_ms * 1e-3) / 1e12
-    hbm_frac = gbs / hbm_peak
-    alu_frac = tflops / NOMINAL_FP64_TFLOPS
-    src = kernel_source_hash()
-    traffic = profile_traffic(src)
-    roof = {"bound": "alu", "achieved": tflops, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-            "frac": alu_frac, "traffic": traffic,
-            "peak_kind": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)",
-            "kernel": "k_spmv_dia<2> FP64 (q = L~p, fused (p,q))",
-            "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": hbm_frac,
-                    "peak_kind": peak_kind},
-            "bytes_per_launch": spmv_bytes, "flops_per_launch": spmv_flops, "launch_ms": spmv_ms,
-            "launches_timed": live_n,
-            "isolated_cold_l2": {"launch_ms": cold_ms,
-                                 "achieved_tflops": spmv_flops / (cold_ms * 1e-3) / 1e12}}
-    m_cold, m_bytes, m_flops = rmx["spmv"]
-    m_ms, m_live_n = rmx["spmv_live"]
-    m_gbs = m_bytes / (m_ms * 1e-3) / 1e9
-    mixed = {
-        "value": rmx["job_units"] / (rmx["ms"] / 1e3), "unit": UNIT,
-        "ms_per_step": rmx["ms"] / args.steps,
-        "speedup_vs_fp64_per_step": ms_step / (rmx["ms"] / args.steps),
-        "pcg_iters_per_step": rmx["iters"] / args.steps,
-        "refinements_per_step": rmx["refine"] / args.steps,
-        "cut_value": rmx["cut"], "cut_rel_diff_vs_fp64": abs(rmx["cut"] - cut_value) / cut_value,
-        "x_max_abs_diff_vs_fp64": float(np.max(np.abs(rmx["x"] - r64["x"]))),
-        "time_to_cut_1e-6": time_to_cut(rmx["track"]),
-        "gpu_launches": int(rmx["launches"]),
-        "roofline": {"bound": "hbm", "achieved": m_gbs, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": m_gbs / hbm_peak, "peak_kind": peak_kind,
-                     "kernel": "k_spmv32v_fused_dia<2> FP32 (p = r + beta p, d += alpha p, "
-                               "q = A^ p, compensated (p,q))",
-                     "bytes_per_launch": m_bytes, "launch_ms": m_ms, "launches_timed": m_live_n,
-                     "isolated_cold_l2": {"launch_ms": m_cold,
-                                          "achieved_gbs": m_bytes / (m_cold * 1e-3) / 1e9}},
-        "dtype": "f32 inner PCG + f64 residual/refinement (same FP64 stopping test)",
-    }
-    clk_summary = r64["clocks"]
+    def mixed_roofline(r):
+        m_cold, m_bytes, _ = r["spmv"]
+        m_ms, m_live_n = r["spmv_live"]
+        m_gbs = m_bytes / (m_ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": m_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": m_gbs / hbm_peak, "peak_kind": peak_kind,
+                "traffic": profile_traffic(f"k_spmv32v_fused_dia<2> mixed {args.workload}",
+                                           mixed_source_hash()),
+                "kernel": "k_spmv32v_fused_dia<2> FP32 (p = r + beta p, d += alpha p, "
+                          "q = A^ p, compensated (p,q))",
+                "bytes_per_launch": m_bytes, "launch_ms": m_ms, "launches_timed": m_live_n,
+                "isolated_cold_l2": {"launch_ms": m_cold,
+                                     "achieved_gbs": m_bytes / (m_cold * 1e-3) / 1e9}}
+
+    mixed = None
+    if rmx is not None and r64 is not None:
+        mixed = {
+            "value": rmx["job_units"] / (rmx["ms"] / 1e3), "unit": UNIT,
+            "ms_per_step": rmx["ms"] / args.steps,
+            "speedup_vs_fp64_per_step": ms_step / (rmx["ms"] / args.steps),
+            "pcg_iters_per_step": rmx["iters"] / args.steps,
+            "refinements_per_step": rmx["refine"] / args.steps,
+            "cut_value": rmx["cut"], "cut_rel_diff_vs_fp64": abs(rmx["cut"] - cut_value) / cut_value,
+            "x_max_abs_diff_vs_fp64": float(np.max(np.abs(rmx["x"] - r64["x"]))),
+            "time_to_cut_1e-6": time_to_cut(rmx["track"], mu_ref),
+            "gpu_launches": int(rmx["launches"]),
+            "roofline": mixed_roofline(rmx),
+            "dtype": "f32 inner PCG + f64 residual/refinement (same FP64 stopping test)",
+        }
+    clk_summary = head["clocks"]
 
     # end to end through the C ABI from host buffers
     e2e = None
@@ -646,7 +752,9 @@ def main():
         d2h = side_host.nbytes + 8 * 3 + (T_STEPS + 1) * 64
         e_iters = 0
         reps = max(1, min(args.steps, 3))
-        opt = B.pirmcut_default_options(pcg_tol=PCG_TOL, graph_launch=int(args.launch == "graph"))
+        opt = B.pirmcut_default_options(pcg_tol=PCG_TOL, graph_launch=int(args.launch == "graph"),
+                                        precision=B.PREC_MIXED if args.only == "mixed" else B.PREC_FP64,
+                                        inner_tol=args.inner_tol)
         # one untimed pass: the first call of a process loads the library's
         # device code (a one-time cost, like the device-timed warm-up steps)
         h = B.pirmcut_create(g.n, g.row_ptr, g.col, g.c, g.s, g.t, opt, stream)
@@ -671,10 +779,18 @@ def main():
                "includes": "create (host CSR upload, validation and packing on the GPU), solve, "
                            "sweep cut, side D2H, destroy; one untimed pass first"}
 
+    # time to cut on the 256^3 volume, where x^(0)'s sweep is not yet the cut
+    ttc = None
+    if rank == 0 and ws == 1 and not args.no_ttc and args.workload == "grid2048" and args.only is None:
+        ttc = ttc_volume(B, stream, args)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == "grid2048":
-        r = cpu_oracle_sample(g, budget_s=15.0)
-        cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        system = oracle_x0_system(g)
+        all_cores = cpu_oracle_sample(g, budget_s=8.0, system=system)
+        one = cpu_oracle_sample(g, budget_s=8.0, threads=1, system=system)
+        cpu = {k: all_cores[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu["single_thread"] = {k: one[k] for k in ("value", "unit", "cores", "sample")}
 
     if rank == 0:
         # spmv (g^: one value per edge in DIA, value + column per direction
@@ -682,11 +798,14 @@ def main():
         # written, FP32 d^1/2) + update_xp (x^, p read and written, r^)
         g_bytes = 8 * ne if fmt == 1 else 12 * 2 * ne + 8 * nt
         bytes_iter = g_bytes + nt * 8 * 2 + nt * (8 * 3 + 4) + nt * 8 * 5
+        only_mixed = args.only == "mixed"
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 inner PCG + f64 refinement" if only_mixed else "f64", "data": "synthetic",
             "config": {"workload": wl_desc,
+                       "path": "mixed" if only_mixed else "fp64",
                        "n_nonterminal": nt, "n_edges": ne, "format": {1: "DIA", 2: "CSR"}[fmt],
                        "T": T_STEPS, "pcg_tol": PCG_TOL, "eps": "max(0.1*2^-(l-1), 1e-6)",
                        "step": f"x0 + {T_STEPS} IRLS steps + sweep cut",
@@ -695,16 +814,18 @@ def main():
                        "launch": args.launch},
             "pcg_iters_per_step": iters / args.steps,
             "cut_value": cut_value,
-            "hbm_gbs_pcg_algorithmic": bytes_iter * iters / args.steps / (ms_step * 1e-3) / 1e9,
-            "roofline": roof,
-            "time_to_cut_1e-6": time_to_cut(r64["track"]),
+            "cut_rel_diff_vs_oracle": (abs(cut_value - mu_ref) / mu_ref) if mu_ref else None,
+            "roofline": mixed_roofline(head) if only_mixed else fp64_roofline(head),
+            "time_to_cut_1e-6": time_to_cut(head["track"], mu_ref),
             "mixed": mixed,
+            "time_to_cut_vol256": ttc,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": int(launches),
             "clocks": clk_summary,
-            "kernel_source": src,
         }
+        if not only_mixed:
+            line["hbm_gbs_pcg_algorithmic"] = bytes_iter * iters / args.steps / (ms_step * 1e-3) / 1e9
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

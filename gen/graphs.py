@@ -117,6 +117,56 @@ def segmentation_grid(I: np.ndarray, sigma: float = 0.1, tscale: float = 2.0,
     c_pq = exp(-(I_p - I_q)^2 / (2 sigma^2)); terminal capacities
     c_sp = tscale * I_p and c_pt = tscale * (1 - I_p); s = N, t = N + 1.
     Terminal edges whose capacity is 0 (clipped pixels) are still stored.
+
+    The CSR is written row by row in column order without a sort: a pixel
+    row lists its lower neighbours (largest stride first), its upper
+    neighbours (smallest stride first), then s and t; rows s and t list every
+    pixel.  Equal, entry for entry, to :func:`segmentation_grid_from_edges`.
+    """
+    shape = I.shape
+    flat = I.reshape(-1)
+    N = flat.shape[0]
+    nd = I.ndim
+    strides = [int(np.prod(shape[ax + 1:], dtype=np.int64)) for ax in range(nd)]
+    p = np.arange(N, dtype=np.int64)
+    coord = [(p // strides[ax]) % shape[ax] for ax in range(nd)]
+    slots = []  # (valid, column) in column order
+    for ax in range(nd):                      # p - stride, largest stride first
+        slots.append((coord[ax] > 0, p - strides[ax]))
+    for ax in reversed(range(nd)):            # p + stride, smallest stride first
+        slots.append((coord[ax] < shape[ax] - 1, p + strides[ax]))
+    k = len(slots) + 2
+    valid = np.ones((N, k), dtype=bool)
+    cols = np.empty((N, k), dtype=np.int32)
+    caps = np.empty((N, k), dtype=np.float64)
+    for j, (ok, q) in enumerate(slots):
+        qq = np.where(ok, q, p)
+        valid[:, j] = ok
+        cols[:, j] = qq
+        caps[:, j] = np.exp(-((flat - flat[qq]) ** 2) / (2.0 * sigma * sigma))
+    cols[:, k - 2] = N
+    caps[:, k - 2] = tscale * flat
+    cols[:, k - 1] = N + 1
+    caps[:, k - 1] = tscale * (1.0 - flat)
+    counts = np.concatenate([valid.sum(axis=1), [N, N]]).astype(np.int64)
+    row_ptr = np.zeros(N + 3, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    vm = valid.reshape(-1)
+    col = np.concatenate([cols.reshape(-1)[vm], np.arange(N, dtype=np.int32),
+                          np.arange(N, dtype=np.int32)])
+    c = np.concatenate([caps.reshape(-1)[vm], tscale * flat, tscale * (1.0 - flat)])
+    return Graph(N + 2, row_ptr, col, c, N, N + 1, name=name)
+
+
+def segmentation_grid_from_edges(I: np.ndarray, sigma: float = 0.1, tscale: float = 2.0,
+                                 name: str = "") -> Graph:
+    """The graph of :func:`segmentation_grid` built from an edge list and a
+    global sort (the plain construction; kept to check the direct one).
+
+    Pixel p = x + W*y (+ W*H*z).  Neighbour capacity
+    c_pq = exp(-(I_p - I_q)^2 / (2 sigma^2)); terminal capacities
+    c_sp = tscale * I_p and c_pt = tscale * (1 - I_p); s = N, t = N + 1.
+    Terminal edges whose capacity is 0 (clipped pixels) are still stored.
     """
     flat = I.reshape(-1)
     N = flat.shape[0]

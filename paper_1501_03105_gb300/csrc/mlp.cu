@@ -169,12 +169,24 @@ k_features_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __rest
 // Each thread keeps its B fragments of W1 and W2 (BF16) in registers.
 // ---------------------------------------------------------------------------
 
-struct MlpFrags {
-  uint32_t w1[8][2];     // layer 1, per 8-unit output tile: K pairs (2t, 2t+1) and (8+2t, 9+2t)
-  uint32_t w2[8][4][2];  // layer 2, [output tile][16-wide K chunk]
-  uint32_t b2[8];        // (b2[8j+2t], b2[8j+2t+1]) as BF16 pairs
-  uint32_t w3[8];        // (w3[8j+2t], w3[8j+2t+1])
+// Weights of the tensor-core evaluation, staged once per block in shared
+// memory in the order the fragments are read: the layer-2 B fragments as
+// [output tile j][K chunk c][lane] pairs of 32-bit words (one 8-byte load per
+// fragment, consecutive lanes on consecutive words: no bank conflicts).
+struct MlpSmem {
+  uint2 w2[8][4][32];
+  uint32_t w1[8][32][2];  // layer 1, [output tile][lane]: K pairs (2t, 2t+1), (8+2t, 9+2t)
+  uint32_t b2[8][4];      // [tile j][t]: (b2[8j+2t], b2[8j+2t+1]) as BF16 pairs
+  uint32_t w3[8][4];
   float b3;
+};
+
+struct MlpFrags {
+  uint32_t w1[8][2];     // layer 1, per 8-unit output tile
+  uint32_t b2[8];
+  uint32_t w3[8];
+  float b3;
+  const uint2* w2;       // this lane's layer-2 fragments in shared memory, stride 32
 };
 
 __device__ __forceinline__ uint32_t bf16_bits(const __nv_bfloat16* p) {
@@ -209,25 +221,41 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// This thread's fragments of the BF16 weights (lane = 4 g + t).
-__device__ __forceinline__ void load_frags(const __nv_bfloat16* __restrict__ w16, MlpFrags& F) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int u = 8 * j + g;  // the output unit of this thread's B column
+// The block stages the weights (every thread of the block takes part; ends
+// with a barrier), then each thread takes its small fragments into registers.
+__device__ __forceinline__ void load_frags(const __nv_bfloat16* __restrict__ w16, MlpSmem& S,
+                                           MlpFrags& F) {
+  for (int idx = threadIdx.x; idx < 8 * 4 * 32; idx += blockDim.x) {
+    const int j = idx >> 7, c = (idx >> 5) & 3, ln = idx & 31;
+    const int u = 8 * j + (ln >> 2), t = ln & 3;
+    S.w2[j][c][ln] = make_uint2(bf16_pair(w16 + OFF_W2 + u * H + 16 * c + 2 * t),
+                                bf16_pair(w16 + OFF_W2 + u * H + 16 * c + 8 + 2 * t));
+  }
+  for (int idx = threadIdx.x; idx < 8 * 32; idx += blockDim.x) {
+    const int j = idx >> 5, ln = idx & 31;
+    const int u = 8 * j + (ln >> 2), t = ln & 3;
     const uint32_t head = t < 3 ? bf16_pair(w16 + OFF_W1 + u * NF + 2 * t)  // (W1[u][2t], W1[u][2t+1])
                                 : bf16_bits(w16 + OFF_B1 + u);              // (b1[u], 0)
-    F.w1[j][0] = head;
-    F.w1[j][1] = t < 3 ? head : 0u;  // the tails of the features meet the same weights
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      F.w2[j][c][0] = bf16_pair(w16 + OFF_W2 + u * H + 16 * c + 2 * t);
-      F.w2[j][c][1] = bf16_pair(w16 + OFF_W2 + u * H + 16 * c + 8 + 2 * t);
-    }
-    F.b2[j] = bf16_pair(w16 + OFF_B2 + 8 * j + 2 * t);
-    F.w3[j] = bf16_pair(w16 + OFF_W3 + 8 * j + 2 * t);
+    S.w1[j][ln][0] = head;
+    S.w1[j][ln][1] = t < 3 ? head : 0u;  // the tails of the features meet the same weights
   }
-  F.b3 = bf16_lo(bf16_bits(w16 + OFF_B3));
+  if (threadIdx.x < 32) {
+    const int j = threadIdx.x >> 2, t = threadIdx.x & 3;
+    S.b2[j][t] = bf16_pair(w16 + OFF_B2 + 8 * j + 2 * t);
+    S.w3[j][t] = bf16_pair(w16 + OFF_W3 + 8 * j + 2 * t);
+  }
+  if (threadIdx.x == 0) S.b3 = bf16_lo(bf16_bits(w16 + OFF_B3));
+  __syncthreads();
+  const int lane = threadIdx.x & 31, t = lane & 3;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    F.w1[j][0] = S.w1[j][lane][0];
+    F.w1[j][1] = S.w1[j][lane][1];
+    F.b2[j] = S.b2[j][t];
+    F.w3[j] = S.w3[j][t];
+  }
+  F.b3 = S.b3;
+  F.w2 = &S.w2[0][0][lane];
 }
 
 constexpr int kStage = 9;  // words per row of a warp's A-fragment staging area (8 + 1 pad)
@@ -280,7 +308,10 @@ __device__ __forceinline__ float mlp_warp32(const MlpFrags& W, const float (&f)[
       const float bl = bf16_lo(W.b2[j]), bh = bf16_hi(W.b2[j]);
       float d[4] = {bl, bh, bl, bh};
 #pragma unroll
-      for (int c = 0; c < 4; ++c) mma_bf16_16816(d, a2[c], W.w2[j][c][0], W.w2[j][c][1]);
+      for (int c = 0; c < 4; ++c) {
+        const uint2 b = W.w2[(j * 4 + c) * 32];
+        mma_bf16_16816(d, a2[c], b.x, b.y);
+      }
       const float wl = bf16_lo(W.w3[j]), wh = bf16_hi(W.w3[j]);
       pg = fmaf(fmaxf(d[0], 0.f), wl, pg);
       pg = fmaf(fmaxf(d[1], 0.f), wh, pg);
@@ -407,7 +438,7 @@ __device__ __forceinline__ void features_dia32(const DiaDesc& d, const double* _
 // and, with kPredict, the network's output into dir (FP64).  A warp takes 32
 // consecutive rows at a time.
 template <int K, bool kPredict>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 4)
 k_mlp_fused_dia(DiaDesc d, const double* __restrict__ g, const double* __restrict__ gprev,
                 const double* __restrict__ cs, const double* __restrict__ ct,
                 const double* __restrict__ x, const double* __restrict__ eps_list,
@@ -415,12 +446,13 @@ k_mlp_fused_dia(DiaDesc d, const double* __restrict__ g, const double* __restric
                 const __nv_bfloat16* __restrict__ w16, float* __restrict__ feat, int with_feat,
                 double* __restrict__ dir) {
   __shared__ uint32_t stage_all[4][32 * kStage];
+  __shared__ MlpSmem wsm;
   const int64_t nt = d.nt;
   const double eps = eps_list[C->eps_idx];
   const float eps2f = float(eps) * float(eps);
   const float log_eps8 = logf(float(eps)) * 0.125f;
   MlpFrags W;
-  if (kPredict) load_frags(w16, W);
+  if (kPredict) load_frags(w16, wsm, W);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* stage = stage_all[warp];
   const int64_t tiles = (nt + 31) / 32;
@@ -444,12 +476,13 @@ k_mlp_fused_dia(DiaDesc d, const double* __restrict__ g, const double* __restric
 // The network on stored feature rows (CSR problems, and the inference entry
 // point): delta -> dir (FP64) or out32 (FP32).
 template <bool kF32>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 4)
 k_mlp_predict_tc(int64_t nt, const float* __restrict__ f, const __nv_bfloat16* __restrict__ w16,
                  double* __restrict__ dir, float* __restrict__ out32) {
   __shared__ uint32_t stage_all[4][32 * kStage];
+  __shared__ MlpSmem wsm;
   MlpFrags W;
-  load_frags(w16, W);
+  load_frags(w16, wsm, W);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* stage = stage_all[warp];
   const int64_t tiles = (nt + 31) / 32;
@@ -468,12 +501,12 @@ k_mlp_predict_tc(int64_t nt, const float* __restrict__ f, const __nv_bfloat16* _
   }
 }
 
-// Grid of the warp-tile kernels: 4 warps of 32 rows per block, at most three
-// blocks per SM (about 160 registers a thread).
+// Grid of the warp-tile kernels: 4 warps of 32 rows per block, four blocks
+// per SM (at most 128 registers a thread), every warp walking several tiles.
 inline int mlp_tile_grid(int64_t rows) {
   const int64_t tiles = (rows + 31) / 32;
   int64_t b = (tiles + 3) / 4;
-  if (b > 152 * 3) b = 152 * 3;
+  if (b > 152 * 4) b = 152 * 4;
   return int(b < 1 ? 1 : b);
 }
 

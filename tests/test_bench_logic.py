@@ -1,0 +1,41 @@
+"""Host logic of bench.py: time-to-cut against a reference value (reading
+c10: the first step within 1e-6, and the last step must be within it too),
+the oracle's reference values on file, and the CPU baseline's sample."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import gen  # noqa: E402
+
+
+def test_time_to_cut_first_step_within_tolerance():
+    track = [(110.0, 1.0), (100.5, 2.0), (100.001, 3.0), (100.0000001, 4.0), (100.0, 5.0)]
+    r = bench.time_to_cut(track, 100.0)
+    assert r["reached"] and r["step"] == 3 and r["ms"] == 10.0 and r["solve_ms"] == 15.0
+
+
+def test_time_to_cut_requires_the_last_step():
+    track = [(100.0, 1.0), (100.0, 1.0), (100.01, 1.0)]
+    r = bench.time_to_cut(track, 100.0)
+    assert not r["reached"] and r["ms"] is None and r["final_rel_err"] == pytest.approx(1e-4)
+
+
+def test_time_to_cut_without_reference():
+    assert bench.time_to_cut([(1.0, 1.0)], None)["reached"] is False
+
+
+def test_oracle_reference_values_on_file():
+    mu = bench.golden_mu_ref("grid2048")
+    assert mu is not None and mu > 0
+    assert bench.golden_mu_ref("no-such-workload") is None
+
+
+def test_cpu_baseline_sample_counts_iterations_and_cores():
+    g = gen.config_graph(1, scale=32)
+    r = bench.cpu_oracle_sample(g, budget_s=0.05, threads=2)
+    assert r["cores"] == 2 and r["iters"] > 0 and r["value"] > 0 and r["kind"] == "oracle"
