@@ -352,6 +352,60 @@ def ttc_volume(B, stream, args):
             "arms": arms}
 
 
+def run_mlp(args):
+    """Throughput of the learned warm start's network on the tensor cores:
+    pirmcut_mlp_predict (6 -> 64 -> 64 -> 1, BF16 operands, FP32
+    accumulation) on 16M seeded feature rows resident in device memory,
+    CUDA events around each launch, after warm-up.  Algorithmic flops per
+    row: 2 (6 * 64 + 64 * 64 + 64) = 9088."""
+    import torch
+    import gen
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_1501_03105_gb300 import binding as B
+    from paper_1501_03105_gb300 import build as _build
+    if not os.path.exists(B.LIB_PATH):
+        _build.build()
+    rows = args.mlp_rows
+    rng = np.random.default_rng(7)
+    w = rng.normal(0, 0.2, 4673).astype(np.float32)
+    F = torch.from_numpy(rng.normal(0, 1, (rows, 6)).astype(np.float32)).cuda()
+    out = torch.empty(rows, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    g = gen.config_graph(1, scale=8)
+    with B.Solver(g, stream=stream) as s:
+        s.mlp_enable(B.MLP_PREDICT, seed=1)
+        s.mlp_weights(w)
+        for _ in range(args.warmup):
+            s.mlp_predict(F, out)
+        torch.cuda.synchronize()
+        times = []
+        with ClockSampler(local) as clk:
+            for _ in range(args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.mlp_predict(F, out)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+    ms = float(np.median(times))
+    flops = 9088.0 * rows
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak = json.load(open(p)).get("bf16_tflops", 1900.0) if os.path.exists(p) else 1900.0
+    tf = flops / (ms * 1e-3) / 1e12
+    line = {"metric": "MLP inference TFLOP/s", "value": tf, "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "bf16 operands, f32 accumulate", "data": "synthetic",
+            "config": {"workload": f"mlp: {rows} feature rows, 6 -> 64 -> 64 -> 1", "rows": rows},
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tf / peak, "peak_kind": "measured bf16 burst (cuBLAS)",
+                         "bytes_per_launch": 28.0 * rows,
+                         "hbm_gbs": 28.0 * rows / (ms * 1e-3) / 1e9},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batch(args):
     """64 uneven Chung-Lu FlowImprove-style instances solved as one batch
     (one launch per kernel for all instances), against the same instances
@@ -577,7 +631,10 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=10.0)
     ap.add_argument("--no-ttc", action="store_true",
                     help="skip the time-to-cut arms on the 256^3 volume")
-    ap.add_argument("--workload", default="grid2048", choices=list(WORKLOADS) + ["chunglu64", "seq128"])
+    ap.add_argument("--workload", default="grid2048",
+                    choices=list(WORKLOADS) + ["chunglu64", "seq128", "mlp"])
+    ap.add_argument("--mlp-rows", type=int, default=16 * 1024 * 1024,
+                    help="mlp: feature rows per inference launch")
     ap.add_argument("--problems", type=int, default=200, help="seq128: problems in the sequence")
     ap.add_argument("--seq-scale", type=int, default=128, help="seq128: side of the volume")
     ap.add_argument("--seq-tol", type=float, default=PCG_TOL, help="seq128: PCG tolerance")
@@ -595,6 +652,8 @@ def main():
         return run_batch(args)
     if args.workload == "seq128":
         return run_sequence(args)
+    if args.workload == "mlp":
+        return run_mlp(args)
 
     import torch
     ws, rank, local = dist_env()

@@ -66,18 +66,33 @@ struct BArgs {
   double* partials;     // NV * ntiles
   int ntiles;
   int* active;
+  // the CG iterations' work list (rebuilt at the head of every iteration):
+  // the active instances in order and the prefix sums of their tile counts
+  const int* act_inst;  // [count]
+  const int* act_pref;  // [count + 1]; act_pref[n_act] = active tiles
+  const int* n_act;     // number of active instances
 };
+
+// Tile of virtual index v of the work list (v < act_pref[n_act]).
+__device__ __forceinline__ int work_tile(const BArgs& a, int n, int v) {
+  int lo = 0, hi = n;  // act_pref[lo] <= v < act_pref[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(a.act_pref + mid) <= v) lo = mid;
+    else hi = mid;
+  }
+  return a.insts[a.act_inst[lo]].t0 + (v - a.act_pref[lo]);
+}
 
 __device__ __forceinline__ int64_t deg_of(const BArgs& a, int64_t r) { return a.rp[r + 1] - a.rp[r]; }
 
 // Per-tile partials -> per-instance totals.  Returns true in every thread of
 // the block that finished the instance; totals valid in thread 0.
 template <int NV>
-__device__ __forceinline__ bool inst_sum(const BArgs& a, const Tile& tl, double (&v)[NV],
+__device__ __forceinline__ bool inst_sum(const BArgs& a, const Tile& tl, int tile, double (&v)[NV],
                                          int site, double (&tot)[NV]) {
   __shared__ unsigned int s_last;
   block_sum<NV>(v);
-  const int tile = blockIdx.x;
   const BInst in = a.insts[tl.inst];
   if (threadIdx.x == 0) {
 #pragma unroll
@@ -246,7 +261,7 @@ kb_assemble(BArgs a, const double* __restrict__ g, BAssemble b) {
     }
   }
   double v[3] = {rz, rr, bb}, tot[3];
-  if (inst_sum<3>(a, tl, v, 0, tot) && threadIdx.x == 0) {
+  if (inst_sum<3>(a, tl, int(blockIdx.x), v, 0, tot) && threadIdx.x == 0) {
     PcgState* S = &a.S[tl.inst];
     S->rz = tot[0];
     S->rr = tot[1];
@@ -272,70 +287,112 @@ kb_assemble(BArgs a, const double* __restrict__ g, BAssemble b) {
 // PCG iteration
 // ---------------------------------------------------------------------------
 
+// Work list of a CG iteration: the instances that have not stopped, in
+// order, with the prefix sums of their tile counts (one block, fixed order).
+// Instances that stopped cost the iteration's kernels nothing.
+__global__ void __launch_bounds__(kBT)
+kb_worklist(BArgs a, int count, int* act_inst, int* act_pref, int* n_act) {
+  __shared__ int s_cnt[kBT], s_tiles[kBT];
+  const int per = (count + kBT - 1) / kBT;  // consecutive instances per thread
+  const int i0 = threadIdx.x * per, i1 = min(count, i0 + per);
+  int cnt = 0, tiles = 0;
+  for (int i = i0; i < i1; ++i)
+    if (!a.S[i].stop_req) {
+      ++cnt;
+      tiles += a.insts[i].t1 - a.insts[i].t0;
+    }
+  s_cnt[threadIdx.x] = cnt;
+  s_tiles[threadIdx.x] = tiles;
+  __syncthreads();
+  if (threadIdx.x == 0) {  // exclusive scan in place, in thread order
+    int c = 0, t = 0;
+    for (int k = 0; k < kBT; ++k) {
+      const int ck = s_cnt[k], tk = s_tiles[k];
+      s_cnt[k] = c;
+      s_tiles[k] = t;
+      c += ck;
+      t += tk;
+    }
+    *n_act = c;
+    act_pref[c] = t;
+  }
+  __syncthreads();
+  int j = s_cnt[threadIdx.x], t = s_tiles[threadIdx.x];
+  for (int i = i0; i < i1; ++i)
+    if (!a.S[i].stop_req) {
+      act_inst[j] = i;
+      act_pref[j] = t;
+      ++j;
+      t += a.insts[i].t1 - a.insts[i].t0;
+    }
+}
+
+// The CG iteration kernels run a fixed grid; each block walks the work list.
 template <int G>
 __global__ void __launch_bounds__(kBT)
 kb_spmv(BArgs a, const double* __restrict__ g, const double* __restrict__ diag,
         const double* __restrict__ p, double* __restrict__ q) {
-  const Tile tl = a.tiles[blockIdx.x];
-  PcgState* S = &a.S[tl.inst];
-  if (S->stop_req) {  // instance finished: nothing to do (no partial either)
-    if (threadIdx.x == 0) S->stopped = 1;
-    return;
-  }
-  const int64_t base = a.insts[tl.inst].base;
-  double pq = 0.0;
-  if (tl.kind == kHubTile) {
-    const int64_t r = tl.r0;
-    double acc = 0.0;
-    for (int64_t e = a.rp[r] + threadIdx.x; e < a.rp[r + 1]; e += kBT)
-      acc = fma(-g[e], p[base + a.col[e]], acc);
-    acc = block_total(acc);
-    if (threadIdx.x == 0) {
-      acc = fma(diag[r], p[r], acc);
-      q[r] = acc;
-      pq = p[r] * acc;
-    }
-  } else if (tl.kind == kMediumTile) {
-    const int lane = threadIdx.x & 31;
-    for (int64_t m = tl.r0 + threadIdx.x / 32; m < tl.r1; m += kBT / 32) {
-      const int64_t r = a.med[m];
+  const int n = *a.n_act;
+  const int work = a.act_pref[n];
+  for (int v = blockIdx.x; v < work; v += gridDim.x) {
+    const int tile = work_tile(a, n, v);
+    const Tile tl = a.tiles[tile];
+    PcgState* S = &a.S[tl.inst];
+    const int64_t base = a.insts[tl.inst].base;
+    double pq = 0.0;
+    if (tl.kind == kHubTile) {
+      const int64_t r = tl.r0;
       double acc = 0.0;
-      acc = row_dot_neg(g, a.col, p + base, a.rp[r] + lane, a.rp[r + 1], 32, acc);
-      acc = group_reduce<32>(acc, 0xffffffffu);
-      if (lane == 0) {
-        const double pr = p[r];
-        acc = fma(diag[r], pr, acc);
+      for (int64_t e = a.rp[r] + threadIdx.x; e < a.rp[r + 1]; e += kBT)
+        acc = fma(-g[e], p[base + a.col[e]], acc);
+      acc = block_total(acc);
+      if (threadIdx.x == 0) {
+        acc = fma(diag[r], p[r], acc);
         q[r] = acc;
-        pq = fma(pr, acc, pq);
+        pq = p[r] * acc;
       }
-    }
-  } else {
-    const int lane = threadIdx.x % G;
-    const unsigned mask = group_mask<G>();
-    for (int64_t r = tl.r0 + threadIdx.x / G; r < tl.r1; r += kBT / G) {
-      if (deg_of(a, r) > a.mid_deg) continue;
-      double acc = 0.0;
-      acc = row_dot_neg(g, a.col, p + base, a.rp[r] + lane, a.rp[r + 1], G, acc);
-      acc = group_reduce<G>(acc, mask);
-      if (lane == 0) {
-        const double pr = p[r];
-        acc = fma(diag[r], pr, acc);
-        q[r] = acc;
-        pq = fma(pr, acc, pq);
+    } else if (tl.kind == kMediumTile) {
+      const int lane = threadIdx.x & 31;
+      for (int64_t m = tl.r0 + threadIdx.x / 32; m < tl.r1; m += kBT / 32) {
+        const int64_t r = a.med[m];
+        double acc = 0.0;
+        acc = row_dot_neg(g, a.col, p + base, a.rp[r] + lane, a.rp[r + 1], 32, acc);
+        acc = group_reduce<32>(acc, 0xffffffffu);
+        if (lane == 0) {
+          const double pr = p[r];
+          acc = fma(diag[r], pr, acc);
+          q[r] = acc;
+          pq = fma(pr, acc, pq);
+        }
       }
-    }
-  }
-  double v[1] = {pq}, tot[1];
-  if (inst_sum<1>(a, tl, v, 1, tot) && threadIdx.x == 0) {
-    const double al = S->rz / tot[0];
-    S->pq = tot[0];
-    if (!(tot[0] > 0.0) || !isfinite(al)) {
-      S->alpha = 0.0;
-      S->status = PIRMCUT_ENUMERIC;
-      S->stop_req = 1;
-      atomicSub(a.active, 1);
     } else {
-      S->alpha = al;
+      const int lane = threadIdx.x % G;
+      const unsigned mask = group_mask<G>();
+      for (int64_t r = tl.r0 + threadIdx.x / G; r < tl.r1; r += kBT / G) {
+        if (deg_of(a, r) > a.mid_deg) continue;
+        double acc = 0.0;
+        acc = row_dot_neg(g, a.col, p + base, a.rp[r] + lane, a.rp[r + 1], G, acc);
+        acc = group_reduce<G>(acc, mask);
+        if (lane == 0) {
+          const double pr = p[r];
+          acc = fma(diag[r], pr, acc);
+          q[r] = acc;
+          pq = fma(pr, acc, pq);
+        }
+      }
+    }
+    double vv[1] = {pq}, tot[1];
+    if (inst_sum<1>(a, tl, tile, vv, 1, tot) && threadIdx.x == 0) {
+      const double al = S->rz / tot[0];
+      S->pq = tot[0];
+      if (!(tot[0] > 0.0) || !isfinite(al)) {
+        S->alpha = 0.0;
+        S->status = PIRMCUT_ENUMERIC;
+        S->stop_req = 1;
+        atomicSub(a.active, 1);
+      } else {
+        S->alpha = al;
+      }
     }
   }
 }
@@ -345,46 +402,57 @@ kb_spmv(BArgs a, const double* __restrict__ g, const double* __restrict__ diag,
 __global__ void __launch_bounds__(kBT)
 kb_update_r(BArgs a, double* __restrict__ qz, const double* __restrict__ dinv,
             double* __restrict__ r) {
-  const Tile tl = a.tiles[blockIdx.x];
-  PcgState* S = &a.S[tl.inst];
-  if (S->stop_req) return;
-  const double alpha = S->alpha;
-  double rz = 0.0, rr = 0.0;
-  if (tl.kind == kRangeTile) {
-    for (int64_t i = tl.r0 + threadIdx.x; i < tl.r1; i += kBT) {
-      const double ri = fma(-alpha, qz[i], r[i]);
-      const double zi = dinv[i] * ri;
-      r[i] = ri;
-      qz[i] = zi;
-      rz = fma(ri, zi, rz);
-      rr = fma(ri, ri, rr);
+  const int n = *a.n_act;
+  const int work = a.act_pref[n];
+  for (int v = blockIdx.x; v < work; v += gridDim.x) {
+    const int tile = work_tile(a, n, v);
+    const Tile tl = a.tiles[tile];
+    PcgState* S = &a.S[tl.inst];
+    if (S->stop_req) continue;  // broke down in this iteration's SpMV (the instance agrees)
+    const double alpha = S->alpha;
+    double rz = 0.0, rr = 0.0;
+    if (tl.kind == kRangeTile) {
+      for (int64_t i = tl.r0 + threadIdx.x; i < tl.r1; i += kBT) {
+        const double ri = fma(-alpha, qz[i], r[i]);
+        const double zi = dinv[i] * ri;
+        r[i] = ri;
+        qz[i] = zi;
+        rz = fma(ri, zi, rz);
+        rr = fma(ri, ri, rr);
+      }
     }
-  }
-  double v[2] = {rz, rr}, tot[2];
-  if (inst_sum<2>(a, tl, v, 2, tot) && threadIdx.x == 0) {
-    const int it = S->iters + 1;
-    S->iters = it;
-    const double beta = tot[0] / S->rz;
-    S->beta = beta;
-    S->rz = tot[0];
-    S->rr = tot[1];
-    int stop = (tot[1] <= S->tol2 * S->bb) || it >= S->maxit;
-    if (!isfinite(tot[1]) || !isfinite(beta)) {
-      stop = 1;
-      S->status = PIRMCUT_ENUMERIC;
-      S->beta = 0.0;
+    double vv[2] = {rz, rr}, tot[2];
+    if (inst_sum<2>(a, tl, tile, vv, 2, tot) && threadIdx.x == 0) {
+      const int it = S->iters + 1;
+      S->iters = it;
+      const double beta = tot[0] / S->rz;
+      S->beta = beta;
+      S->rz = tot[0];
+      S->rr = tot[1];
+      int stop = (tot[1] <= S->tol2 * S->bb) || it >= S->maxit;
+      if (!isfinite(tot[1]) || !isfinite(beta)) {
+        stop = 1;
+        S->status = PIRMCUT_ENUMERIC;
+        S->beta = 0.0;
+      }
+      S->stop_req = stop;
+      if (stop) atomicSub(a.active, 1);
     }
-    S->stop_req = stop;
-    if (stop) atomicSub(a.active, 1);
   }
 }
 
+// x += alpha p, p = z + beta p for the instances of this iteration's list
+// (an instance that stopped in this iteration's residual update still takes
+// its last step); ends the loop once no instance is active.
 __global__ void __launch_bounds__(kBT)
 kb_update_xp(BArgs a, double* __restrict__ x, double* __restrict__ p, const double* __restrict__ z,
              cudaGraphConditionalHandle h, int use_cond) {
-  const Tile tl = a.tiles[blockIdx.x];
-  PcgState* S = &a.S[tl.inst];
-  if (tl.kind == kRangeTile && !S->stopped) {
+  const int n = *a.n_act;
+  const int work = a.act_pref[n];
+  for (int v = blockIdx.x; v < work; v += gridDim.x) {
+    const Tile tl = a.tiles[work_tile(a, n, v)];
+    if (tl.kind != kRangeTile) continue;
+    const PcgState* S = &a.S[tl.inst];
     const double alpha = S->alpha, beta = S->beta;
     for (int64_t i = tl.r0 + threadIdx.x; i < tl.r1; i += kBT) {
       const double pi = p[i];
@@ -516,6 +584,10 @@ struct Batch {
   Tile* tiles = nullptr;
   int64_t* med = nullptr;
   BInst* insts = nullptr;
+  int* act_inst = nullptr;   // CG work list: active instances, prefix of their tiles, count
+  int* act_pref = nullptr;
+  int* n_act = nullptr;
+  int work_grid = 608;       // blocks of the CG iteration kernels (SMs x resident blocks)
   PcgState* S = nullptr;
   double* partials = nullptr;
   int* active = nullptr;
@@ -550,7 +622,21 @@ BArgs make_args(Batch& b) {
   a.partials = b.partials;
   a.ntiles = int(b.h_tiles.size());
   a.active = b.active;
+  a.act_inst = b.act_inst;
+  a.act_pref = b.act_pref;
+  a.n_act = b.n_act;
   return a;
+}
+
+// Blocks of the CG iteration kernels: every block resident at once, never
+// more than there are tiles.
+int work_grid(const Batch& b) {
+  const int nt = int(b.h_tiles.size());
+  return nt < b.work_grid ? nt : b.work_grid;
+}
+
+void enqueue_worklist(Batch& b, cudaStream_t st) {
+  kb_worklist<<<1, kBT, 0, st>>>(make_args(b), b.count, b.act_inst, b.act_pref, b.n_act);
 }
 
 void build_tiles(Batch& b) {
@@ -600,8 +686,8 @@ cudaError_t upload_tiles(Batch& b) {
 
 void enqueue_spmv(Batch& b, cudaStream_t st, const double* g) {
   BArgs a = make_args(b);
-  const int nt = int(b.h_tiles.size());
-  PIRMCUT_DISPATCH_G(b.G, (kb_spmv<GG><<<nt, kBT, 0, st>>>(a, g, b.diag, b.p, b.q)));
+  const int wg = work_grid(b);
+  PIRMCUT_DISPATCH_G(b.G, (kb_spmv<GG><<<wg, kBT, 0, st>>>(a, g, b.diag, b.p, b.q)));
 }
 
 int enqueue_bstep(Batch& b, cudaStream_t st, bool initial, cudaGraphConditionalHandle h,
@@ -638,10 +724,12 @@ int enqueue_bstep(Batch& b, cudaStream_t st, bool initial, cudaGraphConditionalH
     ++k;
     if (as.zero_start) cudaMemsetAsync(b.x, 0, sizeof(double) * b.N, st);
   } else if (part == 1) {
+    const int wg = work_grid(b);
+    enqueue_worklist(b, st);
     enqueue_spmv(b, st, b.gval);
-    kb_update_r<<<nt, kBT, 0, st>>>(a, b.q, b.dinv, b.r);
-    kb_update_xp<<<nt, kBT, 0, st>>>(a, b.x, b.p, b.q, h, use_cond);
-    k += 3;
+    kb_update_r<<<wg, kBT, 0, st>>>(a, b.q, b.dinv, b.r);
+    kb_update_xp<<<wg, kBT, 0, st>>>(a, b.x, b.p, b.q, h, use_cond);
+    k += 4;
   } else {
     kb_zero_if_b0<<<nt, kBT, 0, st>>>(a, b.x);
     kb_step_end<<<nt, kBT, 0, st>>>(a, b.x, b.recs, b.rec_cap, b.C, b.eps_list, initial ? 0 : 1);
@@ -699,7 +787,8 @@ cudaError_t build_bgraph(Batch& b, bool initial, cudaGraphExec_t* out) {
 
 void free_batch(Batch& b) {
   void* ps[] = {b.rp, b.col, b.cval, b.gval, b.cs, b.ct, b.x, b.r, b.p, b.q, b.diag, b.dinv,
-                b.tiles, b.med, b.insts, b.S, b.partials, b.active, b.C, b.eps_list, b.recs, b.xfull};
+                b.tiles, b.med, b.insts, b.S, b.partials, b.active, b.C, b.eps_list, b.recs, b.xfull,
+                b.act_inst, b.act_pref, b.n_act};
   for (void* p : ps)
     if (p) cudaFree(p);
   sweep_free(b.view);
@@ -753,6 +842,7 @@ cudaError_t autotune(Batch& b) {
       float tot = 0.f;
       for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
         e = cudaMemcpy(b.S, st.data(), sizeof(PcgState) * b.count, cudaMemcpyHostToDevice);
+        enqueue_worklist(b, b.stream);
         cudaEventRecord(e0, b.stream);
         enqueue_spmv(b, b.stream, b.gval);
         cudaEventRecord(e1, b.stream);
@@ -896,6 +986,9 @@ pirmcut_status pirmcut_batch_create(int count, const int64_t* n, const int64_t* 
   A((void**)&b.gval, sizeof(double) * b.M);
   for (double** v : {&b.cs, &b.ct, &b.x, &b.r, &b.p, &b.q, &b.diag, &b.dinv}) A((void**)v, sizeof(double) * b.N);
   A((void**)&b.insts, sizeof(BInst) * count);
+  A((void**)&b.act_inst, sizeof(int) * count);
+  A((void**)&b.act_pref, sizeof(int) * (count + 1));
+  A((void**)&b.n_act, sizeof(int));
   A((void**)&b.S, sizeof(PcgState) * count);
   A((void**)&b.active, sizeof(int));
   A((void**)&b.C, sizeof(StepCounters));
@@ -912,6 +1005,13 @@ pirmcut_status pirmcut_batch_create(int count, const int64_t* n, const int64_t* 
   if (e != cudaSuccess) return bail(e, "upload");
   // hub rows: more entries than 32 threads can cover in 16 passes
   b.heavy_deg = kHubDeg;
+  {
+    int dev = 0, sms = 152, per_sm = 4;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_update_r, kBT, 0);
+    b.work_grid = std::max(1, sms) * std::max(1, std::min(per_sm, 8));
+  }
   e = autotune(b);
   if (e != cudaSuccess) return bail(e, "autotune");
   *out = h;
@@ -1008,7 +1108,7 @@ pirmcut_status pirmcut_batch_solve(pirmcut_batch* h, int T, const double* eps, p
       if (st == PIRMCUT_ENUMERIC) worst = PIRMCUT_ENUMERIC;
       else if (st == PIRMCUT_ENOCONV && worst == PIRMCUT_OK) worst = PIRMCUT_ENOCONV;
     }
-    if (graphs) b.launches += 8 + 3 * (it_total + 1);
+    if (graphs) b.launches += 8 + 4 * (it_total + 1);
   }
   if (worst != PIRMCUT_OK) return bfail(h, worst, "an instance did not converge or broke down");
   return PIRMCUT_OK;
