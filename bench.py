@@ -330,8 +330,9 @@ def ttc_volume(B, stream, args):
     for name, prec, learned in (("fp64", B.PREC_FP64, False), ("mixed", B.PREC_MIXED, False),
                                 ("learned_fp64", B.PREC_FP64, True),
                                 ("learned_mixed", B.PREC_MIXED, True)):
+        # the volume's capacities are float32 values: handed over as floats
         opt = B.pirmcut_default_options(pcg_tol=PCG_TOL, precision=prec, track_cut=1,
-                                        inner_tol=args.inner_tol)
+                                        inner_tol=args.inner_tol, capacity_fp32=1)
         with B.Solver(g, opt, stream=stream) as s:
             if learned:
                 s.mlp_enable(B.MLP_PREDICT, seed=5)

@@ -108,6 +108,12 @@ typedef struct {
   int step_stats;      /* 1: every step also records its objective and flow
                           value in pirmcut_step_info (one more pass over the
                           edges per step); batches leave them NaN             */
+  int capacity_fp32;   /* 0: the capacities c passed to pirmcut_create and
+                          pirmcut_update_weights are double[nnz]; 1: they are
+                          float[nnz] (half the bytes to copy in), widened
+                          exactly to FP64 by the library: the problem is the
+                          same as for the doubles of equal value.  Batches
+                          take doubles.                                      */
 } pirmcut_options;
 
 typedef struct {
@@ -132,7 +138,8 @@ typedef struct {
 
 /* Fill *opt with the defaults: WEIGHTED_L1, FP64, pcg_tol 1e-10,
  * pcg_max_iter 20000, warm_start 1, FORMAT_AUTO, track_cut 0, graph_launch 1,
- * inner_tol 1e-5, time_spmv 0, reduce_on_host 0, batch_* 0, step_stats 0.  With MIXED,
+ * inner_tol 1e-5, time_spmv 0, reduce_on_host 0, batch_* 0, step_stats 0,
+ * capacity_fp32 0.  With MIXED,
  * pcg_iters counts FP32 inner iterations, at most
  * min(pcg_max_iter, 2000) per refinement cycle and 64 cycles per system. */
 void pirmcut_default_options(pirmcut_options* opt);
@@ -144,7 +151,8 @@ void pirmcut_default_options(pirmcut_options* opt);
  * n        number of vertices (>= 3 and < 2^31), terminals included.
  * row_ptr  int64[n+1], CSR row offsets, row_ptr[0] = 0, non-decreasing.
  * col      int32[row_ptr[n]], neighbour ids in [0, n).
- * c        double[row_ptr[n]], capacities, finite and >= 0.
+ * c        double[row_ptr[n]] (float[row_ptr[n]] with opt->capacity_fp32),
+ *          capacities, finite and >= 0.
  *          The CSR must be symmetric: each undirected edge {u, v} appears in
  *          row u and in row v with the same total capacity.  Parallel entries
  *          of one pair are summed; self-loops are rejected.
@@ -162,7 +170,7 @@ void pirmcut_default_options(pirmcut_options* opt);
  * Errors: EINVAL (malformed input), EDISCONNECTED, ENOMEM, ECUDA.
  */
 pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* col,
-                              const double* c, int32_t s, int32_t t,
+                              const void* c, int32_t s, int32_t t,
                               const pirmcut_options* opt, int mem_kind, void* stream,
                               pirmcut_ctx** out);
 
@@ -219,11 +227,12 @@ pirmcut_status pirmcut_set_x(pirmcut_ctx* ctx, const double* x, int mem_kind);
 
 /*
  * Replace the capacities of the instance while keeping its structure (a
- * sequence of related problems, Section 6): c is double[nnz] in the CSR
- * layout given to pirmcut_create.  The current x is kept as a warm start.
+ * sequence of related problems, Section 6): c is double[nnz] (float[nnz]
+ * with options.capacity_fp32) in the CSR layout given to pirmcut_create.
+ * The current x is kept as a warm start.
  * Errors: EINVAL (non-finite, negative or asymmetric c), EDISCONNECTED, ECUDA.
  */
-pirmcut_status pirmcut_update_weights(pirmcut_ctx* ctx, const double* c, int mem_kind);
+pirmcut_status pirmcut_update_weights(pirmcut_ctx* ctx, const void* c, int mem_kind);
 
 /* Sizes of the reduced problem: n~ (non-terminals), e~ (non-terminal
  * undirected edges), and the storage format chosen (PIRMCUT_FORMAT_DIA/CSR). */

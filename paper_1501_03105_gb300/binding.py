@@ -37,7 +37,7 @@ class Options(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("time_spmv", ctypes.c_int),
                 ("reduce_on_host", ctypes.c_int), ("batch_threads_per_row", ctypes.c_int),
                 ("batch_tile_rows", ctypes.c_int), ("batch_medium_deg", ctypes.c_int),
-                ("step_stats", ctypes.c_int)]
+                ("step_stats", ctypes.c_int), ("capacity_fp32", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):
@@ -198,10 +198,12 @@ def pirmcut_default_options(**kw) -> Options:
 
 
 def pirmcut_create(n, row_ptr, col, c, s, t, opt: Options | None = None, stream=None):
-    """Create a context; returns the opaque handle (int).  Raises PirmcutError."""
+    """Create a context; returns the opaque handle (int).  Raises PirmcutError.
+    c is float64, or float32 when opt.capacity_fp32 is set."""
     prp, k1, a1 = _ptr(row_ptr, np.int64)
     pcl, k2, a2 = _ptr(col, np.int32)
-    pc, k3, a3 = _ptr(c, np.float64)
+    fp32 = opt is not None and opt.capacity_fp32
+    pc, k3, a3 = _ptr(c, np.float32 if fp32 else np.float64)
     if len({k1, k2, k3}) != 1:
         raise ValueError("row_ptr, col and c must live in the same memory")
     h = _P()
@@ -275,8 +277,10 @@ def pirmcut_set_x(h, x):
     _check(h, lib().pirmcut_set_x(h, p, kind))
 
 
-def pirmcut_update_weights(h, c):
-    p, kind, keep = _ptr(c, np.float64)
+def pirmcut_update_weights(h, c, fp32=False):
+    """New capacities (float32 when the context was created with
+    capacity_fp32, else float64) on the same structure."""
+    p, kind, keep = _ptr(c, np.float32 if fp32 else np.float64)
     _check(h, lib().pirmcut_update_weights(h, p, kind))
 
 
@@ -503,7 +507,9 @@ class Solver:
         if opt is None:
             opt = pirmcut_default_options(**kw)
         self.n = int(graph.n)
-        self.h = pirmcut_create(graph.n, graph.row_ptr, graph.col, graph.c, graph.s, graph.t,
+        self.fp32 = bool(opt.capacity_fp32)
+        c = graph.c.astype(np.float32) if self.fp32 and isinstance(graph.c, np.ndarray) else graph.c
+        self.h = pirmcut_create(graph.n, graph.row_ptr, graph.col, c, graph.s, graph.t,
                                 opt, stream)
 
     def initial(self):
@@ -530,7 +536,9 @@ class Solver:
         pirmcut_set_x(self.h, x)
 
     def update_weights(self, c):
-        pirmcut_update_weights(self.h, c)
+        if self.fp32 and isinstance(c, np.ndarray):
+            c = c.astype(np.float32)
+        pirmcut_update_weights(self.h, c, self.fp32)
 
     def problem_size(self):
         return pirmcut_problem_size(self.h)

@@ -89,6 +89,10 @@ pirmcut_status check_options(const pirmcut_options& o, std::string* msg) {
     *msg = "unknown format";
     return PIRMCUT_EINVAL;
   }
+  if (o.capacity_fp32 != 0 && o.capacity_fp32 != 1) {
+    *msg = "capacity_fp32 must be 0 or 1";
+    return PIRMCUT_EINVAL;
+  }
   if (o.step_stats != 0 && o.step_stats != 1) {
     *msg = "step_stats must be 0 or 1";
     return PIRMCUT_EINVAL;
@@ -104,6 +108,36 @@ cudaError_t to_host(pirmcut::hvec<T>& dst, const T* src, size_t count, int mem_k
   if (mem_kind == PIRMCUT_MEM_DEVICE)
     return cudaMemcpy(dst.data(), src, sizeof(T) * count, cudaMemcpyDeviceToHost);
   pirmcut::parallel_copy(dst.data(), src, int64_t(count));
+  return cudaSuccess;
+}
+
+// The capacities as doubles on the host for the host reduction: read in
+// place (host doubles), copied (device doubles), or widened exactly from
+// floats (options.capacity_fp32), in parallel.
+cudaError_t host_capacities(pirmcut::hvec<double>& buf, const void* c, int fp32, size_t nnz,
+                            int mem_kind, const double** out) {
+  if (!fp32) {
+    if (mem_kind != PIRMCUT_MEM_DEVICE) {
+      *out = static_cast<const double*>(c);
+      return cudaSuccess;
+    }
+    cudaError_t e = to_host(buf, static_cast<const double*>(c), nnz, mem_kind);
+    *out = buf.data();
+    return e;
+  }
+  pirmcut::hvec<float> f;
+  const float* src = static_cast<const float*>(c);
+  if (mem_kind == PIRMCUT_MEM_DEVICE) {
+    cudaError_t e = to_host(f, src, nnz, mem_kind);
+    if (e != cudaSuccess) return e;
+    src = f.data();
+  }
+  buf.resize(nnz);
+  double* dst = buf.data();
+  pirmcut::parallel_for(int64_t(nnz), [=](int64_t lo, int64_t hi) {
+    for (int64_t k = lo; k < hi; ++k) dst[k] = double(src[k]);
+  }, 1 << 20);
+  *out = buf.data();
   return cudaSuccess;
 }
 
@@ -453,10 +487,11 @@ void pirmcut_default_options(pirmcut_options* opt) {
   opt->batch_tile_rows = 0;
   opt->batch_medium_deg = 0;
   opt->step_stats = 0;
+  opt->capacity_fp32 = 0;
 }
 
 pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* col,
-                              const double* c, int32_t s, int32_t t,
+                              const void* c, int32_t s, int32_t t,
                               const pirmcut_options* opt, int mem_kind, void* stream,
                               pirmcut_ctx** out) {
   if (!out) return fail(nullptr, PIRMCUT_EINVAL, "out must not be NULL");
@@ -480,7 +515,8 @@ pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* 
   if (!o.reduce_on_host) {
     // a failed device attempt (no device, no memory, an unusable storage
     // request) leaves the problem and its diagnosis to the host reduction
-    pirmcut_status dps = pirmcut::reduce_graph_device(n, row_ptr, col, c, s, t, o.format, mem_kind,
+    pirmcut_status dps = pirmcut::reduce_graph_device(n, row_ptr, col, c, o.capacity_fp32, s, t,
+                                                      o.format, mem_kind,
                                                       stream, nullptr, nullptr, &dhg, &dg, &taken, &msg);
     if (dps != PIRMCUT_OK) {
       taken = false;
@@ -500,11 +536,8 @@ pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* 
   if (nnz < 0 || rp[0] != 0) return fail(nullptr, PIRMCUT_EINVAL, "bad row_ptr");
   if (nnz > 0 && (!col || !c)) return fail(nullptr, PIRMCUT_EINVAL, "col and c must not be NULL");
   e = to_host(cl, col, size_t(nnz), mem_kind);
-  const double* cin = c;
-  if (e == cudaSuccess && mem_kind == PIRMCUT_MEM_DEVICE) {
-    e = to_host(cv, c, size_t(nnz), mem_kind);
-    cin = cv.data();
-  }
+  const double* cin = static_cast<const double*>(c);
+  if (e == cudaSuccess) e = host_capacities(cv, c, o.capacity_fp32, size_t(nnz), mem_kind, &cin);
   if (e != cudaSuccess) return fail(nullptr, PIRMCUT_ECUDA, std::string("reading the graph: ") + cudaGetErrorString(e));
 
   pirmcut_ctx* h = new (std::nothrow) pirmcut_ctx();
@@ -646,7 +679,7 @@ void drop_graphs_baking_cst(Ctx& c, double old_cst) {
 }
 }  // namespace
 
-pirmcut_status pirmcut_update_weights(pirmcut_ctx* h, const double* cnew, int mem_kind) {
+pirmcut_status pirmcut_update_weights(pirmcut_ctx* h, const void* cnew, int mem_kind) {
   if (!h) return fail(nullptr, PIRMCUT_EINVAL, "ctx is NULL");
   Ctx& c = h->c;
   if (mem_kind != PIRMCUT_MEM_HOST && mem_kind != PIRMCUT_MEM_DEVICE)
@@ -658,7 +691,8 @@ pirmcut_status pirmcut_update_weights(pirmcut_ctx* h, const double* cnew, int me
     pirmcut::HostGraph ng;
     bool taken = false;
     std::string msg;
-    pirmcut_status dps = pirmcut::reduce_graph_device(c.hg.n, nullptr, nullptr, cnew, c.hg.s, c.hg.t,
+    pirmcut_status dps = pirmcut::reduce_graph_device(c.hg.n, nullptr, nullptr, cnew,
+                                                      c.opt.capacity_fp32, c.hg.s, c.hg.t,
                                                       c.format, mem_kind, c.stream, c.d_in_rp,
                                                       c.d_in_col, &ng, &dg, &taken, &msg);
     if (dps != PIRMCUT_OK) return fail(h, dps, msg);
@@ -696,11 +730,8 @@ pirmcut_status pirmcut_update_weights(pirmcut_ctx* h, const double* cnew, int me
   const int64_t nnz = c.in_rp.back();
   if (nnz > 0 && !cnew) return fail(h, PIRMCUT_EINVAL, "c must not be NULL");
   pirmcut::hvec<double> cv;
-  const double* cin = cnew;
-  if (mem_kind == PIRMCUT_MEM_DEVICE) {
-    CK(h, to_host(cv, cnew, size_t(nnz), mem_kind), "reading c");
-    cin = cv.data();
-  }
+  const double* cin = static_cast<const double*>(cnew);
+  CK(h, host_capacities(cv, cnew, c.opt.capacity_fp32, size_t(nnz), mem_kind, &cin), "reading c");
   pirmcut::HostGraph ng;
   std::string msg;
   pirmcut_status ps = pirmcut::reduce_graph(c.hg.n, c.in_rp.data(), c.in_col.data(), cin,

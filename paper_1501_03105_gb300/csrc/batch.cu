@@ -71,7 +71,20 @@ struct BArgs {
   const int* act_inst;  // [count]
   const int* act_pref;  // [count + 1]; act_pref[n_act] = active tiles
   const int* n_act;     // number of active instances
+  int* work_next;       // [3] next work item of the three iteration kernels
+  const int* order;     // instances, heaviest row first (the work list's order)
 };
+
+// Next item of a kernel's work list for this block (every thread gets it):
+// blocks take items as they free up, so that long tiles (hub rows) do not
+// hold up a fixed share of the list.
+__device__ __forceinline__ int next_item(int* counter) {
+  __shared__ int s_item;
+  __syncthreads();  // every thread has read the previous item
+  if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+  __syncthreads();
+  return s_item;
+}
 
 // Tile of virtual index v of the work list (v < act_pref[n_act]).
 __device__ __forceinline__ int work_tile(const BArgs& a, int n, int v) {
@@ -293,14 +306,16 @@ kb_assemble(BArgs a, const double* __restrict__ g, BAssemble b) {
 __global__ void __launch_bounds__(kBT)
 kb_worklist(BArgs a, int count, int* act_inst, int* act_pref, int* n_act) {
   __shared__ int s_cnt[kBT], s_tiles[kBT];
-  const int per = (count + kBT - 1) / kBT;  // consecutive instances per thread
+  const int per = (count + kBT - 1) / kBT;  // consecutive list positions per thread
   const int i0 = threadIdx.x * per, i1 = min(count, i0 + per);
   int cnt = 0, tiles = 0;
-  for (int i = i0; i < i1; ++i)
+  for (int k = i0; k < i1; ++k) {
+    const int i = a.order[k];
     if (!a.S[i].stop_req) {
       ++cnt;
       tiles += a.insts[i].t1 - a.insts[i].t0;
     }
+  }
   s_cnt[threadIdx.x] = cnt;
   s_tiles[threadIdx.x] = tiles;
   __syncthreads();
@@ -315,16 +330,21 @@ kb_worklist(BArgs a, int count, int* act_inst, int* act_pref, int* n_act) {
     }
     *n_act = c;
     act_pref[c] = t;
+    a.work_next[0] = 0;
+    a.work_next[1] = 0;
+    a.work_next[2] = 0;
   }
   __syncthreads();
   int j = s_cnt[threadIdx.x], t = s_tiles[threadIdx.x];
-  for (int i = i0; i < i1; ++i)
+  for (int k = i0; k < i1; ++k) {
+    const int i = a.order[k];
     if (!a.S[i].stop_req) {
       act_inst[j] = i;
       act_pref[j] = t;
       ++j;
       t += a.insts[i].t1 - a.insts[i].t0;
     }
+  }
 }
 
 // The CG iteration kernels run a fixed grid; each block walks the work list.
@@ -334,7 +354,7 @@ kb_spmv(BArgs a, const double* __restrict__ g, const double* __restrict__ diag,
         const double* __restrict__ p, double* __restrict__ q) {
   const int n = *a.n_act;
   const int work = a.act_pref[n];
-  for (int v = blockIdx.x; v < work; v += gridDim.x) {
+  for (int v = next_item(a.work_next); v < work; v = next_item(a.work_next)) {
     const int tile = work_tile(a, n, v);
     const Tile tl = a.tiles[tile];
     PcgState* S = &a.S[tl.inst];
@@ -404,7 +424,7 @@ kb_update_r(BArgs a, double* __restrict__ qz, const double* __restrict__ dinv,
             double* __restrict__ r) {
   const int n = *a.n_act;
   const int work = a.act_pref[n];
-  for (int v = blockIdx.x; v < work; v += gridDim.x) {
+  for (int v = next_item(a.work_next + 1); v < work; v = next_item(a.work_next + 1)) {
     const int tile = work_tile(a, n, v);
     const Tile tl = a.tiles[tile];
     PcgState* S = &a.S[tl.inst];
@@ -449,7 +469,7 @@ kb_update_xp(BArgs a, double* __restrict__ x, double* __restrict__ p, const doub
              cudaGraphConditionalHandle h, int use_cond) {
   const int n = *a.n_act;
   const int work = a.act_pref[n];
-  for (int v = blockIdx.x; v < work; v += gridDim.x) {
+  for (int v = next_item(a.work_next + 2); v < work; v = next_item(a.work_next + 2)) {
     const Tile tl = a.tiles[work_tile(a, n, v)];
     if (tl.kind != kRangeTile) continue;
     const PcgState* S = &a.S[tl.inst];
@@ -587,6 +607,8 @@ struct Batch {
   int* act_inst = nullptr;   // CG work list: active instances, prefix of their tiles, count
   int* act_pref = nullptr;
   int* n_act = nullptr;
+  int* work_next = nullptr;  // [3]
+  int* order = nullptr;      // instances by descending largest row degree
   int work_grid = 608;       // blocks of the CG iteration kernels (SMs x resident blocks)
   PcgState* S = nullptr;
   double* partials = nullptr;
@@ -625,6 +647,8 @@ BArgs make_args(Batch& b) {
   a.act_inst = b.act_inst;
   a.act_pref = b.act_pref;
   a.n_act = b.n_act;
+  a.work_next = b.work_next;
+  a.order = b.order;
   return a;
 }
 
@@ -640,16 +664,14 @@ void enqueue_worklist(Batch& b, cudaStream_t st) {
 }
 
 void build_tiles(Batch& b) {
+  // per instance: hub tiles first (the longest work items), then medium
+  // tiles, then consecutive-row tiles
   b.h_tiles.clear();
   b.h_med.clear();
   for (int i = 0; i < b.count; ++i) {
     BInst& in = b.h_insts[i];
     const HostGraph& g = b.hg[i];
     in.t0 = int32_t(b.h_tiles.size());
-    for (int64_t r0 = 0; r0 < g.nt; r0 += b.tile_rows) {
-      const int64_t r1 = std::min<int64_t>(g.nt, r0 + b.tile_rows);
-      b.h_tiles.push_back(Tile{i, kRangeTile, in.base + r0, in.base + r1});
-    }
     const int64_t m0 = int64_t(b.h_med.size());
     for (int64_t r = 0; r < g.nt; ++r) {
       const int64_t deg = g.rp[r + 1] - g.rp[r];
@@ -661,6 +683,10 @@ void build_tiles(Batch& b) {
     const int64_t m1 = int64_t(b.h_med.size());
     for (int64_t m = m0; m < m1; m += kMediumRowsPerTile)
       b.h_tiles.push_back(Tile{i, kMediumTile, m, std::min<int64_t>(m1, m + kMediumRowsPerTile)});
+    for (int64_t r0 = 0; r0 < g.nt; r0 += b.tile_rows) {
+      const int64_t r1 = std::min<int64_t>(g.nt, r0 + b.tile_rows);
+      b.h_tiles.push_back(Tile{i, kRangeTile, in.base + r0, in.base + r1});
+    }
     in.t1 = int32_t(b.h_tiles.size());
   }
 }
@@ -788,7 +814,7 @@ cudaError_t build_bgraph(Batch& b, bool initial, cudaGraphExec_t* out) {
 void free_batch(Batch& b) {
   void* ps[] = {b.rp, b.col, b.cval, b.gval, b.cs, b.ct, b.x, b.r, b.p, b.q, b.diag, b.dinv,
                 b.tiles, b.med, b.insts, b.S, b.partials, b.active, b.C, b.eps_list, b.recs, b.xfull,
-                b.act_inst, b.act_pref, b.n_act};
+                b.act_inst, b.act_pref, b.n_act, b.work_next, b.order};
   for (void* p : ps)
     if (p) cudaFree(p);
   sweep_free(b.view);
@@ -989,6 +1015,8 @@ pirmcut_status pirmcut_batch_create(int count, const int64_t* n, const int64_t* 
   A((void**)&b.act_inst, sizeof(int) * count);
   A((void**)&b.act_pref, sizeof(int) * (count + 1));
   A((void**)&b.n_act, sizeof(int));
+  A((void**)&b.work_next, sizeof(int) * 3);
+  A((void**)&b.order, sizeof(int) * count);
   A((void**)&b.S, sizeof(PcgState) * count);
   A((void**)&b.active, sizeof(int));
   A((void**)&b.C, sizeof(StepCounters));
@@ -1003,6 +1031,22 @@ pirmcut_status pirmcut_batch_create(int count, const int64_t* n, const int64_t* 
   if (e == cudaSuccess)
     e = cudaHostAlloc((void**)&b.h_ctr, sizeof(StepCounters) + sizeof(int), cudaHostAllocDefault);
   if (e != cudaSuccess) return bail(e, "upload");
+  // the work list's instance order: largest row degree first, then larger
+  // instances first (longest work items early)
+  {
+    std::vector<int> ord(count);
+    std::vector<int64_t> maxdeg(count, 0);
+    for (int i = 0; i < count; ++i) {
+      ord[i] = i;
+      const HostGraph& g = b.hg[i];
+      for (int64_t r = 0; r < g.nt; ++r) maxdeg[i] = std::max(maxdeg[i], g.rp[r + 1] - g.rp[r]);
+    }
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+      return maxdeg[x] != maxdeg[y] ? maxdeg[x] > maxdeg[y] : b.hg[x].nt > b.hg[y].nt;
+    });
+    e = cudaMemcpy(b.order, ord.data(), sizeof(int) * count, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(e, "upload");
+  }
   // hub rows: more entries than 32 threads can cover in 16 passes
   b.heavy_deg = kHubDeg;
   {

@@ -312,12 +312,19 @@ void DeviceGraph::release() {
   *this = DeviceGraph();
 }
 
+// float -> double, exact
+__global__ void k_widen(int64_t n, const float* __restrict__ in, double* __restrict__ out) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = double(in[i]);
+}
+
 // Returns PIRMCUT_OK with *taken = true when the GPU built the problem (the
 // arrays in *dg, the scalars in *g), PIRMCUT_OK with *taken = false when the
 // host must do it, or a CUDA error status.  rp_dev / col_dev: when non-null,
 // the input structure already on the device (kept from an earlier call).
 pirmcut_status reduce_graph_device(int64_t n, const int64_t* row_ptr, const int32_t* col,
-                                   const double* c, int32_t s, int32_t t, int format_req,
+                                   const void* c, int c_fp32, int32_t s, int32_t t, int format_req,
                                    int mem_kind, void* stream, const int64_t* rp_dev,
                                    const int32_t* col_dev, HostGraph* g, DeviceGraph* dg,
                                    bool* taken, std::string* err) {
@@ -331,6 +338,7 @@ pirmcut_status reduce_graph_device(int64_t n, const int64_t* row_ptr, const int3
   int64_t* d_cnt = nullptr;
   int64_t* d_tile = nullptr;
   double* d_c = nullptr;
+  float* d_c32 = nullptr;     // float capacities uploaded from the host
   double* d_cs_s = nullptr;
   double* d_ct_t = nullptr;
   double* d_small = nullptr;  // [cst_s, cst_t, sum]
@@ -340,7 +348,7 @@ pirmcut_status reduce_graph_device(int64_t n, const int64_t* row_ptr, const int3
   pirmcut_status ret = PIRMCUT_OK;
   DeviceGraph out;
   auto cleanup = [&]() {
-    void* ps[] = {d_cnt, d_tile, d_c, d_cs_s, d_ct_t, d_small, d_flags, d_off};
+    void* ps[] = {d_cnt, d_tile, d_c, d_c32, d_cs_s, d_ct_t, d_small, d_flags, d_off};
     for (void* p : ps)
       if (p) cudaFree(p);
   };
@@ -390,8 +398,22 @@ pirmcut_status reduce_graph_device(int64_t n, const int64_t* row_ptr, const int3
       return cuda_error(e, "uploading the graph");
   }
   if (nnz > 0 && !c) return give_up();
-  const double* dc = c;
-  if (mem_kind != PIRMCUT_MEM_DEVICE) {
+  const double* dc = static_cast<const double*>(c);
+  if (c_fp32) {
+    // float capacities: uploaded as they are (half the bytes of doubles)
+    // and widened exactly on the GPU
+    const float* src = static_cast<const float*>(c);
+    if (mem_kind != PIRMCUT_MEM_DEVICE) {
+      if ((e = dmalloc(&d_c32, size_t(nnz))) != cudaSuccess) return cuda_error(e, "cudaMalloc");
+      if (nnz && (e = cudaMemcpyAsync(d_c32, c, sizeof(float) * size_t(nnz), h2d, st)) != cudaSuccess)
+        return cuda_error(e, "uploading the capacities");
+      src = d_c32;
+    }
+    if ((e = dmalloc(&d_c, size_t(nnz))) != cudaSuccess) return cuda_error(e, "cudaMalloc");
+    if (nnz) k_widen<<<grid_for(nnz), kThreads, 0, st>>>(nnz, src, d_c);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "widening the capacities");
+    dc = d_c;
+  } else if (mem_kind != PIRMCUT_MEM_DEVICE) {
     if ((e = dmalloc(&d_c, size_t(nnz))) != cudaSuccess) return cuda_error(e, "cudaMalloc");
     if (nnz && (e = cudaMemcpyAsync(d_c, c, sizeof(double) * size_t(nnz), h2d, st)) != cudaSuccess)
       return cuda_error(e, "uploading the capacities");

@@ -207,10 +207,11 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
 // The same reduction on the GPU for inputs whose rows list strictly increasing
 // columns and whose non-terminals all have a terminal capacity; *taken says
 // whether it built the problem (otherwise the host reduction must run).
+// c is double[nnz], or float[nnz] when c_fp32 (widened exactly on the GPU).
 // mem_kind says where row_ptr, col and c live; rp_dev / col_dev, when non-null,
 // are an input structure already on the device (owned by the caller).
 pirmcut_status reduce_graph_device(int64_t n, const int64_t* row_ptr, const int32_t* col,
-                                   const double* c, int32_t s, int32_t t, int format_req,
+                                   const void* c, int c_fp32, int32_t s, int32_t t, int format_req,
                                    int mem_kind, void* stream, const int64_t* rp_dev,
                                    const int32_t* col_dev, HostGraph* g, DeviceGraph* dg,
                                    bool* taken, std::string* err);

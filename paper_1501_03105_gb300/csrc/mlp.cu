@@ -279,7 +279,10 @@ __device__ __forceinline__ float mlp_warp32(const MlpFrags& W, const float (&f)[
   my[6] = pack_bf16(f[4] - bf16_lo(h2), f[5] - bf16_hi(h2));
   my[7] = 0u;
   __syncwarp();
-  float out_g[2], out_g8[2];
+  // layer 1 of both 16-row halves (bias through the constant-1 column),
+  // ReLU, BF16: the A fragments of layer 2 (K chunk c = hidden units
+  // 16c .. 16c + 15)
+  uint32_t a2[2][4][4];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int r0 = 16 * h + g, r1 = r0 + 8;
@@ -288,42 +291,49 @@ __device__ __forceinline__ float mlp_warp32(const MlpFrags& W, const float (&f)[
     a[1] = stage[r1 * kStage + t];
     a[2] = stage[r0 * kStage + 4 + t];
     a[3] = stage[r1 * kStage + 4 + t];
-    // layer 1 (bias through the constant-1 column), ReLU, BF16: the A
-    // fragments of layer 2 (K chunk c = hidden units 16c .. 16c + 15)
-    uint32_t a2[4][4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
       mma_bf16_16816(d0, a, W.w1[2 * c][0], W.w1[2 * c][1]);
       mma_bf16_16816(d1, a, W.w1[2 * c + 1][0], W.w1[2 * c + 1][1]);
-      a2[c][0] = pack_relu_bf16(d0[0], d0[1]);
-      a2[c][1] = pack_relu_bf16(d0[2], d0[3]);
-      a2[c][2] = pack_relu_bf16(d1[0], d1[1]);
-      a2[c][3] = pack_relu_bf16(d1[2], d1[3]);
+      a2[h][c][0] = pack_relu_bf16(d0[0], d0[1]);
+      a2[h][c][1] = pack_relu_bf16(d0[2], d0[3]);
+      a2[h][c][2] = pack_relu_bf16(d1[0], d1[1]);
+      a2[h][c][3] = pack_relu_bf16(d1[2], d1[3]);
     }
-    // layer 2 from b2, then ReLU and the dot with w3 (FP32)
-    float pg = 0.f, pg8 = 0.f;
+  }
+  // layer 2 from b2 for both halves (each W2 fragment loaded once, two
+  // independent accumulation chains), then ReLU and the dot with w3 (FP32)
+  float pg[2] = {0.f, 0.f}, pg8[2] = {0.f, 0.f};
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float bl = bf16_lo(W.b2[j]), bh = bf16_hi(W.b2[j]);
-      float d[4] = {bl, bh, bl, bh};
+  for (int j = 0; j < 8; ++j) {
+    const float bl = bf16_lo(W.b2[j]), bh = bf16_hi(W.b2[j]);
+    float d[2][4] = {{bl, bh, bl, bh}, {bl, bh, bl, bh}};
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const uint2 b = W.w2[(j * 4 + c) * 32];
-        mma_bf16_16816(d, a2[c], b.x, b.y);
-      }
-      const float wl = bf16_lo(W.w3[j]), wh = bf16_hi(W.w3[j]);
-      pg = fmaf(fmaxf(d[0], 0.f), wl, pg);
-      pg = fmaf(fmaxf(d[1], 0.f), wh, pg);
-      pg8 = fmaf(fmaxf(d[2], 0.f), wl, pg8);
-      pg8 = fmaf(fmaxf(d[3], 0.f), wh, pg8);
+    for (int c = 0; c < 4; ++c) {
+      const uint2 b = W.w2[(j * 4 + c) * 32];
+      mma_bf16_16816(d[0], a2[0][c], b.x, b.y);
+      mma_bf16_16816(d[1], a2[1][c], b.x, b.y);
     }
-    pg += __shfl_xor_sync(0xffffffffu, pg, 1);
-    pg += __shfl_xor_sync(0xffffffffu, pg, 2);
-    pg8 += __shfl_xor_sync(0xffffffffu, pg8, 1);
-    pg8 += __shfl_xor_sync(0xffffffffu, pg8, 2);
-    out_g[h] = pg + W.b3;
-    out_g8[h] = pg8 + W.b3;
+    const float wl = bf16_lo(W.w3[j]), wh = bf16_hi(W.w3[j]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      pg[h] = fmaf(fmaxf(d[h][0], 0.f), wl, pg[h]);
+      pg[h] = fmaf(fmaxf(d[h][1], 0.f), wh, pg[h]);
+      pg8[h] = fmaf(fmaxf(d[h][2], 0.f), wl, pg8[h]);
+      pg8[h] = fmaf(fmaxf(d[h][3], 0.f), wh, pg8[h]);
+    }
+  }
+  float out_g[2], out_g8[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float u = pg[h], v = pg8[h];
+    u += __shfl_xor_sync(0xffffffffu, u, 1);
+    u += __shfl_xor_sync(0xffffffffu, u, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    out_g[h] = u + W.b3;
+    out_g8[h] = v + W.b3;
   }
   // back to one row per lane through the staging area
   __syncwarp();

@@ -147,3 +147,51 @@ def test_invalid_inputs_report_the_same_error(P, name, g):
             P.Solver(g, reduce_on_host=host)
         msgs.append((ei.value.status, ei.value.message))
     assert msgs[0] == msgs[1]
+
+
+@pytest.mark.parametrize("host", [0, 1])
+@pytest.mark.parametrize("name,make", GRAPHS)
+def test_float32_capacities_give_the_same_problem(P, name, make, host):
+    """options.capacity_fp32: float capacities (host and device buffers) are
+    widened exactly, so the solve equals the one from the doubles of equal
+    value bit for bit; update_weights takes floats the same way."""
+    import torch
+    B = P.binding
+    g = make()
+    c32 = g.c.astype(np.float32)
+    g64 = gen.Graph(g.n, g.row_ptr, g.col, c32.astype(np.float64), g.s, g.t)
+    T = 4
+    eps = O.eps_schedule(T)
+    with P.Solver(g64, pcg_tol=1e-12, reduce_on_host=host) as ref:
+        ref.solve(T, eps)
+        x_ref = ref.get_x()
+        cut_ref = ref.cut()[1]
+    opt = B.pirmcut_default_options(pcg_tol=1e-12, reduce_on_host=host, capacity_fp32=1)
+    with P.Solver(g, opt) as s:               # host float32 array
+        s.solve(T, eps)
+        assert np.array_equal(s.get_x(), x_ref)
+        assert s.cut()[1] == cut_ref
+        # new capacities as floats
+        c2 = (g.c * np.exp(np.random.default_rng(3).normal(0, 0.01, g.c.shape[0]))).astype(np.float32)
+        rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+        key = np.minimum(rows, g.col) * g.n + np.maximum(rows, g.col)
+        _, first = np.unique(key, return_index=True)
+        inv = np.unique(key, return_inverse=True)[1]
+        c2 = c2[first][inv]                   # symmetric: both directions equal
+        s.update_weights(c2)
+        s.solve(T, eps)
+        x2 = s.get_x()
+    g2 = gen.Graph(g.n, g.row_ptr, g.col, c2.astype(np.float64), g.s, g.t)
+    with P.Solver(g2, pcg_tol=1e-12, reduce_on_host=host) as ref2:
+        ref2.solve(T, eps)
+        assert np.array_equal(ref2.get_x(), x2)
+    # device buffers
+    d = lambda a: torch.from_numpy(a).cuda()  # noqa: E731
+    h = B.pirmcut_create(g.n, d(g.row_ptr), d(g.col), d(c32), g.s, g.t, opt)
+    try:
+        B.pirmcut_solve(h, T, np.asarray(eps))
+        x = np.empty(g.n)
+        B.pirmcut_get_x(h, x)
+        assert np.array_equal(x, x_ref)
+    finally:
+        B.pirmcut_destroy(h)
