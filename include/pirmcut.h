@@ -294,8 +294,10 @@ pirmcut_status pirmcut_cut_two_level(pirmcut_ctx* ctx, uint8_t* side, double* va
  * (Section 3.1) and aims at sequences of related problems (Section 6).  With
  * PIRMCUT_MLP_PREDICT on, each IRLS step after x^(0) (with warm_start = 1)
  * starts instead from x^(l-1) + alpha * d, where d is a per-node direction
- * predicted by an MLP (6 features -> 64 -> 64 -> 1, ReLU; BF16 weights, FP32
- * arithmetic) and alpha comes from an exact line search (FP64) on the
+ * predicted by an MLP (6 features -> 64 -> 64 -> 1, ReLU; BF16 weights;
+ * inference on the tensor cores with BF16 operands -- the features enter as
+ * a BF16 head and tail, about 2^-17 relative -- and FP32 accumulation) and
+ * alpha comes from an exact line search (FP64) on the
  * quadratic energy E(v) = v^T L~ v - 2 b^T v = ||v - v*||^2_{L~} - const:
  *   alpha = d^T r / d^T L~ d,  r = b - L~ x^(l-1)   (alpha = 0 if d^T L~ d <= 0).
  * E is the error norm that CG minimises, so the learned start is never
@@ -333,7 +335,8 @@ pirmcut_status pirmcut_cut_two_level(pirmcut_ctx* ctx, uint8_t* side, double* va
  *   training.  Errors: EINVAL.
  * pirmcut_mlp_predict: the model's output d for count feature rows
  *   (float[count * 6], row-major) into float[count]; both arrays in mem_kind
- *   memory.  Errors: EINVAL (no model, sizes), ENOMEM, ECUDA.
+ *   memory.  Errors: EINVAL (no model, sizes), ENOMEM, ECUDA, ETIMEOUT (a
+ *   bounded wait on the tensor cores expired).
  * pirmcut_mlp_weights: direction 0 copies the FP32 master weights to w
  *   (host, PIRMCUT_MLP_PARAMS floats); direction 1 loads them from w and
  *   resets the optimizer state.  Errors: EINVAL (no model, NULL w), ECUDA.
@@ -357,6 +360,9 @@ typedef struct {
   double energy_change;
   double res_plain;
   double mean_alpha;
+  int tensor_timeouts; /* 1 once a bounded wait of the tensor-core network
+                          expired (its outputs past that point were not
+                          written; the line search then uses what it finds) */
 } pirmcut_mlp_info;
 pirmcut_status pirmcut_mlp_enable(pirmcut_ctx* ctx, int mode, uint64_t seed);
 pirmcut_status pirmcut_mlp_configure(pirmcut_ctx* ctx, int iters_per_step, float learning_rate);

@@ -55,7 +55,7 @@ class MlpInfo(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("used", ctypes.c_int), ("train_steps", ctypes.c_int),
                 ("loss", ctypes.c_float), ("alpha", ctypes.c_double),
                 ("energy_change", ctypes.c_double), ("res_plain", ctypes.c_double),
-                ("mean_alpha", ctypes.c_double)]
+                ("mean_alpha", ctypes.c_double), ("tensor_timeouts", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -854,6 +854,18 @@ pirmcut_status pirmcut_mlp_configure(pirmcut_ctx* h, int iters_per_step, float l
   return PIRMCUT_OK;
 }
 
+namespace {
+// ETIMEOUT when a bounded wait of the tensor-core network expired (the
+// outputs past that point are not written).
+pirmcut_status tensor_status(pirmcut_ctx* h) {
+  pirmcut::MlpState m;
+  cudaError_t e = pirmcut::mlp_get_state(h->c, &m);
+  if (e != cudaSuccess) return cuda_fail(h, e, "reading the model state");
+  if (m.tc_error) return fail(h, PIRMCUT_ETIMEOUT, "a tensor-core wait of the network expired");
+  return PIRMCUT_OK;
+}
+}  // namespace
+
 pirmcut_status pirmcut_mlp_predict(pirmcut_ctx* h, const float* features, int64_t count,
                                    float* delta, int mem_kind) {
   if (!h) return fail(nullptr, PIRMCUT_EINVAL, "null context");
@@ -869,7 +881,7 @@ pirmcut_status pirmcut_mlp_predict(pirmcut_ctx* h, const float* features, int64_
   if (mem_kind == PIRMCUT_MEM_DEVICE) {
     CK(h, pirmcut::mlp_predict_delta(c, features, count, delta), "inference");
     CK(h, cudaStreamSynchronize(c.stream), "inference");
-    return PIRMCUT_OK;
+    return tensor_status(h);
   }
   float* df = nullptr;
   float* dd = nullptr;
@@ -882,7 +894,7 @@ pirmcut_status pirmcut_mlp_predict(pirmcut_ctx* h, const float* features, int64_
   if (df) cudaFree(df);
   if (dd) cudaFree(dd);
   if (e != cudaSuccess) return cuda_fail(h, e, "inference");
-  return PIRMCUT_OK;
+  return tensor_status(h);
 }
 
 pirmcut_status pirmcut_mlp_weights(pirmcut_ctx* h, float* w, int direction) {
@@ -915,6 +927,7 @@ pirmcut_status pirmcut_mlp_stats(pirmcut_ctx* h, pirmcut_mlp_info* info) {
   info->energy_change = m.energy_change;
   info->res_plain = std::sqrt(m.res_plain);
   info->mean_alpha = m.steps ? m.sum_alpha / m.steps : 0.0;
+  info->tensor_timeouts = m.tc_error;
   return PIRMCUT_OK;
 }
 

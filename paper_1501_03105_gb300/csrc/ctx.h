@@ -86,6 +86,7 @@ struct MlpState {
   int train_steps;       // Adam steps taken
   unsigned int counter;  // last-block counter of the residual reductions
   unsigned int adam_ticket;  // last-block counter of the Adam step
+  int tc_error;          // 1 once a tensor-core wait of the network expired
 };
 
 struct MlpBuf {

@@ -17,17 +17,22 @@
 // the error norm CG minimises, so the learned start is never worse than the
 // plain warm start (alpha = 0 is always available): x^(l-1) is both the
 // fallback and the yardstick.  The reweighting point stays x^(l-1) (in xprev).
+// Inference runs on the tcgen05 tensor cores (BF16 operands, FP32
+// accumulation in tensor memory; mlp_tc.cuh), the features in FP32 on DIA
+// grids (a memory-bound pass) and FP64 on CSR rows.
 // Training runs on the trajectory the solver itself produces: after a step,
 // minibatches of nodes drawn by a counter-based hash go through hand-written
-// forward/backward kernels; each block accumulates its samples' gradients in
-// a fixed order, blocks are summed in block order, and one Adam step updates
-// the FP32 master weights and their BF16 copy.  Runs are bit-reproducible.
+// forward/backward kernels written as block-level GEMMs over each block's
+// samples; each block sums its samples' gradients in a fixed order, blocks
+// are summed in block order, and one Adam step updates the FP32 master
+// weights and their BF16 copy.  Runs are bit-reproducible.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
 
 #include "ctx.h"
+#include "mlp_tc.cuh"
 
 namespace pirmcut {
 
@@ -152,203 +157,6 @@ k_features_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __rest
   }
 }
 
-// ---------------------------------------------------------------------------
-// Inference on the tensor cores: mma.sync.m16n8k16 with BF16 operands and
-// FP32 accumulation.  A warp evaluates 32 rows at a time as two 16-row tiles:
-//   layer 1  [16 x 16] x [16 x 64]: the 16-wide K slot holds the six
-//            features split into a BF16 head and a BF16 tail (f = hi + lo to
-//            about 2^-17 relative, so that differences such as f1 - f0 keep
-//            their digits), a constant 1 for the bias b1, and zeros;
-//   layer 2  [16 x 64] x [64 x 64]: the layer-1 accumulators, after ReLU and
-//            rounding to BF16, are already laid out as the A fragments of
-//            this product (no shared-memory round trip); the accumulators
-//            start from b2;
-//   layer 3  64 -> 1 on the CUDA cores in FP32 from the layer-2
-//            accumulators (ReLU, dot with w3, a reduction over the four
-//            threads that hold a row, + b3).
-// Each thread keeps its B fragments of W1 and W2 (BF16) in registers.
-// ---------------------------------------------------------------------------
-
-// Weights of the tensor-core evaluation, staged once per block in shared
-// memory in the order the fragments are read: the layer-2 B fragments as
-// [output tile j][K chunk c][lane] pairs of 32-bit words (one 8-byte load per
-// fragment, consecutive lanes on consecutive words: no bank conflicts).
-struct MlpSmem {
-  uint2 w2[8][4][32];
-  uint32_t w1[8][32][2];  // layer 1, [output tile][lane]: K pairs (2t, 2t+1), (8+2t, 9+2t)
-  uint32_t b2[8][4];      // [tile j][t]: (b2[8j+2t], b2[8j+2t+1]) as BF16 pairs
-  uint32_t w3[8][4];
-  float b3;
-};
-
-struct MlpFrags {
-  uint32_t w1[8][2];     // layer 1, per 8-unit output tile
-  uint32_t b2[8];
-  uint32_t w3[8];
-  float b3;
-  const uint2* w2;       // this lane's layer-2 fragments in shared memory, stride 32
-};
-
-__device__ __forceinline__ uint32_t bf16_bits(const __nv_bfloat16* p) {
-  return uint32_t(__bfloat16_as_ushort(*p));
-}
-// BF16 pair (p[0] in the low half = the lower K index, p[1] in the high half)
-__device__ __forceinline__ uint32_t bf16_pair(const __nv_bfloat16* p) {
-  return bf16_bits(p) | (bf16_bits(p + 1) << 16);
-}
-__device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
-__device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
-
-// round two FP32 values to BF16 (nearest even) and pack them: lo in the low half
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  uint32_t r;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-  return r;
-}
-// the same after ReLU
-__device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
-  uint32_t r;
-  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-  return r;
-}
-
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                               uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// The block stages the weights (every thread of the block takes part; ends
-// with a barrier), then each thread takes its small fragments into registers.
-__device__ __forceinline__ void load_frags(const __nv_bfloat16* __restrict__ w16, MlpSmem& S,
-                                           MlpFrags& F) {
-  for (int idx = threadIdx.x; idx < 8 * 4 * 32; idx += blockDim.x) {
-    const int j = idx >> 7, c = (idx >> 5) & 3, ln = idx & 31;
-    const int u = 8 * j + (ln >> 2), t = ln & 3;
-    S.w2[j][c][ln] = make_uint2(bf16_pair(w16 + OFF_W2 + u * H + 16 * c + 2 * t),
-                                bf16_pair(w16 + OFF_W2 + u * H + 16 * c + 8 + 2 * t));
-  }
-  for (int idx = threadIdx.x; idx < 8 * 32; idx += blockDim.x) {
-    const int j = idx >> 5, ln = idx & 31;
-    const int u = 8 * j + (ln >> 2), t = ln & 3;
-    const uint32_t head = t < 3 ? bf16_pair(w16 + OFF_W1 + u * NF + 2 * t)  // (W1[u][2t], W1[u][2t+1])
-                                : bf16_bits(w16 + OFF_B1 + u);              // (b1[u], 0)
-    S.w1[j][ln][0] = head;
-    S.w1[j][ln][1] = t < 3 ? head : 0u;  // the tails of the features meet the same weights
-  }
-  if (threadIdx.x < 32) {
-    const int j = threadIdx.x >> 2, t = threadIdx.x & 3;
-    S.b2[j][t] = bf16_pair(w16 + OFF_B2 + 8 * j + 2 * t);
-    S.w3[j][t] = bf16_pair(w16 + OFF_W3 + 8 * j + 2 * t);
-  }
-  if (threadIdx.x == 0) S.b3 = bf16_lo(bf16_bits(w16 + OFF_B3));
-  __syncthreads();
-  const int lane = threadIdx.x & 31, t = lane & 3;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    F.w1[j][0] = S.w1[j][lane][0];
-    F.w1[j][1] = S.w1[j][lane][1];
-    F.b2[j] = S.b2[j][t];
-    F.w3[j] = S.w3[j][t];
-  }
-  F.b3 = S.b3;
-  F.w2 = &S.w2[0][0][lane];
-}
-
-constexpr int kStage = 9;  // words per row of a warp's A-fragment staging area (8 + 1 pad)
-
-// The network on 32 rows: lane L supplies the features f of row L (any
-// values when the row does not exist) and gets that row's output back.
-// stage: 32 * kStage words of shared memory owned by this warp.
-__device__ __forceinline__ float mlp_warp32(const MlpFrags& W, const float (&f)[NF],
-                                            uint32_t* stage) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  // this row's K slot: words 0-3 = (f0,f1) (f2,f3) (f4,f5) (1,0) rounded to
-  // BF16, words 4-6 = the tails f - BF16(f), word 7 = 0
-  uint32_t* my = stage + lane * kStage;
-  const uint32_t h0 = pack_bf16(f[0], f[1]), h1 = pack_bf16(f[2], f[3]), h2 = pack_bf16(f[4], f[5]);
-  my[0] = h0;
-  my[1] = h1;
-  my[2] = h2;
-  my[3] = pack_bf16(1.0f, 0.0f);
-  my[4] = pack_bf16(f[0] - bf16_lo(h0), f[1] - bf16_hi(h0));
-  my[5] = pack_bf16(f[2] - bf16_lo(h1), f[3] - bf16_hi(h1));
-  my[6] = pack_bf16(f[4] - bf16_lo(h2), f[5] - bf16_hi(h2));
-  my[7] = 0u;
-  __syncwarp();
-  // layer 1 of both 16-row halves (bias through the constant-1 column),
-  // ReLU, BF16: the A fragments of layer 2 (K chunk c = hidden units
-  // 16c .. 16c + 15)
-  uint32_t a2[2][4][4];
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int r0 = 16 * h + g, r1 = r0 + 8;
-    uint32_t a[4];
-    a[0] = stage[r0 * kStage + t];
-    a[1] = stage[r1 * kStage + t];
-    a[2] = stage[r0 * kStage + 4 + t];
-    a[3] = stage[r1 * kStage + 4 + t];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
-      mma_bf16_16816(d0, a, W.w1[2 * c][0], W.w1[2 * c][1]);
-      mma_bf16_16816(d1, a, W.w1[2 * c + 1][0], W.w1[2 * c + 1][1]);
-      a2[h][c][0] = pack_relu_bf16(d0[0], d0[1]);
-      a2[h][c][1] = pack_relu_bf16(d0[2], d0[3]);
-      a2[h][c][2] = pack_relu_bf16(d1[0], d1[1]);
-      a2[h][c][3] = pack_relu_bf16(d1[2], d1[3]);
-    }
-  }
-  // layer 2 from b2 for both halves (each W2 fragment loaded once, two
-  // independent accumulation chains), then ReLU and the dot with w3 (FP32)
-  float pg[2] = {0.f, 0.f}, pg8[2] = {0.f, 0.f};
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const float bl = bf16_lo(W.b2[j]), bh = bf16_hi(W.b2[j]);
-    float d[2][4] = {{bl, bh, bl, bh}, {bl, bh, bl, bh}};
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const uint2 b = W.w2[(j * 4 + c) * 32];
-      mma_bf16_16816(d[0], a2[0][c], b.x, b.y);
-      mma_bf16_16816(d[1], a2[1][c], b.x, b.y);
-    }
-    const float wl = bf16_lo(W.w3[j]), wh = bf16_hi(W.w3[j]);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      pg[h] = fmaf(fmaxf(d[h][0], 0.f), wl, pg[h]);
-      pg[h] = fmaf(fmaxf(d[h][1], 0.f), wh, pg[h]);
-      pg8[h] = fmaf(fmaxf(d[h][2], 0.f), wl, pg8[h]);
-      pg8[h] = fmaf(fmaxf(d[h][3], 0.f), wh, pg8[h]);
-    }
-  }
-  float out_g[2], out_g8[2];
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    float u = pg[h], v = pg8[h];
-    u += __shfl_xor_sync(0xffffffffu, u, 1);
-    u += __shfl_xor_sync(0xffffffffu, u, 2);
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    out_g[h] = u + W.b3;
-    out_g8[h] = v + W.b3;
-  }
-  // back to one row per lane through the staging area
-  __syncwarp();
-  float* so = reinterpret_cast<float*>(stage);
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    if (t == 0) so[16 * h + g] = out_g[h];
-    if (t == 1) so[16 * h + g + 8] = out_g8[h];
-  }
-  __syncwarp();
-  const float r = so[lane];
-  __syncwarp();
-  return r;
-}
-
 // FP32 value of a double by truncation of its significand, built with
 // integer instructions (GB300 runs FP64 <-> FP32 conversions on its narrow
 // FP64 pipe); relative error below 2^-23, magnitudes below the FP32 normal
@@ -444,42 +252,29 @@ __device__ __forceinline__ void features_dia32(const DiaDesc& d, const double* _
   f[5] = log_eps8;
 }
 
-// Learned direction on a DIA grid: features (kept in feat when with_feat)
-// and, with kPredict, the network's output into dir (FP64).  A warp takes 32
-// consecutive rows at a time.
-template <int K, bool kPredict>
-__global__ void __launch_bounds__(128, 4)
-k_mlp_fused_dia(DiaDesc d, const double* __restrict__ g, const double* __restrict__ gprev,
-                const double* __restrict__ cs, const double* __restrict__ ct,
-                const double* __restrict__ x, const double* __restrict__ eps_list,
-                const StepCounters* __restrict__ C, int form,
-                const __nv_bfloat16* __restrict__ w16, float* __restrict__ feat, int with_feat,
-                double* __restrict__ dir) {
-  __shared__ uint32_t stage_all[4][32 * kStage];
-  __shared__ MlpSmem wsm;
+// ---- Inference on the tcgen05 tensor cores (mlp_tc.cuh: BF16 operands,
+// FP32 accumulation in tensor memory): one CTA of 128 threads walks 128-row
+// tiles, one thread per row.  Four CTAs share an SM (128 TMEM columns each).
+// A wait that expires sets M->tc_error.
+
+// The features of a DIA grid in FP32 (features_dia32), one row per thread:
+// a memory-bound pass; the network then reads them (k_mlp_predict_t5).
+template <int K>
+__global__ void __launch_bounds__(kThreads)
+k_features_dia32(DiaDesc d, const double* __restrict__ g, const double* __restrict__ gprev,
+                 const double* __restrict__ cs, const double* __restrict__ ct,
+                 const double* __restrict__ x, const double* __restrict__ eps_list,
+                 const StepCounters* __restrict__ C, int form, float* __restrict__ feat) {
   const int64_t nt = d.nt;
   const double eps = eps_list[C->eps_idx];
   const float eps2f = float(eps) * float(eps);
   const float log_eps8 = logf(float(eps)) * 0.125f;
-  MlpFrags W;
-  if (kPredict) load_frags(w16, wsm, W);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t* stage = stage_all[warp];
-  const int64_t tiles = (nt + 31) / 32;
-  for (int64_t tile = int64_t(blockIdx.x) * 4 + warp; tile < tiles; tile += int64_t(gridDim.x) * 4) {
-    const int64_t i = tile * 32 + lane;
-    float f[NF] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (i < nt) {
-      features_dia32<K>(d, g, gprev, cs, ct, x, eps2f, log_eps8, form, i, f);
-      if (with_feat) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nt;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    float f[NF];
+    features_dia32<K>(d, g, gprev, cs, ct, x, eps2f, log_eps8, form, i, f);
 #pragma unroll
-        for (int k = 0; k < NF; ++k) feat[i * NF + k] = f[k];
-      }
-    }
-    if (kPredict) {
-      const float out = mlp_warp32(W, f, stage);
-      if (i < nt) dir[i] = double(out);
-    }
+    for (int k = 0; k < NF; ++k) feat[i * NF + k] = f[k];
   }
 }
 
@@ -487,38 +282,69 @@ k_mlp_fused_dia(DiaDesc d, const double* __restrict__ g, const double* __restric
 // point): delta -> dir (FP64) or out32 (FP32).
 template <bool kF32>
 __global__ void __launch_bounds__(128, 4)
-k_mlp_predict_tc(int64_t nt, const float* __restrict__ f, const __nv_bfloat16* __restrict__ w16,
-                 double* __restrict__ dir, float* __restrict__ out32) {
-  __shared__ uint32_t stage_all[4][32 * kStage];
-  __shared__ MlpSmem wsm;
-  MlpFrags W;
-  load_frags(w16, wsm, W);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t* stage = stage_all[warp];
-  const int64_t tiles = (nt + 31) / 32;
-  for (int64_t tile = int64_t(blockIdx.x) * 4 + warp; tile < tiles; tile += int64_t(gridDim.x) * 4) {
-    const int64_t i = tile * 32 + lane;
-    float in[NF] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (i < nt) {
+k_mlp_predict_t5(int64_t nt, const float* __restrict__ f, const __nv_bfloat16* __restrict__ w16,
+                 double* __restrict__ dir, float* __restrict__ out32, MlpState* M) {
+  __shared__ tc5::Smem S;
+  tc5::setup(S, w16);
+  uint32_t phase = 0;
+  bool ok = true;
+  const int64_t tiles = (nt + tc5::kRows - 1) / tc5::kRows;
+  // the next tile's features are loaded while this one runs
+  auto load = [&](int64_t t, float (&v)[NF]) {
+    const int64_t i = t * tc5::kRows + threadIdx.x;
 #pragma unroll
-      for (int k = 0; k < NF; ++k) in[k] = f[i * NF + k];
+    for (int k = 0; k < NF; ++k) v[k] = 0.f;
+    if (t < tiles && i < nt) {
+#pragma unroll
+      for (int k = 0; k < NF; ++k) v[k] = __ldcs(f + i * NF + k);
     }
-    const float out = mlp_warp32(W, in, stage);
-    if (i < nt) {
+  };
+  float nxt[NF];
+  load(blockIdx.x, nxt);
+  for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+    const int64_t i = t * tc5::kRows + threadIdx.x;
+    float in[NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) in[k] = nxt[k];
+    load(t + gridDim.x, nxt);
+    float out = 0.f;
+    ok = tc5::tile(S, in, phase, out);
+    if (ok && i < nt) {
       if (kF32) out32[i] = out;
       else dir[i] = double(out);
     }
   }
+  if (!ok) {
+    tc5::wait_phase(tc5::smem_u32(&S.mbar), phase);
+    if (threadIdx.x == 0) atomicExch(&M->tc_error, 1);
+  }
+  tc5::teardown(S);
 }
 
-// Grid of the warp-tile kernels: 4 warps of 32 rows per block, four blocks
-// per SM (at most 128 registers a thread), every warp walking several tiles.
-inline int mlp_tile_grid(int64_t rows) {
-  const int64_t tiles = (rows + 31) / 32;
-  int64_t b = (tiles + 3) / 4;
-  if (b > 152 * 4) b = 152 * 4;
-  return int(b < 1 ? 1 : b);
+// Unused dynamic shared memory added to each launch of the tcgen05 kernels,
+// up to the 48 KB a block may use without opting in: at most four such
+// blocks fit on an SM (228 KB, 1 KB reserved per block), 4 x 128 = the 512
+// TMEM columns of an SM (a fifth CTA would wait in tcgen05.alloc).
+constexpr size_t kT5Pad = 48 * 1024 - sizeof(tc5::Smem);
+static_assert(sizeof(tc5::Smem) <= 48 * 1024 && 5 * (48 + 1) * 1024 > 228 * 1024,
+              "four CTAs per SM");
+
+// CTAs of the tcgen05 kernels: four per SM, never more than there are tiles.
+inline int mlp_t5_grid(int64_t rows) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, v = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      sms = v;
+    else
+      sms = 152;
+  }
+  const int64_t tiles = (rows + tc5::kRows - 1) / tc5::kRows;
+  const int64_t cap = int64_t(sms) * 4;
+  return int(tiles < 1 ? 1 : (tiles < cap ? tiles : cap));
 }
+
 
 // Line search along the learned direction d from x = x^(l-1): with
 // r = b - L~ x, the last block forms alpha = (d, r) / (d, L~ d) (0 when the
@@ -1004,24 +830,17 @@ int enqueue_mlp_post(Ctx& c, cudaStream_t st) {
   const bool predict = (c.mlp_mode & PIRMCUT_MLP_PREDICT) != 0;
   const int keep_feat = (c.mlp_mode & PIRMCUT_MLP_TRAIN) ? 1 : 0;
   if (c.format == PIRMCUT_FORMAT_DIA) {
-    const int tg = mlp_tile_grid(c.nt);
-    if (predict) {
-      PIRMCUT_DISPATCH_K(c.K, (k_mlp_fused_dia<KK, true><<<tg, 128, 0, st>>>(
-                                  c.dd, c.gdia, b.gprev, c.cs, c.ct, c.x, c.eps_list, c.C, form,
-                                  b.w16, b.feat, keep_feat, b.dir)));
-    } else {
-      PIRMCUT_DISPATCH_K(c.K, (k_mlp_fused_dia<KK, false><<<tg, 128, 0, st>>>(
-                                  c.dd, c.gdia, b.gprev, c.cs, c.ct, c.x, c.eps_list, c.C, form,
-                                  b.w16, b.feat, 1, b.dir)));
-      return 1;
-    }
+    PIRMCUT_DISPATCH_K(c.K, (k_features_dia32<KK><<<grid, kThreads, 0, st>>>(
+                                c.dd, c.gdia, b.gprev, c.cs, c.ct, c.x, c.eps_list, c.C, form,
+                                b.feat)));
   } else {
     k_features_csr<<<grid + c.n_heavy, kThreads, 0, st>>>(c.nt, c.rp, c.col, c.gval, b.gprev, c.cs,
                                                           c.ct, c.x, c.eps_list, c.C, form, b.feat,
                                                           c.heavy_deg, c.heavy, grid);
-    if (!predict) return 1;
-    k_mlp_predict_tc<false><<<mlp_tile_grid(c.nt), 128, 0, st>>>(c.nt, b.feat, b.w16, b.dir, nullptr);
   }
+  if (!predict) return 1;
+  k_mlp_predict_t5<false><<<mlp_t5_grid(c.nt), 128, kT5Pad, st>>>(c.nt, b.feat, b.w16, b.dir,
+                                                                   nullptr, b.state);
   if (c.format == PIRMCUT_FORMAT_DIA) {
     PIRMCUT_DISPATCH_K(c.K, (k_linesearch_dia<KK><<<grid, kThreads, 0, st>>>(
                                 c.dd, c.gdia, c.cs, c.ct, c.x, b.dir, c.eps_list, c.C, form,
@@ -1033,7 +852,7 @@ int enqueue_mlp_post(Ctx& c, cudaStream_t st) {
                                                             c.heavy, grid);
   }
   k_mlp_commit<<<grid, kThreads, 0, st>>>(c.nt, b.state, b.dir, c.x);
-  return c.format == PIRMCUT_FORMAT_DIA ? 3 : 4;
+  return 4;
 }
 
 // After the solve of a step, with training on: iters_per_step Adam steps on
@@ -1052,8 +871,8 @@ int enqueue_mlp_train(Ctx& c, cudaStream_t st) {
 
 // Inference on caller-supplied features (count x kMlpFeatures, device) -> delta (device).
 cudaError_t mlp_predict_delta(Ctx& c, const float* feat, int64_t count, float* delta) {
-  k_mlp_predict_tc<true><<<mlp_tile_grid(count), 128, 0, c.stream>>>(count, feat, c.mlp.w16, nullptr,
-                                                                     delta);
+  k_mlp_predict_t5<true><<<mlp_t5_grid(count), 128, kT5Pad, c.stream>>>(count, feat, c.mlp.w16, nullptr,
+                                                                     delta, c.mlp.state);
   c.launches += 1;
   return cudaGetLastError();
 }
