@@ -370,6 +370,13 @@ pirmcut_status pirmcut_mlp_predict(pirmcut_ctx* ctx, const float* features, int6
                                    float* delta, int mem_kind);
 pirmcut_status pirmcut_mlp_weights(pirmcut_ctx* ctx, float* w, int direction);
 pirmcut_status pirmcut_mlp_stats(pirmcut_ctx* ctx, pirmcut_mlp_info* info);
+/* Diagnostics for roofline reports: reps launches of the inference kernel of
+ * pirmcut_mlp_predict on count feature rows (device memory, as there),
+ * back to back between CUDA events on the context's stream after one
+ * untimed launch; avg_ms receives the mean time per launch.  Errors:
+ * EINVAL, ECUDA, ETIMEOUT. */
+pirmcut_status pirmcut_mlp_time_predict(pirmcut_ctx* ctx, const float* features, int64_t count,
+                                        float* delta, int reps, double* avg_ms);
 pirmcut_status pirmcut_mlp_features(pirmcut_ctx* ctx, float* f);
 
 /*

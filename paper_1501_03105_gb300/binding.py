@@ -138,6 +138,9 @@ def lib() -> ctypes.CDLL:
     L.pirmcut_mlp_weights.restype = ctypes.c_int
     L.pirmcut_mlp_stats.argtypes = [_P, ctypes.POINTER(MlpInfo)]
     L.pirmcut_mlp_stats.restype = ctypes.c_int
+    L.pirmcut_mlp_time_predict.argtypes = [_P, _P, ctypes.c_int64, _P, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_double)]
+    L.pirmcut_mlp_time_predict.restype = ctypes.c_int
     L.pirmcut_mlp_features.argtypes = [_P, _P]
     L.pirmcut_mlp_features.restype = ctypes.c_int
     L.pirmcut_spmv_timing.argtypes = [_P, ctypes.POINTER(dbl), ctypes.POINTER(i64), ctypes.c_int]
@@ -339,6 +342,19 @@ def pirmcut_mlp_predict(h, features, delta=None):
         raise TypeError("features and delta must be in the same kind of memory")
     _check(h, lib().pirmcut_mlp_predict(h, pf, int(f.shape[0]), pd, kind))
     return delta
+
+
+def pirmcut_mlp_time_predict(h, features, delta, reps=20):
+    """Mean device time (ms) of one launch of the inference kernel on the
+    device feature rows (reps back-to-back launches between CUDA events)."""
+    pf, kf, a1 = _ptr(features, np.float32)
+    pd, kd, a2 = _ptr(delta, np.float32)
+    if kf != MEM_DEVICE or kd != MEM_DEVICE:
+        raise ValueError("features and delta must be device tensors")
+    ms = ctypes.c_double()
+    _check(h, lib().pirmcut_mlp_time_predict(h, pf, int(features.shape[0]), pd, int(reps),
+                                             ctypes.byref(ms)))
+    return ms.value
 
 
 def pirmcut_mlp_weights(h, w=None):
@@ -560,6 +576,9 @@ class Solver:
 
     def mlp_predict(self, features, delta=None):
         return pirmcut_mlp_predict(self.h, features, delta)
+
+    def mlp_time_predict(self, features, delta, reps=20):
+        return pirmcut_mlp_time_predict(self.h, features, delta, reps)
 
     def mlp_weights(self, w=None):
         return pirmcut_mlp_weights(self.h, w)

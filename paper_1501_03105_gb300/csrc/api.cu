@@ -897,6 +897,17 @@ pirmcut_status pirmcut_mlp_predict(pirmcut_ctx* h, const float* features, int64_
   return tensor_status(h);
 }
 
+pirmcut_status pirmcut_mlp_time_predict(pirmcut_ctx* h, const float* features, int64_t count,
+                                        float* delta, int reps, double* avg_ms) {
+  if (!h) return fail(nullptr, PIRMCUT_EINVAL, "null context");
+  Ctx& c = h->c;
+  if (!c.mlp.master) return fail(h, PIRMCUT_EINVAL, "no model: call pirmcut_mlp_enable first");
+  if (count < 1 || reps < 1 || !features || !delta || !avg_ms)
+    return fail(h, PIRMCUT_EINVAL, "count and reps must be >= 1 and every pointer non-NULL");
+  CK(h, pirmcut::mlp_time_predict(c, features, count, delta, reps, avg_ms), "timed inference");
+  return tensor_status(h);
+}
+
 pirmcut_status pirmcut_mlp_weights(pirmcut_ctx* h, float* w, int direction) {
   if (!h) return fail(nullptr, PIRMCUT_EINVAL, "null context");
   Ctx& c = h->c;

@@ -241,6 +241,8 @@ cudaError_t mlp_set_weights(Ctx& c, const float* host);
 cudaError_t mlp_get_state(Ctx& c, MlpState* host);
 cudaError_t mlp_get_features(Ctx& c, float* host);
 cudaError_t mlp_predict_delta(Ctx& c, const float* feat, int64_t count, float* delta);
+cudaError_t mlp_time_predict(Ctx& c, const float* feat, int64_t count, float* delta, int reps,
+                             double* avg_ms);
 int enqueue_mlp_pre(Ctx& c, cudaStream_t st);    // before the reweighting
 int enqueue_mlp_post(Ctx& c, cudaStream_t st);   // after it: features, candidate, choice
 int enqueue_mlp_train(Ctx& c, cudaStream_t st);  // after the solve

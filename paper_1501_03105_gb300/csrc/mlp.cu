@@ -254,7 +254,7 @@ __device__ __forceinline__ void features_dia32(const DiaDesc& d, const double* _
 
 // ---- Inference on the tcgen05 tensor cores (mlp_tc.cuh: BF16 operands,
 // FP32 accumulation in tensor memory): one CTA of 128 threads walks 128-row
-// tiles, one thread per row.  Four CTAs share an SM (128 TMEM columns each).
+// tiles, one thread per row.  Five CTAs share an SM (64 TMEM columns each).
 // A wait that expires sets M->tc_error.
 
 // The features of a DIA grid in FP32 (features_dia32), one row per thread:
@@ -281,7 +281,7 @@ k_features_dia32(DiaDesc d, const double* __restrict__ g, const double* __restri
 // The network on stored feature rows (CSR problems, and the inference entry
 // point): delta -> dir (FP64) or out32 (FP32).
 template <bool kF32>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, 5)
 k_mlp_predict_t5(int64_t nt, const float* __restrict__ f, const __nv_bfloat16* __restrict__ w16,
                  double* __restrict__ dir, float* __restrict__ out32, MlpState* M) {
   __shared__ tc5::Smem S;
@@ -321,15 +321,13 @@ k_mlp_predict_t5(int64_t nt, const float* __restrict__ f, const __nv_bfloat16* _
   tc5::teardown(S);
 }
 
-// Unused dynamic shared memory added to each launch of the tcgen05 kernels,
-// up to the 48 KB a block may use without opting in: at most four such
-// blocks fit on an SM (228 KB, 1 KB reserved per block), 4 x 128 = the 512
-// TMEM columns of an SM (a fifth CTA would wait in tcgen05.alloc).
-constexpr size_t kT5Pad = 48 * 1024 - sizeof(tc5::Smem);
-static_assert(sizeof(tc5::Smem) <= 48 * 1024 && 5 * (48 + 1) * 1024 > 228 * 1024,
-              "four CTAs per SM");
+// Resident CTAs per SM of the tcgen05 kernels: five (registers bound them;
+// 5 x 64 TMEM columns of the SM's 512; shared memory would allow six).
+constexpr int kT5PerSm = 5;
+static_assert(kT5PerSm * tc5::kTmemCols <= 512, "tensor memory of an SM");
+constexpr size_t kT5Pad = 0;
 
-// CTAs of the tcgen05 kernels: four per SM, never more than there are tiles.
+// CTAs of the tcgen05 kernels: kT5PerSm per SM, never more than there are tiles.
 inline int mlp_t5_grid(int64_t rows) {
   static int sms = 0;
   if (sms == 0) {
@@ -341,7 +339,7 @@ inline int mlp_t5_grid(int64_t rows) {
       sms = 152;
   }
   const int64_t tiles = (rows + tc5::kRows - 1) / tc5::kRows;
-  const int64_t cap = int64_t(sms) * 4;
+  const int64_t cap = int64_t(sms) * kT5PerSm;
   return int(tiles < 1 ? 1 : (tiles < cap ? tiles : cap));
 }
 
@@ -867,6 +865,36 @@ int enqueue_mlp_train(Ctx& c, cudaStream_t st) {
                                                      b.m, b.v, b.state, b.lr);
   }
   return 2 * b.iters_per_step;
+}
+
+// reps launches of the inference kernel back to back between CUDA events on
+// the context's stream; mean milliseconds per launch.
+cudaError_t mlp_time_predict(Ctx& c, const float* feat, int64_t count, float* delta, int reps,
+                             double* avg_ms) {
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return e;
+  }
+  k_mlp_predict_t5<true><<<mlp_t5_grid(count), 128, kT5Pad, c.stream>>>(count, feat, c.mlp.w16,
+                                                                         nullptr, delta, c.mlp.state);
+  e = cudaEventRecord(e0, c.stream);
+  for (int k = 0; k < reps && e == cudaSuccess; ++k) {
+    k_mlp_predict_t5<true><<<mlp_t5_grid(count), 128, kT5Pad, c.stream>>>(
+        count, feat, c.mlp.w16, nullptr, delta, c.mlp.state);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, c.stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  *avg_ms = reps > 0 ? double(ms) / reps : 0.0;
+  c.launches += reps + 1;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return e;
 }
 
 // Inference on caller-supplied features (count x kMlpFeatures, device) -> delta (device).

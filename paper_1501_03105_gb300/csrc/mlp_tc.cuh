@@ -8,7 +8,9 @@
 //            feature enters with about 2^-17 relative precision and
 //            differences such as f1 - f0 keep their digits;
 //   layer 2  D2[128 x 64] = A2[128 x 80] B2^T: ReLU(D1) rounded to BF16
-//            (K 0-63), a constant 1 that meets b2 (K 64), zeros;
+//            (K 0-63), a constant 1 that meets b2 (K 64), zeros; D2 takes the
+//            tensor-memory columns of D1, which every thread has read out
+//            before the barrier that precedes the MMA;
 //   layer 3  out = b3 + sum_j w3[j] ReLU(D2[:, j]) in FP32 on the CUDA cores.
 //
 // Operands live in shared memory in the K-major layout without swizzling
@@ -30,7 +32,7 @@ constexpr int kRows = 128;        // rows of a tile: the MMA's M, TMEM lanes
 constexpr int kLBO = 128;         // bytes between core matrices along K
 constexpr int kSboA1 = 2 * kLBO;  // K = 16: two core matrices per 8-row group
 constexpr int kSboA2 = 10 * kLBO; // K = 80
-constexpr int kTmemCols = 128;    // D1 in columns 0-63, D2 in 64-127
+constexpr int kTmemCols = 64;     // D1, then D2 in the same columns (D1 is read out first)
 constexpr uint32_t kMaxPolls = 1u << 22;  // bound on the polls of one mbarrier wait
 
 struct __align__(1024) Smem {
@@ -139,7 +141,10 @@ __device__ __forceinline__ void st16(uint8_t* base, uint32_t off, uint32_t a, ui
 __device__ __forceinline__ uint32_t bf(const __nv_bfloat16* p) {
   return uint32_t(__bfloat16_as_ushort(*p));
 }
-__device__ __forceinline__ uint32_t bf2(const __nv_bfloat16* p) { return bf(p) | (bf(p + 1) << 16); }
+// two adjacent BF16 values (the first at an even index, so 4-byte aligned)
+__device__ __forceinline__ uint32_t bf2(const __nv_bfloat16* p) {
+  return __ldg(reinterpret_cast<const unsigned int*>(p));
+}
 
 // two FP32 values rounded to BF16 and packed, lo in the low half
 __device__ __forceinline__ uint32_t pk(float lo, float hi) {
@@ -171,17 +176,12 @@ __device__ __forceinline__ void setup(Smem& S, const __nv_bfloat16* __restrict__
   }
   for (int idx = tid; idx < 64 * 10; idx += blockDim.x) {  // B2: 64 units x 10 K chunks
     const int n = idx / 10, kc = idx % 10;
-    uint32_t q[4] = {0u, 0u, 0u, 0u};
-    if (kc < 8) {
-      const __nv_bfloat16* w = w16 + kW2 + n * 64 + kc * 8;
-      q[0] = bf2(w);
-      q[1] = bf2(w + 2);
-      q[2] = bf2(w + 4);
-      q[3] = bf2(w + 6);
-    } else if (kc == 8) {
-      q[0] = bf(w16 + kB2 + n);  // (b2[n], 0)
-    }
-    st16(S.b2, cm_off(n, kc, kSboA2), q[0], q[1], q[2], q[3]);
+    uint4 q = make_uint4(0u, 0u, 0u, 0u);
+    if (kc < 8)  // eight weights W2[n][8kc ..]: 16 bytes at a 16-byte boundary
+      q = __ldg(reinterpret_cast<const uint4*>(w16 + kW2 + n * 64 + kc * 8));
+    else if (kc == 8)
+      q.x = bf(w16 + kB2 + n);  // (b2[n], 0)
+    st16(S.b2, cm_off(n, kc, kSboA2), q.x, q.y, q.z, q.w);
   }
   for (int idx = tid; idx < kRows * 2; idx += blockDim.x) {  // A2 K chunks 8 (1, 0 ...), 9 (0)
     const int r = idx >> 1, kc = 8 + (idx & 1);
@@ -264,7 +264,7 @@ __device__ __forceinline__ bool tile(Smem& S, const float (&f)[6], uint32_t& pha
     const uint32_t a2 = smem_u32(S.a2), b2 = smem_u32(S.b2);
 #pragma unroll
     for (int j = 0; j < 5; ++j)  // K chunks of 16: 64 hidden units, then b2
-      mma(tbase + 64u, sdesc(a2 + 256u * j, kSboA2), sdesc(b2 + 256u * j, kSboA2), j > 0 ? 1u : 0u);
+      mma(tbase, sdesc(a2 + 256u * j, kSboA2), sdesc(b2 + 256u * j, kSboA2), j > 0 ? 1u : 0u);
     commit(mbar);
   }
   ok = wait_phase(mbar, phase);
@@ -276,7 +276,7 @@ __device__ __forceinline__ bool tile(Smem& S, const float (&f)[6], uint32_t& pha
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     uint32_t v[32];
-    ld32(lane_addr + 64u + 32u * h, v);
+    ld32(lane_addr + 32u * h, v);
     ld_wait();
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
