@@ -152,6 +152,21 @@ __device__ __forceinline__ double conductance(double c, double d, double eps2, i
   return c * rsqrt(fma(d, d, eps2));
 }
 
+// FP32 value of a double by truncation of its significand, built with
+// integer instructions (GB300 runs FP64 <-> FP32 conversions on its narrow
+// FP64 pipe); relative error below 2^-23, magnitudes below the FP32 normal
+// range give a signed zero, above it (and NaN) an infinity.
+__device__ __forceinline__ float f32_trunc(double v) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  const unsigned hi = unsigned(b >> 32), lo = unsigned(b);
+  const int e = int((hi >> 20) & 0x7FFu) - 896;
+  const unsigned m = __funnelshift_r(lo, hi, 29) & 0x7FFFFFu;
+  const unsigned sgn = hi & 0x80000000u;
+  if (e <= 0) return __uint_as_float(sgn);
+  if (e >= 255) return __uint_as_float(sgn | 0x7f800000u);
+  return __uint_as_float(sgn | (unsigned(e) << 23) | m);
+}
+
 // Compile-time dispatch of the DIA width K (1..8) and the CSR group size G.
 #define PIRMCUT_DISPATCH_K(KVAR, CALL) \
   switch (KVAR) {                      \

@@ -310,7 +310,8 @@ k_massemble_csr(int64_t nt, const int64_t* __restrict__ rp, const double* __rest
   massemble_finish(a, bb);
 }
 
-// scaled conductances g_uv d_u^-1/2 d_v^-1/2, rounded once to FP32
+// scaled conductances g_uv d_u^-1/2 d_v^-1/2 in FP32 (g truncated to FP32
+// with integer instructions; the scaled system only shapes the inner solve)
 template <int K>
 __global__ void __launch_bounds__(kThreads)
 k_mscale_dia(DiaDesc d, const double* __restrict__ g, const float* __restrict__ s32,
@@ -321,7 +322,7 @@ k_mscale_dia(DiaDesc d, const double* __restrict__ g, const float* __restrict__ 
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int64_t j = i + d.off[k];
-      g32[k * nt + i] = j < nt ? float(g[k * nt + i]) * si * s32[j] : 0.0f;
+      g32[k * nt + i] = j < nt ? f32_trunc(g[k * nt + i]) * si * s32[j] : 0.0f;
     }
   }
 }
@@ -337,7 +338,7 @@ k_mscale_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restri
     const int64_t i = heavy[blockIdx.x - light_blocks];
     const float si = s32[i];
     for (int64_t e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x)
-      g32[e] = float(g[e]) * (si * s32[col[e]]);
+      g32[e] = f32_trunc(g[e]) * (si * s32[col[e]]);
     return;
   }
   const int lane = threadIdx.x % G;
@@ -345,7 +346,7 @@ k_mscale_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restri
   for (int64_t i = gtid() / G; i < nt; i += ng) {
     if (rp[i + 1] - rp[i] > heavy_deg) continue;  // the group agrees: same row
     const float si = s32[i];
-    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) g32[e] = float(g[e]) * (si * s32[col[e]]);
+    for (int64_t e = rp[i] + lane; e < rp[i + 1]; e += G) g32[e] = f32_trunc(g[e]) * (si * s32[col[e]]);
   }
 }
 
@@ -370,10 +371,11 @@ struct Resid {
 
 // r = b - L~x in FP64; the scaled FP32 residual D^-1/2 r starts the inner CG.
 // ||r||^2 (for the FP64 stopping test) and ||D^-1/2 r||^2 are accumulated from
-// FP32-rounded values in float-float: relative error ~1e-7 in norms used only
-// for stopping decisions.
+// the FP32 values (truncated from FP64 with integer instructions) in
+// float-float: relative error below 3e-7 in norms used only for stopping
+// decisions.
 __device__ __forceinline__ void resid_row(const Resid& a, int64_t i, double ax, FF& rr, FF& ss) {
-  const float r = float(a.b64[i] - ax);
+  const float r = f32_trunc(a.b64[i] - ax);  // within 2^-23: an inner right-hand side
   const float rs = a.s32[i] * r;
   a.r32[i] = rs;
   a.p32[i] = rs;

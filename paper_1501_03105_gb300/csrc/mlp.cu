@@ -157,20 +157,6 @@ k_features_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __rest
   }
 }
 
-// FP32 value of a double by truncation of its significand, built with
-// integer instructions (GB300 runs FP64 <-> FP32 conversions on its narrow
-// FP64 pipe); relative error below 2^-23, magnitudes below the FP32 normal
-// range give a signed zero, above it an infinity.
-__device__ __forceinline__ float f32_trunc(double v) {
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
-  const unsigned hi = unsigned(b >> 32), lo = unsigned(b);
-  const int e = int((hi >> 20) & 0x7FFu) - 896;
-  const unsigned m = __funnelshift_r(lo, hi, 29) & 0x7FFFFFu;
-  const unsigned sgn = hi & 0x80000000u;
-  if (e <= 0) return __uint_as_float(sgn);
-  if (e >= 255) return __uint_as_float(sgn | 0x7f800000u);
-  return __uint_as_float(sgn | (unsigned(e) << 23) | m);
-}
 
 // Conductance in FP32 (a feature input only): the two reweighting forms.
 __device__ __forceinline__ float conductance32(float c, float d, float eps2, int form) {
