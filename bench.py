@@ -207,14 +207,23 @@ def make_batch(count=64, seed=4):
 
 
 def cpu_model():
+    """The host CPU's name (x86: the model name; Arm: implementer and part
+    numbers from /proc/cpuinfo, e.g. 0x41/0xd4f for Neoverse V2)."""
+    fields = {}
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
-                if line.lower().startswith(("model name", "cpu model")):
-                    return line.split(":", 1)[1].strip()
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields.setdefault(k.strip().lower(), v.strip())
     except OSError:
         pass
     import platform
+    if "model name" in fields:
+        return fields["model name"]
+    if "cpu implementer" in fields:
+        return (f"{platform.machine()} (implementer {fields['cpu implementer']}, "
+                f"part {fields.get('cpu part', '?')})")
     return platform.processor() or platform.machine()
 
 
