@@ -232,7 +232,6 @@ cudaError_t run_step_stream_mixed(Ctx& c, bool initial, int* flag_host, int64_t*
 cudaError_t launch_spmv32_once(Ctx& c);
 // mlp.cu
 bool mlp_active(const Ctx& c, bool initial);          // the step runs the MLP hooks
-const double* reweight_point(const Ctx& c, bool initial);  // x^(l-1) for gs/gt
 cudaError_t mlp_alloc(Ctx& c);
 void mlp_free(Ctx& c);
 cudaError_t mlp_init(Ctx& c, uint64_t seed);
@@ -244,7 +243,8 @@ cudaError_t mlp_predict_delta(Ctx& c, const float* feat, int64_t count, float* d
 cudaError_t mlp_time_predict(Ctx& c, const float* feat, int64_t count, float* delta, int reps,
                              double* avg_ms);
 int enqueue_mlp_pre(Ctx& c, cudaStream_t st);    // before the reweighting
-int enqueue_mlp_post(Ctx& c, cudaStream_t st);   // after it: features, candidate, choice
+int enqueue_mlp_post(Ctx& c, cudaStream_t st);   // after it: features and the learned direction
+int enqueue_mlp_start_mixed(Ctx& c, cudaStream_t st);  // mixed path, after its assembly
 int enqueue_mlp_train(Ctx& c, cudaStream_t st);  // after the solve
 // sweep.cu
 cudaError_t sweep_alloc(Ctx& c);

@@ -833,7 +833,7 @@ int enqueue_massemble(Ctx& c, cudaStream_t st, bool initial) {
   MAssemble a;
   a.cs = c.cs;
   a.ct = c.ct;
-  a.x = reweight_point(c, initial);
+  a.x = c.x;
   a.eps_list = c.eps_list;
   a.C = c.C;
   a.form = c.opt.reweight_form;
@@ -1041,6 +1041,7 @@ cudaError_t build_step_graph_mixed(Ctx& c, bool initial, cudaGraphExec_t* out, i
     n_nodes += enqueue_reweight(c, st, initial);
     if (mlp) n_nodes += enqueue_mlp_post(c, st);
     n_nodes += enqueue_massemble(c, st, initial);
+    if (mlp) n_nodes += enqueue_mlp_start_mixed(c, st);
     if (initial || !c.opt.warm_start) cudaMemsetAsync(c.x, 0, sizeof(double) * c.nt, st);
     if (e == cudaSuccess) e = add_while(st, ho, &out_node, &out_body);
   }
@@ -1098,6 +1099,7 @@ cudaError_t run_step_stream_mixed(Ctx& c, bool initial, int* flag_host, int64_t*
   k += enqueue_reweight(c, st, initial);
   if (mlp) k += enqueue_mlp_post(c, st);
   k += enqueue_massemble(c, st, initial);
+  if (mlp) k += enqueue_mlp_start_mixed(c, st);
   if (initial || !c.opt.warm_start) cudaMemsetAsync(c.x, 0, sizeof(double) * c.nt, st);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = ep;

@@ -330,10 +330,11 @@ inline int mlp_t5_grid(int64_t rows) {
 }
 
 
-// Line search along the learned direction d from x = x^(l-1): with
+// Line search of the mixed path along the learned direction d from
+// x = x^(l-1), after the assembly (its FP64 diagonal and b = g(s, .)): with
 // r = b - L~ x, the last block forms alpha = (d, r) / (d, L~ d) (0 when the
 // denominator is not positive and finite) and the energy change
-// -(d, r)^2 / (d, L~ d).
+// -(d, r)^2 / (d, L~ d).  No conductance is computed again.
 __device__ __forceinline__ void linesearch_finish(double dr, double dad, double rr, double* partials,
                                                   MlpState* M) {
   double v[3] = {dr, dad, rr}, tot[3];
@@ -348,39 +349,32 @@ __device__ __forceinline__ void linesearch_finish(double dr, double dad, double 
 
 template <int K>
 __global__ void __launch_bounds__(kThreads)
-k_linesearch_dia(DiaDesc d, const double* __restrict__ g, const double* __restrict__ cs,
-                 const double* __restrict__ ct, const double* __restrict__ x,
-                 const double* __restrict__ dir, const double* __restrict__ eps_list,
-                 const StepCounters* __restrict__ C, int form, double* partials, MlpState* M) {
+k_linesearch_dia(DiaDesc d, const double* __restrict__ g, const double* __restrict__ diag,
+                 const double* __restrict__ b, const double* __restrict__ x,
+                 const double* __restrict__ dir, double* partials, MlpState* M) {
   const int64_t nt = d.nt;
-  const double eps = eps_list[C->eps_idx];
-  const double eps2 = eps * eps;
   double dr = 0.0, dad = 0.0, rr = 0.0;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nt;
        i += int64_t(gridDim.x) * blockDim.x) {
-    const double xi = x[i], di = dir[i];
-    const double gs = conductance(cs[i], 1.0 - xi, eps2, form);
-    const double gt = conductance(ct[i], xi, eps2, form);
-    double sum = gs + gt, ax = 0.0, ad = 0.0;
+    const double xi = x[i], di = dir[i], dg = diag[i];
+    double ax = 0.0, ad = 0.0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int64_t o = d.off[k];
       if (i + o < nt) {
         const double w = g[k * nt + i];
-        sum += w;
         ax = fma(w, x[i + o], ax);
         ad = fma(w, dir[i + o], ad);
       }
       if (i >= o) {
         const double w = g[k * nt + i - o];
-        sum += w;
         ax = fma(w, x[i - o], ax);
         ad = fma(w, dir[i - o], ad);
       }
     }
-    const double r = gs - fma(sum, xi, -ax);
+    const double r = b[i] - fma(dg, xi, -ax);
     dr = fma(di, r, dr);
-    dad = fma(di, fma(sum, di, -ad), dad);
+    dad = fma(di, fma(dg, di, -ad), dad);
     rr = fma(r, r, rr);
   }
   linesearch_finish(dr, dad, rr, partials, M);
@@ -388,32 +382,25 @@ k_linesearch_dia(DiaDesc d, const double* __restrict__ g, const double* __restri
 
 __global__ void __launch_bounds__(kThreads)
 k_linesearch_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                 const double* __restrict__ g, const double* __restrict__ cs,
-                 const double* __restrict__ ct, const double* __restrict__ x,
-                 const double* __restrict__ dir, const double* __restrict__ eps_list,
-                 const StepCounters* __restrict__ C, int form, double* partials, MlpState* M,
+                 const double* __restrict__ g, const double* __restrict__ diag,
+                 const double* __restrict__ b, const double* __restrict__ x,
+                 const double* __restrict__ dir, double* partials, MlpState* M,
                  int64_t heavy_deg, const int32_t* __restrict__ heavy, int light_blocks) {
-  const double eps = eps_list[C->eps_idx];
-  const double eps2 = eps * eps;
   double dr = 0.0, dad = 0.0, rr = 0.0;
   if (int(blockIdx.x) >= light_blocks) {  // one heavy row (a hub) for the whole block
     const int64_t i = heavy[blockIdx.x - light_blocks];
-    double v[3] = {0.0, 0.0, 0.0};  // sum of g, (g, x), (g, d) over the row
+    double v[2] = {0.0, 0.0};  // (g, x), (g, d) over the row
     for (int64_t e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x) {
       const double w = g[e];
-      v[0] += w;
-      v[1] = fma(w, x[col[e]], v[1]);
-      v[2] = fma(w, dir[col[e]], v[2]);
+      v[0] = fma(w, x[col[e]], v[0]);
+      v[1] = fma(w, dir[col[e]], v[1]);
     }
-    block_sum<3>(v);
+    block_sum<2>(v);
     if (threadIdx.x == 0) {
-      const double xi = x[i], di = dir[i];
-      const double gs = conductance(cs[i], 1.0 - xi, eps2, form);
-      const double gt = conductance(ct[i], xi, eps2, form);
-      const double sum = v[0] + (gs + gt);
-      const double r = gs - fma(sum, xi, -v[1]);
+      const double xi = x[i], di = dir[i], dg = diag[i];
+      const double r = b[i] - fma(dg, xi, -v[0]);
       dr = di * r;
-      dad = di * fma(sum, di, -v[2]);
+      dad = di * fma(dg, di, -v[1]);
       rr = r * r;
     }
     linesearch_finish(dr, dad, rr, partials, M);
@@ -422,19 +409,16 @@ k_linesearch_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __re
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nt;
        i += int64_t(light_blocks) * blockDim.x) {
     if (rp[i + 1] - rp[i] > heavy_deg) continue;
-    const double xi = x[i], di = dir[i];
-    const double gs = conductance(cs[i], 1.0 - xi, eps2, form);
-    const double gt = conductance(ct[i], xi, eps2, form);
-    double sum = gs + gt, ax = 0.0, ad = 0.0;
+    const double xi = x[i], di = dir[i], dg = diag[i];
+    double ax = 0.0, ad = 0.0;
     for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
       const double w = g[e];
-      sum += w;
       ax = fma(w, x[col[e]], ax);
       ad = fma(w, dir[col[e]], ad);
     }
-    const double r = gs - fma(sum, xi, -ax);
+    const double r = b[i] - fma(dg, xi, -ax);
     dr = fma(di, r, dr);
-    dad = fma(di, fma(sum, di, -ad), dad);
+    dad = fma(di, fma(dg, di, -ad), dad);
     rr = fma(r, r, rr);
   }
   linesearch_finish(dr, dad, rr, partials, M);
@@ -709,10 +693,6 @@ bool mlp_active(const Ctx& c, bool initial) {
   return !initial && c.opt.warm_start && c.mlp_mode != 0 && c.mlp.master != nullptr;
 }
 
-const double* reweight_point(const Ctx& c, bool initial) {
-  return mlp_active(c, initial) ? c.mlp.xprev : c.x;
-}
-
 cudaError_t mlp_alloc(Ctx& c) {
   if (c.mlp.master) return cudaSuccess;
   MlpBuf& b = c.mlp;
@@ -825,18 +805,26 @@ int enqueue_mlp_post(Ctx& c, cudaStream_t st) {
   if (!predict) return 1;
   k_mlp_predict_t5<false><<<mlp_t5_grid(c.nt), 128, kT5Pad, st>>>(c.nt, b.feat, b.w16, b.dir,
                                                                    nullptr, b.state);
+  return 2;
+}
+
+// The learned start of the mixed path, after its assembly: the FP64 line
+// search on the assembled system and x += alpha d (the refinement loop then
+// forms the residual at the moved start).
+int enqueue_mlp_start_mixed(Ctx& c, cudaStream_t st) {
+  if (!(c.mlp_mode & PIRMCUT_MLP_PREDICT)) return 0;
+  MlpBuf& b = c.mlp;
+  const int grid = grid_for(c.nt);
   if (c.format == PIRMCUT_FORMAT_DIA) {
     PIRMCUT_DISPATCH_K(c.K, (k_linesearch_dia<KK><<<grid, kThreads, 0, st>>>(
-                                c.dd, c.gdia, c.cs, c.ct, c.x, b.dir, c.eps_list, c.C, form,
-                                c.partials, b.state)));
+                                c.dd, c.gdia, c.diag, c.b64, c.x, b.dir, c.partials, b.state)));
   } else {
-    k_linesearch_csr<<<grid + c.n_heavy, kThreads, 0, st>>>(c.nt, c.rp, c.col, c.gval, c.cs, c.ct,
-                                                            c.x, b.dir, c.eps_list, c.C, form,
-                                                            c.partials, b.state, c.heavy_deg,
-                                                            c.heavy, grid);
+    k_linesearch_csr<<<grid + c.n_heavy, kThreads, 0, st>>>(c.nt, c.rp, c.col, c.gval, c.diag,
+                                                            c.b64, c.x, b.dir, c.partials, b.state,
+                                                            c.heavy_deg, c.heavy, grid);
   }
   k_mlp_commit<<<grid, kThreads, 0, st>>>(c.nt, b.state, b.dir, c.x);
-  return 4;
+  return 2;
 }
 
 // After the solve of a step, with training on: iters_per_step Adam steps on

@@ -120,7 +120,7 @@ struct AssembleArgs {
   const double* cs;
   const double* ct;
   const double* x;   // start vector of the PCG
-  const double* xw;  // reweighting point x^(l-1) (terminal conductances); x unless a learned start replaced it
+  const double* xw;  // reweighting point x^(l-1) of the terminal conductances (the start x)
   const double* eps_list;
   const StepCounters* C;
   int form;
@@ -807,6 +807,156 @@ k_step_stats_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __re
 }
 
 // ---------------------------------------------------------------------------
+// learned start of the FP64 path, in the Jacobi-scaled space
+// ---------------------------------------------------------------------------
+// After the assembly and the scaling at x^(l-1): d^ = D^1/2 d, w = A^ d^ and
+// the exact minimiser of the CG energy along d^ (the same as along d in the
+// unscaled space: d^T r^ = d^T r, d^T A^ d^ = d^T L~ d),
+//   alpha = (d^, r^) / (d^, w),
+// then x^ += alpha d^, r^ -= alpha w, p = r^, and the CG state from there.
+// No conductance is computed again: the assembly's diagonal and the scaled
+// matrix serve.  alpha = 0 when the start already meets the tolerance, or
+// when the curvature is not positive and finite.
+
+// d^ = D^1/2 d = d * (diag * diag^-1/2), in place
+__global__ void __launch_bounds__(kThreads)
+k_ls_prep(int64_t nt, double* __restrict__ dir, const double* __restrict__ diag,
+          const double* __restrict__ rsd) {
+  for (int64_t i = gtid(); i < nt; i += gstride()) dir[i] *= diag[i] * rsd[i];
+}
+
+__device__ __forceinline__ void ls_scaled_finish(double dr, double dw, double* partials,
+                                                 const PcgState* S, MlpState* M) {
+  double v[2] = {dr, dw}, tot[2];
+  if (grid_sum<2>(v, partials, &M->counter, tot) && threadIdx.x == 0) {
+    const double a = tot[1] > 0.0 ? tot[0] / tot[1] : 0.0;
+    const bool ok = !S->stop_req && S->bb > 0.0 && isfinite(a) && a != 0.0;
+    M->alpha = ok ? a : 0.0;
+    M->energy_change = ok ? -tot[0] * a : 0.0;
+    M->res_plain = S->rr;  // ||b - L~ x^(l-1)||^2 from the assembly
+  }
+}
+
+// w = A^ d^ into w, (d^, r^) and (d^, w)
+template <int K>
+__global__ void __launch_bounds__(kThreads)
+k_ls_scaled_dia(DiaDesc d, const double* __restrict__ gh, const double* __restrict__ dh,
+                const double* __restrict__ rh, double* __restrict__ w, double* partials,
+                const PcgState* S, MlpState* M) {
+  const int64_t nt = d.nt;
+  double dr = 0.0, dw = 0.0;
+  for (int64_t i = gtid(); i < nt; i += gstride()) {
+    const double di = dh[i];
+    double acc = di;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int64_t o = d.off[k];
+      if (i + o < nt) acc = fma(-gh[k * nt + i], dh[i + o], acc);
+      if (i >= o) acc = fma(-gh[k * nt + i - o], dh[i - o], acc);
+    }
+    w[i] = acc;
+    dr = fma(di, rh[i], dr);
+    dw = fma(di, acc, dw);
+  }
+  ls_scaled_finish(dr, dw, partials, S, M);
+}
+
+template <int G>
+__global__ void __launch_bounds__(kThreads)
+k_ls_scaled_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                const double* __restrict__ gh, const double* __restrict__ dh,
+                const double* __restrict__ rh, double* __restrict__ w, double* partials,
+                const PcgState* S, MlpState* M, int64_t heavy_deg,
+                const int32_t* __restrict__ heavy, int light_blocks) {
+  double dr = 0.0, dw = 0.0;
+  if (int(blockIdx.x) >= light_blocks) {
+    const int64_t i = heavy[blockIdx.x - light_blocks];
+    double v[1] = {0.0};
+    for (int64_t e = rp[i] + threadIdx.x; e < rp[i + 1]; e += blockDim.x)
+      v[0] = fma(-gh[e], dh[col[e]], v[0]);
+    block_sum<1>(v);
+    if (threadIdx.x == 0) {
+      const double di = dh[i], acc = v[0] + di;
+      w[i] = acc;
+      dr = di * rh[i];
+      dw = di * acc;
+    }
+    ls_scaled_finish(dr, dw, partials, S, M);
+    return;
+  }
+  const int lane = threadIdx.x % G;
+  const unsigned mask = group_mask<G>();
+  const int64_t ng = int64_t(light_blocks) * blockDim.x / G;
+  for (int64_t i = gtid() / G; i < nt; i += ng) {
+    if (rp[i + 1] - rp[i] > heavy_deg) continue;  // the group agrees: same row
+    double acc = row_dot_neg(gh, col, dh, rp[i] + lane, rp[i + 1], G, 0.0);
+    acc = group_sum<G>(acc, mask);
+    if (lane == 0) {
+      const double di = dh[i];
+      acc += di;
+      w[i] = acc;
+      dr = fma(di, rh[i], dr);
+      dw = fma(di, acc, dw);
+    }
+  }
+  ls_scaled_finish(dr, dw, partials, S, M);
+}
+
+// x^ += alpha d^; r^ -= alpha w; p = r^; the CG state from the moved start
+// (the same sums and stopping test as the assembly).  Counts the step in M.
+__global__ void __launch_bounds__(kThreads)
+k_ls_commit(int64_t nt, const double* __restrict__ dh, const double* __restrict__ w,
+            const float* __restrict__ sq32, const double* __restrict__ diag,
+            double* __restrict__ xs, double* __restrict__ rh, double* __restrict__ p,
+            double* partials, PcgState* S, MlpState* M, cudaGraphConditionalHandle h,
+            int use_cond) {
+  const double a = M->alpha;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    M->steps += 1;
+    M->used += a != 0.0 ? 1 : 0;
+    M->sum_alpha += a;
+  }
+  if (a == 0.0) return;  // the start, its residual and the CG state stand
+  const int sh = S->rr_shift;
+  const bool fp64_norm = S->rr_fp64 != 0;
+  double rz = 0.0, rr = 0.0;
+  float rr32 = 0.0f;
+  for (int64_t i = gtid(); i < nt; i += gstride()) {
+    xs[i] = fma(a, dh[i], xs[i]);
+    const double ri = fma(-a, w[i], rh[i]);
+    rh[i] = ri;
+    p[i] = ri;
+    rz = fma(ri, ri, rz);
+    if (fp64_norm) {
+      rr = fma(diag[i] * ri, ri, rr);
+    } else {
+      const float ui = sq32[i] * abs_f32_scaled(ri, sh);
+      rr32 = fmaf(ui, ui, rr32);
+    }
+  }
+  double tot[2];
+  bool last;
+  if (fp64_norm) {
+    double v[2] = {rz, rr};
+    last = grid_sum<2>(v, partials, &S->counter[0], tot);
+  } else {
+    last = grid_sum_df(rz, rr32, partials, &S->counter[0], tot);
+  }
+  if (last && threadIdx.x == 0) {
+    const double rrt = fp64_norm ? tot[1] : ldexp(tot[1], -2 * sh);
+    S->rz = tot[0];
+    S->rr = rrt;
+    int stop = (rrt <= S->tol2 * S->bb) || S->maxit <= 0;
+    if (!isfinite(tot[0]) || !isfinite(rrt)) {
+      stop = 1;
+      S->status = PIRMCUT_ENUMERIC;
+    }
+    S->stop_req = stop;
+    if (use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // x in the caller's numbering <-> reduced x
 // ---------------------------------------------------------------------------
 
@@ -956,7 +1106,7 @@ int enqueue_prologue(Ctx& c, cudaStream_t st, bool initial, cudaGraphConditional
   a.cs = c.cs;
   a.ct = c.ct;
   a.x = c.x;
-  a.xw = reweight_point(c, initial);
+  a.xw = c.x;
   a.eps_list = c.eps_list;
   a.C = c.C;
   a.form = c.opt.reweight_form;
@@ -983,7 +1133,24 @@ int enqueue_prologue(Ctx& c, cudaStream_t st, bool initial, cudaGraphConditional
     PIRMCUT_DISPATCH_G(c.group, (k_scale_csr<GG><<<grid + c.n_heavy, kThreads, 0, st>>>(
                                     c.nt, c.rp, c.col, g, c.rsd, c.ghat, c.heavy_deg, c.heavy, grid)));
   }
-  return kernels + 2;
+  kernels += 2;
+  if (mlp && (c.mlp_mode & PIRMCUT_MLP_PREDICT)) {
+    // the learned start, in the scaled space of this step's system
+    MlpState* M = c.mlp.state;
+    k_ls_prep<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.mlp.dir, c.diag, c.rsd);
+    if (c.format == PIRMCUT_FORMAT_DIA) {
+      PIRMCUT_DISPATCH_K(c.K, (k_ls_scaled_dia<KK><<<grid, kThreads, 0, st>>>(
+                                  c.dd, c.ghat, c.mlp.dir, c.r, c.q, c.partials, c.S, M)));
+    } else {
+      PIRMCUT_DISPATCH_G(c.group, (k_ls_scaled_csr<GG><<<grid + c.n_heavy, kThreads, 0, st>>>(
+                                      c.nt, c.rp, c.col, c.ghat, c.mlp.dir, c.r, c.q, c.partials,
+                                      c.S, M, c.heavy_deg, c.heavy, grid)));
+    }
+    k_ls_commit<<<grid_for(c.nt), kThreads, 0, st>>>(c.nt, c.mlp.dir, c.q, c.sq32, c.diag, c.xs,
+                                                      c.r, c.p, c.partials, c.S, M, h, use_cond);
+    kernels += 3;
+  }
+  return kernels;
 }
 
 // One PCG iteration: spmv -> update_r -> update_xp (events, when given,
