@@ -300,11 +300,13 @@ def golden_mu_ref(name):
     return float(rec["mu_ref"]) if rec else None
 
 
-def time_to_cut(track, mu_ref, rel=1e-6):
+def time_to_cut(track, mu_ref, rel=1e-6, sweep_ms=None):
     """Device time from the start of a solve to the end of the first IRLS step
     whose sweep value is within rel of mu_ref (the sweep after each step is
     part of the step's time); the last step must be within it too, otherwise
-    not reached.  track: [(sweep value, step ms)] from x^(0) on."""
+    not reached.  track: [(sweep value, step ms)] from x^(0) on.  With
+    sweep_ms (the time of one sweep cut), also the time with a single sweep:
+    the steps up to the reached one without their sweeps, plus one."""
     if not mu_ref or not track:
         return {"ms": None, "step": None, "mu_ref": mu_ref, "reached": False}
     acc, hit = 0.0, None
@@ -314,8 +316,27 @@ def time_to_cut(track, mu_ref, rel=1e-6):
             hit = (acc, l)
     final_err = abs(track[-1][0] - mu_ref) / mu_ref
     reached = hit is not None and final_err <= rel
-    return {"ms": hit[0] if reached else None, "step": hit[1] if reached else None,
-            "solve_ms": acc, "final_rel_err": final_err, "mu_ref": mu_ref, "reached": reached}
+    r = {"ms": hit[0] if reached else None, "step": hit[1] if reached else None,
+         "solve_ms": acc, "final_rel_err": final_err, "mu_ref": mu_ref, "reached": reached}
+    if sweep_ms is not None:
+        r["sweep_ms"] = sweep_ms
+        r["ms_one_sweep"] = (hit[0] - (hit[1] + 1) * sweep_ms + sweep_ms) if reached else None
+    return r
+
+
+def sweep_time(solver, stream, reps=5):
+    """Mean time of one sweep cut of the solver's current x (CUDA events on
+    the working stream around the call; the call waits for its result)."""
+    import torch
+    solver.cut()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        solver.cut()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
 
 
 def ttc_volume(B, stream, args):
@@ -348,7 +369,8 @@ def ttc_volume(B, stream, args):
                 s.mlp_weights(w)
             s.solve(2, eps[:2])
             infos = s.solve(T, eps)
-        r = time_to_cut([(i.cut_value, i.ms) for i in infos], mu_ref)
+            sw = sweep_time(s, stream)
+        r = time_to_cut([(i.cut_value, i.ms) for i in infos], mu_ref, sweep_ms=sw)
         r["pcg_iters"] = int(sum(i.pcg_iters for i in infos))
         arms[name] = r
     base = arms["fp64"]["ms"]
@@ -447,10 +469,18 @@ def run_batch(args):
     batch = B.Batch(graphs, opt, stream=stream)
     info = batch.info()
 
+    activity = {}
+
     def bstep():
         infos = batch.solve(T, eps)
         cuts = [batch.cut(i)[1] for i in range(len(graphs))]
-        return np.array([sum(x.pcg_iters for x in inf) for inf in infos], dtype=np.float64), cuts
+        its = np.array([[x.pcg_iters for x in inf] for inf in infos], dtype=np.float64)  # [inst, step]
+        # iterations the batch ran (the slowest instance of each step) and the
+        # instance-iterations they held: their ratio is the mean number of
+        # instances active in an iteration
+        activity["batch_iters"] = float(its.max(axis=0).sum())
+        activity["instance_iters"] = float(its.sum())
+        return its.sum(axis=1), cuts
 
     for _ in range(args.warmup):
         bstep()
@@ -498,6 +528,8 @@ def run_batch(args):
                                  "tile_rows": info["tile_rows"], "tiles": info["tiles"],
                                  "warp_rows_above_deg": info["medium_deg"]},
                    "T": T, "pcg_tol": PCG_TOL, "step": "batched x0 + 50 IRLS steps + 64 sweep cuts"},
+        "cg_iterations_per_step": activity["batch_iters"],
+        "mean_active_instances_per_iteration": activity["instance_iters"] / max(activity["batch_iters"], 1.0),
         "sequential_ms_per_step": seq_ms,
         "batched_speedup_vs_sequential": seq_ms / (ms / args.steps),
         "cut_max_rel_diff_vs_sequential": rel,
@@ -750,11 +782,12 @@ def main():
         opt.track_cut = 1
         with B.Solver(g, opt, stream=stream) as s2:
             infos = s2.solve(T_STEPS, eps)
+            sweep_ms = sweep_time(s2, stream)
         return dict(ms=ms, iters=iters, job_units=job_units, refine=refine, cut=cut_value,
                     launches=launches,
                     x=x_final, spmv=(spmv_ms, spmv_bytes, spmv_flops), nt=nt, ne=ne, fmt=fmt,
                     spmv_live=(live_ms / max(live_n, 1), live_n),
-                    track=[(i.cut_value, i.ms) for i in infos],
+                    track=[(i.cut_value, i.ms) for i in infos], sweep_ms=sweep_ms,
                     clocks=clk.summary() if clk else None)
 
     r64 = timed(B.PREC_FP64, with_clocks=True) if args.only != "mixed" else None
@@ -811,7 +844,7 @@ def main():
             "refinements_per_step": rmx["refine"] / args.steps,
             "cut_value": rmx["cut"], "cut_rel_diff_vs_fp64": abs(rmx["cut"] - cut_value) / cut_value,
             "x_max_abs_diff_vs_fp64": float(np.max(np.abs(rmx["x"] - r64["x"]))),
-            "time_to_cut_1e-6": time_to_cut(rmx["track"], mu_ref),
+            "time_to_cut_1e-6": time_to_cut(rmx["track"], mu_ref, sweep_ms=rmx["sweep_ms"]),
             "gpu_launches": int(rmx["launches"]),
             "roofline": mixed_roofline(rmx),
             "dtype": "f32 inner PCG + f64 residual/refinement (same FP64 stopping test)",
@@ -891,7 +924,7 @@ def main():
             "cut_value": cut_value,
             "cut_rel_diff_vs_oracle": (abs(cut_value - mu_ref) / mu_ref) if mu_ref else None,
             "roofline": mixed_roofline(head) if only_mixed else fp64_roofline(head),
-            "time_to_cut_1e-6": time_to_cut(head["track"], mu_ref),
+            "time_to_cut_1e-6": time_to_cut(head["track"], mu_ref, sweep_ms=head["sweep_ms"]),
             "mixed": mixed,
             "time_to_cut_vol256": ttc,
             "e2e": e2e,

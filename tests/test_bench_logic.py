@@ -39,3 +39,10 @@ def test_cpu_baseline_sample_counts_iterations_and_cores():
     g = gen.config_graph(1, scale=32)
     r = bench.cpu_oracle_sample(g, budget_s=0.05, threads=2)
     assert r["cores"] == 2 and r["iters"] > 0 and r["value"] > 0 and r["kind"] == "oracle"
+
+
+def test_time_to_cut_with_one_sweep():
+    # steps of 5 ms each, 1 ms of which is the sweep: reached at step 2
+    track = [(110.0, 5.0), (101.0, 5.0), (100.0, 5.0), (100.0, 5.0)]
+    r = bench.time_to_cut(track, 100.0, sweep_ms=1.0)
+    assert r["step"] == 2 and r["ms"] == 15.0 and r["ms_one_sweep"] == 13.0
