@@ -1,6 +1,7 @@
 """Checks at full size: the benchmark's 2048x2048 segmentation grid
 (4,194,304 non-terminals, DIA storage, one CUDA graph per IRLS step, as
-bench.py times it) and the 256^3 volume (16.8M non-terminals).
+bench.py times it), the 256^3 volume (16.8M non-terminals) in FP64 and mixed
+precision, and a batch of FlowImprove-style instances of up to 10^6 vertices.
 
 Against the oracle at these sizes:
 * the sweep cut (Section 3.3): the GPU's value, prefix length k, threshold
@@ -162,17 +163,25 @@ def test_grid2048_mixed_agrees_with_fp64(P, grid):
     assert abs(x64[3] - xmx[3]) <= 1e-9 * x64[3]
 
 
-def test_vol256_against_oracle(P):
-    """The 256^3 volume (16.8M non-terminals, DIA with three offsets, float32
-    capacities): teacher-forced x^(0) and two IRLS steps against the oracle's
-    PCG iterates, the sweep cut against the oracle's sweep of the GPU's x, and
-    a free-running x^(0) + two steps at the benchmark's tolerance checked by
-    true residuals and the maximum principle."""
+@pytest.fixture(scope="module")
+def volume():
     g = gen.config_graph(3)
     prob = O.Problem.from_graph(g)
-    xs_ora = oracle_trajectory(prob, 2, O.eps_schedule(2))
+    return g, prob, oracle_trajectory(prob, 2, O.eps_schedule(2))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_vol256_against_oracle(P, volume, precision):
+    """The 256^3 volume (16.8M non-terminals, DIA with three offsets, float32
+    capacities handed over as floats): teacher-forced x^(0) and two IRLS steps
+    against the oracle's PCG iterates (FP64 and mixed precision), the sweep
+    cut against the oracle's sweep of the GPU's x, and a free-running x^(0) +
+    two steps at the benchmark's tolerance checked by true residuals and the
+    maximum principle."""
+    g, prob, xs_ora = volume
     eps = O.eps_schedule(2)
-    with P.Solver(g, pcg_tol=TF_TOL) as s:
+    opt = P.binding.pirmcut_default_options(pcg_tol=TF_TOL, precision=precision, capacity_fp32=1)
+    with P.Solver(g, opt) as s:
         assert s.problem_size()[2] == 1
         assert s.initial().status == 0
         assert np.max(np.abs(s.get_x() - xs_ora[0])) <= XTOL
@@ -181,6 +190,8 @@ def test_vol256_against_oracle(P):
             assert s.irls_step(eps[l - 1]).status == 0
             err = np.max(np.abs(s.get_x() - xs_ora[l]))
             assert err <= XTOL, (l, err)
+    if precision == 1:
+        return
     with P.Solver(g, pcg_tol=TOL) as s:
         infos = [s.initial()]
         xs = [s.get_x()]
@@ -197,3 +208,25 @@ def test_vol256_against_oracle(P):
     assert sb[prob.s] and not sb[prob.t]
     assert abs(O.cut_value(prob, sb) - value) <= 1e-12 * value
     check_sweep_against_oracle(prob, xs[-1], side, value, tau)
+
+
+def test_batch_of_large_instances_against_oracle(P):
+    """Batched FlowImprove-style instances at the sizes of the 64-instance
+    workload (Chung-Lu, 10^4 to 10^6 vertices, float32 capacities, hub rows):
+    x^(0) and two IRLS steps free-running on both sides with PCG to 1e-13 --
+    every instance's x against the oracle's (1e-9) -- and each instance's
+    sweep cut against the oracle's sweep of the GPU's x."""
+    sizes = [(1000000, 4001), (250000, 4002), (10000, 4003)]
+    graphs = [gen.chung_lu_instance(n, seed, float32_caps=True) for n, seed in sizes]
+    T = 2
+    eps = O.eps_schedule(T)
+    with P.Batch(graphs, pcg_tol=TF_TOL) as b:
+        b.solve(T, eps)
+        xs = [b.get_x(i) for i in range(len(graphs))]
+        cuts = [b.cut(i) for i in range(len(graphs))]
+    for g, x, (side, value, tau) in zip(graphs, xs, cuts):
+        prob = O.Problem.from_graph(g)
+        ref = O.irls(prob, T, eps, solver="pcg", tol=TF_TOL)[0][-1]
+        err = np.max(np.abs(x - ref))
+        assert err <= XTOL, (g.n, err)
+        check_sweep_against_oracle(prob, x, side, value, tau)
