@@ -448,7 +448,7 @@ def run_batch(args):
     """64 uneven Chung-Lu FlowImprove-style instances solved as one batch
     (one launch per kernel for all instances), against the same instances
     solved one after another with single-instance contexts."""
-    graphs = make_batch()  # worker processes start before any CUDA call
+    graphs = make_batch()[:args.batch_instances]  # worker processes start before any CUDA call
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -521,8 +521,8 @@ def run_batch(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "chunglu64: 64 Chung-Lu FlowImprove-style instances, exponent 2.5, "
-                               "avg degree 10, n log-uniform 1e4-1e6, seed 4",
+        "config": {"workload": f"chunglu64: {len(graphs)} of 64 Chung-Lu FlowImprove-style instances, "
+                               "exponent 2.5, avg degree 10, n log-uniform 1e4-1e6, seed 4",
                    "instances": len(graphs), "total_rows": info["rows"], "total_nnz": info["nnz"],
                    "autotuned": {"threads_per_row": info["threads_per_row"],
                                  "tile_rows": info["tile_rows"], "tiles": info["tiles"],
@@ -683,6 +683,8 @@ def main():
                     choices=list(WORKLOADS) + ["chunglu64", "seq128", "mlp"])
     ap.add_argument("--mlp-rows", type=int, default=16 * 1024 * 1024,
                     help="mlp: feature rows per inference launch")
+    ap.add_argument("--batch-instances", type=int, default=64,
+                    help="chunglu64: solve the first N of the 64 instances (smaller profiling case)")
     ap.add_argument("--problems", type=int, default=200, help="seq128: problems in the sequence")
     ap.add_argument("--seq-scale", type=int, default=128, help="seq128: side of the volume")
     ap.add_argument("--seq-tol", type=float, default=PCG_TOL, help="seq128: PCG tolerance")
