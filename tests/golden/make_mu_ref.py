@@ -10,7 +10,7 @@ solved by the oracle's Jacobi-PCG to ||r|| <= 1e-12 ||b||, warm-started from
 the previous iterate.  This script calls only the oracle and the seeded input
 generators; the PCG runs in the oracle's C restatement over every host core.
 
-    python tests/golden/make_mu_ref.py [grid2048] [vol256]
+    python tests/golden/make_mu_ref.py [grid64] [grid2048] [vol256]
 """
 from __future__ import annotations
 
@@ -33,7 +33,7 @@ from oracle import pcg_omp  # noqa: E402
 
 OUT = os.path.join(HERE, "mu_ref.json")
 # workload -> (generator number, IRLS steps T)
-WORKLOADS = {"grid2048": (2, 50), "vol256": (3, 30)}
+WORKLOADS = {"grid64": (1, 50), "grid2048": (2, 50), "vol256": (3, 30)}
 TOL = 1e-12
 
 
