@@ -11,6 +11,17 @@ the previous iterate.  This script calls only the oracle and the seeded input
 generators; the PCG runs in the oracle's C restatement over every host core.
 
     python tests/golden/make_mu_ref.py [grid64] [grid2048] [vol256]
+
+The sequence of related 128^3 volume problems (capacities of problem k+1 =
+those of problem k times exp(N(0, 0.01)) per edge, seed 5) gets one mu_ref per
+evaluation problem (the second half, problems 100-199) in
+tests/golden/mu_ref_seq128.json: x^(0) from zero and T = 30 IRLS steps per
+problem, each system solved by the oracle's Jacobi-PCG to ||r|| <= 1e-3 ||b||
+(the sequence's tolerance, as in the paper's warm-start experiment), each
+warm-started from the previous iterate; the file is rewritten after every
+problem, and a rerun continues after the last problem written.
+
+    python tests/golden/make_mu_ref.py seq128
 """
 from __future__ import annotations
 
@@ -32,6 +43,8 @@ import oracle as O  # noqa: E402
 from oracle import pcg_omp  # noqa: E402
 
 OUT = os.path.join(HERE, "mu_ref.json")
+OUT_SEQ = os.path.join(HERE, "mu_ref_seq128.json")
+SEQ_PROBLEMS, SEQ_T, SEQ_TOL = 200, 30, 1e-3
 # workload -> (generator number, IRLS steps T)
 WORKLOADS = {"grid64": (1, 50), "grid2048": (2, 50), "vol256": (3, 30)}
 TOL = 1e-12
@@ -74,7 +87,58 @@ def run(name):
     }
 
 
+def irls_sweeps(prob, T, tol):
+    """x^(0) from zero, then T warm-started IRLS steps; the sweep value after
+    each step and the PCG iterations of each solve."""
+    eps = O.eps_schedule(T)
+    nt = prob.nonterminals
+    x, sweeps, iters = None, [], []
+    for l in range(T + 1):
+        gl = O.initial_conductance(prob) if l == 0 else O.reweight(prob, x, eps[l - 1])
+        Lt, b = O.reduced_system(prob, O.laplacian(prob, gl))
+        v, it, rel = pcg_omp.pcg_jacobi(Lt, b, None if x is None else x[nt], tol=tol, maxit=10 ** 7)
+        if rel > tol:
+            raise RuntimeError(f"step {l}: PCG stopped at {rel:.3e}")
+        x = prob.full_x(v)
+        sweeps.append(O.sweep_cut(prob, x)["value"])
+        iters.append(it)
+    return sweeps, iters
+
+
+def run_sequence():
+    data = {"workload": "seq128", "generator": "gen.config_graph(5), gen.capacity_sequence(seed=5, sigma=0.01)",
+            "problems": SEQ_PROBLEMS, "evaluation": [SEQ_PROBLEMS // 2, SEQ_PROBLEMS - 1], "T": SEQ_T,
+            "eps": "max(0.1 * 2^-(l-1), 1e-6)",
+            "pcg": f"oracle Jacobi-PCG, tol {SEQ_TOL}, x^(0) from zero, steps warm-started",
+            "command": "python tests/golden/make_mu_ref.py seq128", "mu_ref": {}}
+    if os.path.exists(OUT_SEQ):
+        with open(OUT_SEQ) as f:
+            data = json.load(f)
+    base = gen.config_graph(5)
+    t0 = time.time()
+    for k, c in enumerate(gen.capacity_sequence(base, SEQ_PROBLEMS, seed=5, sigma=0.01)):
+        if k < SEQ_PROBLEMS // 2 or str(k) in data["mu_ref"]:
+            continue
+        prob = O.Problem.from_graph(gen.Graph(base.n, base.row_ptr, base.col, c, base.s, base.t))
+        sweeps, iters = irls_sweeps(prob, SEQ_T, SEQ_TOL)
+        mu = sweeps[-1]
+        first = next(l for l in range(len(sweeps))
+                     if all(abs(v - mu) <= 1e-6 * mu for v in sweeps[l:]))
+        data["mu_ref"][str(k)] = {"mu_ref": mu, "first_step_within_1e-6_for_good": first,
+                                  "pcg_iters": int(sum(iters)), "pcg_iters_x0": int(iters[0])}
+        data["host"] = f"{platform.machine()}, {pcg_omp.max_threads()} OpenMP threads"
+        data["date"] = datetime.date.today().isoformat()
+        with open(OUT_SEQ, "w") as f:
+            json.dump(data, f, indent=1)
+            f.write("\n")
+        print(f"seq128 problem {k}: mu_ref {mu:.12g}, step {first}, {sum(iters)} PCG iterations "
+              f"({time.time() - t0:.0f} s)", flush=True)
+
+
 def main(argv):
+    if argv == ["seq128"]:
+        run_sequence()
+        return 0
     names = argv or list(WORKLOADS)
     data = {}
     if os.path.exists(OUT):
