@@ -22,6 +22,8 @@ warm-started from the previous iterate; the file is rewritten after every
 problem, and a rerun continues after the last problem written.
 
     python tests/golden/make_mu_ref.py seq128
+    python tests/golden/make_mu_ref.py seq128 A B    # problems A..B-1 into a part file
+    python tests/golden/make_mu_ref.py seq128-merge  # fold the part files in
 """
 from __future__ import annotations
 
@@ -105,19 +107,22 @@ def irls_sweeps(prob, T, tol):
     return sweeps, iters
 
 
-def run_sequence():
+def run_sequence(lo=SEQ_PROBLEMS // 2, hi=SEQ_PROBLEMS):
+    out = OUT_SEQ if (lo, hi) == (SEQ_PROBLEMS // 2, SEQ_PROBLEMS) else OUT_SEQ[:-5] + f".part{lo}-{hi}.json"
     data = {"workload": "seq128", "generator": "gen.config_graph(5), gen.capacity_sequence(seed=5, sigma=0.01)",
             "problems": SEQ_PROBLEMS, "evaluation": [SEQ_PROBLEMS // 2, SEQ_PROBLEMS - 1], "T": SEQ_T,
             "eps": "max(0.1 * 2^-(l-1), 1e-6)",
             "pcg": f"oracle Jacobi-PCG, tol {SEQ_TOL}, x^(0) from zero, steps warm-started",
             "command": "python tests/golden/make_mu_ref.py seq128", "mu_ref": {}}
-    if os.path.exists(OUT_SEQ):
-        with open(OUT_SEQ) as f:
+    if os.path.exists(out):
+        with open(out) as f:
             data = json.load(f)
     base = gen.config_graph(5)
     t0 = time.time()
     for k, c in enumerate(gen.capacity_sequence(base, SEQ_PROBLEMS, seed=5, sigma=0.01)):
-        if k < SEQ_PROBLEMS // 2 or str(k) in data["mu_ref"]:
+        if k >= hi:
+            break
+        if k < lo or str(k) in data["mu_ref"]:
             continue
         prob = O.Problem.from_graph(gen.Graph(base.n, base.row_ptr, base.col, c, base.s, base.t))
         sweeps, iters = irls_sweeps(prob, SEQ_T, SEQ_TOL)
@@ -128,16 +133,37 @@ def run_sequence():
                                   "pcg_iters": int(sum(iters)), "pcg_iters_x0": int(iters[0])}
         data["host"] = f"{platform.machine()}, {pcg_omp.max_threads()} OpenMP threads"
         data["date"] = datetime.date.today().isoformat()
-        with open(OUT_SEQ, "w") as f:
+        with open(out, "w") as f:
             json.dump(data, f, indent=1)
             f.write("\n")
         print(f"seq128 problem {k}: mu_ref {mu:.12g}, step {first}, {sum(iters)} PCG iterations "
               f"({time.time() - t0:.0f} s)", flush=True)
 
 
+def merge_sequence_parts():
+    """Fold the part files of run_sequence into tests/golden/mu_ref_seq128.json."""
+    import glob
+    with open(OUT_SEQ) as f:
+        data = json.load(f)
+    parts = sorted(glob.glob(OUT_SEQ[:-5] + ".part*.json"))
+    for path in parts:
+        with open(path) as f:
+            data["mu_ref"].update(json.load(f)["mu_ref"])
+    data["mu_ref"] = {k: data["mu_ref"][k] for k in sorted(data["mu_ref"], key=int)}
+    with open(OUT_SEQ, "w") as f:
+        json.dump(data, f, indent=1)
+        f.write("\n")
+    for path in parts:
+        os.remove(path)
+    print(f"seq128: {len(data['mu_ref'])} problems")
+
+
 def main(argv):
-    if argv == ["seq128"]:
-        run_sequence()
+    if argv and argv[0] == "seq128":
+        run_sequence(*[int(a) for a in argv[1:3]])
+        return 0
+    if argv == ["seq128-merge"]:
+        merge_sequence_parts()
         return 0
     names = argv or list(WORKLOADS)
     data = {}
