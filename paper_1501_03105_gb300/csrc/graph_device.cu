@@ -274,28 +274,25 @@ k_pack_dia(int64_t nt, int K, Offsets os, const int64_t* __restrict__ rrp,
 }
 
 // sum of cs in the order the host reduction uses: kSumChunks fixed chunks, a
-// warp per chunk whose lane j runs over the elements a + j, a + j + 32, ...;
-// the lane sums in lane order, then the chunk sums in order.  One block of
-// kSumThreads threads.
-constexpr int kSumThreads = 1024;
-__global__ void __launch_bounds__(kSumThreads)
-k_sum_chunks(const double* __restrict__ v, int64_t n, double* __restrict__ out) {
-  __shared__ double part[kSumChunks];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int ch = w; ch < kSumChunks; ch += kSumThreads / 32) {
-    const int64_t a = n * ch / kSumChunks, b = n * (ch + 1) / kSumChunks;
-    double acc = 0.0;
-    for (int64_t i = a + lane; i < b; i += 32) acc += v[i];
-    double s = 0.0;
-    for (int j = 0; j < 32; ++j) s += __shfl_sync(0xffffffffu, acc, j);
-    if (lane == 0) part[ch] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < kSumChunks; ++k) s += part[k];
-    *out = s;
-  }
+// warp per chunk (one block each, spread over the SMs) whose lane j runs over
+// the elements a + j, a + j + 32, ...; the lane sums in lane order; then
+// k_sum_parts adds the chunk sums in order.
+__global__ void __launch_bounds__(32)
+k_sum_chunks(const double* __restrict__ v, int64_t n, double* __restrict__ part) {
+  const int lane = threadIdx.x, ch = blockIdx.x;
+  const int64_t a = n * ch / kSumChunks, b = n * (ch + 1) / kSumChunks;
+  double acc = 0.0;
+  for (int64_t i = a + lane; i < b; i += 32) acc += v[i];
+  double s = 0.0;
+  for (int j = 0; j < 32; ++j) s += __shfl_sync(0xffffffffu, acc, j);
+  if (lane == 0) part[ch] = s;
+}
+
+__global__ void k_sum_parts(const double* __restrict__ part, double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double s = 0.0;
+  for (int k = 0; k < kSumChunks; ++k) s += part[k];
+  *out = s;
 }
 
 template <class T>
@@ -341,7 +338,7 @@ pirmcut_status reduce_graph_device(int64_t n, const int64_t* row_ptr, const int3
   float* d_c32 = nullptr;     // float capacities uploaded from the host
   double* d_cs_s = nullptr;
   double* d_ct_t = nullptr;
-  double* d_small = nullptr;  // [cst_s, cst_t, sum]
+  double* d_small = nullptr;  // [cst_s, cst_t, sum, -, kSumChunks chunk sums]
   unsigned int* d_flags = nullptr;
   unsigned long long* d_off = nullptr;
   cudaError_t e = cudaSuccess;
@@ -422,7 +419,7 @@ pirmcut_status reduce_graph_device(int64_t n, const int64_t* row_ptr, const int3
   // ---- per-row pass
   if ((e = dmalloc(&d_cnt, size_t(nt))) != cudaSuccess || (e = dmalloc(&out.cs, size_t(nt))) != cudaSuccess ||
       (e = dmalloc(&out.ct, size_t(nt))) != cudaSuccess || (e = dmalloc(&d_cs_s, size_t(nt))) != cudaSuccess ||
-      (e = dmalloc(&d_ct_t, size_t(nt))) != cudaSuccess || (e = dmalloc(&d_small, 4)) != cudaSuccess ||
+      (e = dmalloc(&d_ct_t, size_t(nt))) != cudaSuccess || (e = dmalloc(&d_small, 4 + kSumChunks)) != cudaSuccess ||
       (e = dmalloc(&d_flags, 1)) != cudaSuccess)
     return cuda_error(e, "cudaMalloc");
   cudaMemsetAsync(d_flags, 0, sizeof(unsigned int), st);
@@ -458,7 +455,8 @@ pirmcut_status reduce_graph_device(int64_t n, const int64_t* row_ptr, const int3
                                                       d_ct_t, d_small, d_flags);
   k_check<<<grid_for(nt), kThreads, 0, st>>>(nt, out.rp, out.col, out.cval, out.cs, out.ct, d_cs_s,
                                              d_ct_t, d_flags);
-  k_sum_chunks<<<1, kSumThreads, 0, st>>>(out.cs, nt, d_small + 2);
+  k_sum_chunks<<<kSumChunks, 32, 0, st>>>(out.cs, nt, d_small + 4);
+  k_sum_parts<<<1, 32, 0, st>>>(d_small + 4, d_small + 2);
   double small[4] = {0, 0, 0, 0};
   if ((e = cudaGetLastError()) != cudaSuccess ||
       (e = cudaMemcpyAsync(&flags, d_flags, sizeof(flags), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
