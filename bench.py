@@ -302,6 +302,17 @@ def golden_mu_ref(name):
     return float(rec["mu_ref"]) if rec else None
 
 
+def sequence_mu_ref(side, problems, tol):
+    """The oracle's mu_ref of each evaluation problem of the sequence workload
+    ({problem index: value}), written by tests/golden/make_mu_ref.py for the
+    default sequence only (128^3, 200 problems, PCG tolerance 1e-3); {} for
+    any other sequence."""
+    if (side, problems, tol) != (128, 200, 1e-3) or not os.path.exists(MU_REF_SEQ_JSON):
+        return {}
+    with open(MU_REF_SEQ_JSON) as f:
+        return {int(k): float(v["mu_ref"]) for k, v in json.load(f)["mu_ref"].items()}
+
+
 def time_to_cut(track, mu_ref, rel=1e-6, sweep_ms=None):
     """Device time from the start of a solve to the end of the first IRLS step
     whose sweep value is within rel of mu_ref (the sweep after each step is
@@ -592,11 +603,7 @@ def run_sequence(args):
     train_iters = []
     stats = {k: {"iters": [], "iters0": [], "ms": [], "ttc": [], "cut": [], "alpha": [], "dE": [],
                  "err": []} for k in arms}
-    # the oracle's mu_ref of each evaluation problem (the default sequence only)
-    seq_ref = {}
-    if (W_side, P, args.seq_tol) == (128, 200, 1e-3) and os.path.exists(MU_REF_SEQ_JSON):
-        with open(MU_REF_SEQ_JSON) as f:
-            seq_ref = {int(k): v["mu_ref"] for k, v in json.load(f)["mu_ref"].items()}
+    seq_ref = sequence_mu_ref(W_side, P, args.seq_tol)
     n_oracle_ref = 0
     log_ratio = {}
     t_start = time.perf_counter()

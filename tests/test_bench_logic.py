@@ -46,3 +46,30 @@ def test_time_to_cut_with_one_sweep():
     track = [(110.0, 5.0), (101.0, 5.0), (100.0, 5.0), (100.0, 5.0)]
     r = bench.time_to_cut(track, 100.0, sweep_ms=1.0)
     assert r["step"] == 2 and r["ms"] == 15.0 and r["ms_one_sweep"] == 13.0
+
+
+def test_sequence_reference_values_on_file():
+    """Every evaluation problem of the default sequence (100-199) has the
+    oracle's mu_ref; other sequences have none (the bench then falls back to
+    the plain FP64 arm's final cut and says so)."""
+    ref = bench.sequence_mu_ref(128, 200, 1e-3)
+    assert sorted(ref) == list(range(100, 200))
+    assert all(v > 0 for v in ref.values())
+    assert bench.sequence_mu_ref(64, 200, 1e-3) == {}
+    assert bench.sequence_mu_ref(128, 20, 1e-3) == {}
+    assert bench.sequence_mu_ref(128, 200, 1e-10) == {}
+
+
+def test_golden_reference_files_name_their_oracle_runs():
+    """The stored reference values come from the committed oracle script:
+    each file names the command that wrote it."""
+    import json
+    with open(bench.MU_REF_JSON) as f:
+        d = json.load(f)
+    assert set(d) >= {"grid64", "grid2048", "vol256"}
+    for name, rec in d.items():
+        assert rec["command"] == f"python tests/golden/make_mu_ref.py {name}"
+        assert rec["steps"][-1]["sweep_value"] == rec["mu_ref"]
+    with open(bench.MU_REF_SEQ_JSON) as f:
+        seq = json.load(f)
+    assert seq["command"] == "python tests/golden/make_mu_ref.py seq128"
