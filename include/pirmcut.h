@@ -460,7 +460,11 @@ pirmcut_status pirmcut_batch_get_x(pirmcut_batch* b, int index, double* x);
 pirmcut_status pirmcut_batch_info(const pirmcut_batch* b, int64_t* total_rows, int64_t* total_nnz,
                                   int* threads_per_row, int* tile_rows, int* tiles,
                                   int64_t* medium_deg);
+/* Kernels the batch has launched so far (creation's autotuner included; the
+ * kernels of a graph launch are counted by its structure).  0 for NULL. */
 int64_t pirmcut_batch_kernel_launches(const pirmcut_batch* b);
+/* Free every host and device resource of the batch (after its stream's work
+ * has finished).  NULL is ignored. */
 void pirmcut_batch_destroy(pirmcut_batch* b);
 
 /* Text of the last error of ctx (or of the last failed create when ctx is NULL). */
