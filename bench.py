@@ -709,6 +709,8 @@ def main():
                     choices=list(WORKLOADS) + ["chunglu64", "seq128", "mlp"])
     ap.add_argument("--mlp-rows", type=int, default=16 * 1024 * 1024,
                     help="mlp: feature rows per inference launch")
+    ap.add_argument("--fuse-reweight", action="store_true",
+                    help="FP64 DIA steps: conductances formed inside the assembly pass")
     ap.add_argument("--batch-instances", type=int, default=64,
                     help="chunglu64: solve the first N of the 64 instances (smaller profiling case)")
     ap.add_argument("--problems", type=int, default=200, help="seq128: problems in the sequence")
@@ -756,7 +758,8 @@ def main():
     def timed(precision, with_clocks):
         """Warm-up, then K timed steps of one path; returns its measurements."""
         opt = B.pirmcut_default_options(pcg_tol=PCG_TOL, graph_launch=int(args.launch == "graph"),
-                                        precision=precision, inner_tol=args.inner_tol)
+                                        precision=precision, inner_tol=args.inner_tol,
+                                        fuse_reweight=int(args.fuse_reweight))
         solver = B.Solver(g, opt, stream=stream)
 
         def step():
@@ -959,7 +962,8 @@ def main():
                               f"per-iteration traffic {bytes_iter / 1e6:.2f} MB fits in the 129 MB L2, not "
                               "flushed: a parity-size configuration, L2-resident by design"),
                        "parallelism": f"{ws} independent instance(s), one per GPU",
-                       "launch": args.launch},
+                       "launch": args.launch,
+                       "reweight": "fused into the assembly" if args.fuse_reweight else "own pass"},
             "pcg_iters_per_step": iters / args.steps,
             "cut_value": cut_value,
             "cut_rel_diff_vs_oracle": (abs(cut_value - mu_ref) / mu_ref) if mu_ref else None,

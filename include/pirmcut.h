@@ -114,6 +114,14 @@ typedef struct {
                           exactly to FP64 by the library: the problem is the
                           same as for the doubles of equal value.  Batches
                           take doubles.                                      */
+  int fuse_reweight;   /* 1: FP64 steps on DIA storage form the conductances
+                          (Eq. define-reweight-vector) inside the assembly
+                          pass instead of a pass of their own, each edge's
+                          twice (once per endpoint row): the same values and
+                          results bit for bit, more FP64 work, one pass fewer.
+                          Ignored on CSR, in mixed precision and while the
+                          learned start predicts (it reads the conductances
+                          first).  0 (default): separate passes.             */
 } pirmcut_options;
 
 typedef struct {

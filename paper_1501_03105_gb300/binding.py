@@ -37,7 +37,8 @@ class Options(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("time_spmv", ctypes.c_int),
                 ("reduce_on_host", ctypes.c_int), ("batch_threads_per_row", ctypes.c_int),
                 ("batch_tile_rows", ctypes.c_int), ("batch_medium_deg", ctypes.c_int),
-                ("step_stats", ctypes.c_int), ("capacity_fp32", ctypes.c_int)]
+                ("step_stats", ctypes.c_int), ("capacity_fp32", ctypes.c_int),
+                ("fuse_reweight", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):

@@ -488,6 +488,7 @@ void pirmcut_default_options(pirmcut_options* opt) {
   opt->batch_medium_deg = 0;
   opt->step_stats = 0;
   opt->capacity_fp32 = 0;
+  opt->fuse_reweight = 0;
 }
 
 pirmcut_status pirmcut_create(int64_t n, const int64_t* row_ptr, const int32_t* col,

@@ -246,6 +246,52 @@ k_assemble_dia(DiaDesc d, const double* __restrict__ g, AssembleArgs a) {
   assemble_finish(a, rz, rr, bb, nbad);
 }
 
+// Step 1 and the assembly in one pass (options.fuse_reweight, FP64 DIA
+// steps): row i forms the conductances of its upper edges and stores them, as
+// k_reweight_dia does, and forms those of its lower edges again (their own
+// rows store them) from the same operands in the same order -- the same
+// values bit for bit -- then assembles the row as k_assemble_dia does.  Each
+// edge's conductance is formed twice (more FP64 work) for one pass fewer
+// over the conductances.
+template <int K>
+__global__ void __launch_bounds__(kThreads, 4)
+k_reweight_assemble_dia(DiaDesc d, const double* __restrict__ cap, double* __restrict__ g,
+                        AssembleArgs a) {
+  const int64_t nt = d.nt;
+  const double eps = a.eps_list[a.C->eps_idx];
+  const double eps2 = eps * eps;
+  const double* __restrict__ x = a.x;
+  double rz = 0.0, rr = 0.0, bb = 0.0, nbad = 0.0;
+  for (int64_t i = gtid(); i < nt; i += gstride()) {
+    const double xi = x[i];
+    const double wi = a.xw[i];
+    const double gs = conductance(a.cs[i], 1.0 - wi, eps2, a.form);
+    const double gt = conductance(a.ct[i], wi, eps2, a.form);
+    double sum = gs + gt, ax = 0.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int64_t o = d.off[k];
+      double gu = 0.0;
+      if (i + o < nt) {
+        const double xj = x[i + o];
+        gu = conductance(cap[k * nt + i], xi - xj, eps2, a.form);
+        sum += gu;
+        ax = fma(gu, xj, ax);
+      }
+      g[k * nt + i] = gu;
+      if (i >= o) {
+        const double xj = x[i - o];
+        const double gl = conductance(cap[k * nt + i - o], xj - xi, eps2, a.form);
+        sum += gl;
+        ax = fma(gl, xj, ax);
+      }
+    }
+    const double ri = a.zero_start ? gs : gs - fma(sum, xi, -ax);
+    assemble_store(a, i, sum, ri, xi, gs, rz, rr, bb, nbad);
+  }
+  assemble_finish(a, rz, rr, bb, nbad);
+}
+
 template <int G>
 __global__ void __launch_bounds__(kThreads, 4)
 k_assemble_csr(int64_t nt, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
@@ -1100,7 +1146,9 @@ int enqueue_prologue(Ctx& c, cudaStream_t st, bool initial, cudaGraphConditional
   double* g = c.format == PIRMCUT_FORMAT_DIA ? c.gdia : c.gval;
   *err = enqueue_stats_pre(c, st);
   int kernels = mlp ? enqueue_mlp_pre(c, st) : 0;
-  kernels += enqueue_reweight(c, st, initial);
+  // the learned start reads this step's conductances before the assembly
+  const bool fused = !initial && !mlp && c.opt.fuse_reweight && c.format == PIRMCUT_FORMAT_DIA;
+  if (!fused) kernels += enqueue_reweight(c, st, initial);
   if (mlp) kernels += enqueue_mlp_post(c, st);
   AssembleArgs a;
   a.cs = c.cs;
@@ -1125,7 +1173,11 @@ int enqueue_prologue(Ctx& c, cudaStream_t st, bool initial, cudaGraphConditional
   a.h = h;
   a.use_cond = use_cond;
   if (c.format == PIRMCUT_FORMAT_DIA) {
-    PIRMCUT_DISPATCH_K(c.K, (k_assemble_dia<KK><<<grid, kThreads, 0, st>>>(c.dd, g, a)));
+    if (fused) {
+      PIRMCUT_DISPATCH_K(c.K, (k_reweight_assemble_dia<KK><<<grid, kThreads, 0, st>>>(c.dd, c.cdia, g, a)));
+    } else {
+      PIRMCUT_DISPATCH_K(c.K, (k_assemble_dia<KK><<<grid, kThreads, 0, st>>>(c.dd, g, a)));
+    }
     PIRMCUT_DISPATCH_K(c.K, (k_scale_dia<KK><<<grid, kThreads, 0, st>>>(c.dd, g, c.rsd, c.ghat)));
   } else {
     PIRMCUT_DISPATCH_G(c.group, (k_assemble_csr<GG><<<grid + c.n_heavy, kThreads, 0, st>>>(

@@ -576,6 +576,36 @@ def test_track_cut_records_each_step(P):
         assert abs(info.cut_value - ref["value"]) <= CUT_RTOL * ref["value"]
 
 
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("make", [lambda: gen.config_graph(1), lambda: gen.config_graph(3, scale=9)],
+                         ids=["grid64", "vol9"])
+def test_fused_reweight_assembly_is_the_same_computation(P, make, form):
+    """options.fuse_reweight forms each row's conductances inside the
+    assembly pass (Eq. define-reweight-vector, Eq. reweighted-laplacian; the
+    lower edges formed again from the same operands): every iterate,
+    iteration count, step statistic and the cut equal the separate passes'
+    bit for bit, with graph and host launches; and x against the oracle."""
+    g = make()
+    T = 8
+    eps = O.eps_schedule(T)
+    runs = []
+    for fuse in (0, 1):
+        for launch in (1, 0):
+            with solver(P, g, format=1, reweight_form=form, step_stats=1, fuse_reweight=fuse,
+                        graph_launch=launch) as s:
+                assert s.problem_size()[2] == 1
+                infos = s.solve(T, eps)
+                side, value, tau = s.cut()
+                runs.append((s.get_x(), [(i.pcg_iters, i.rel_residual, i.objective, i.flow_value)
+                                         for i in infos], value, tau))
+    x0, st0, v0, t0 = runs[0]
+    for x, st, v, t in runs[1:]:
+        assert np.array_equal(x, x0) and st == st0 and v == v0 and t == t0
+    prob = O.Problem.from_graph(g)
+    xo, _ = O.irls(prob, T, eps, form=form)
+    assert np.max(np.abs(x0 - xo[-1])) <= 1e-9
+
+
 @pytest.mark.parametrize("fmt", [0, 2])
 def test_stream_launch_matches_graph_launch(P, fmt):
     """The same kernels launched from the host (graph_launch = 0) give
