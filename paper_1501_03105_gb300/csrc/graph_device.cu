@@ -488,7 +488,8 @@ pirmcut_status reduce_graph_device(int64_t n, const int64_t* row_ptr, const int3
       }
     }
     if (dia_ok && K > 0) {
-      std::sort(offs, offs + K);
+      for (int a = 1; a < K; ++a)  // ascending; K <= kMaxDiag
+        for (int b = a; b > 0 && offs[b - 1] > offs[b]; --b) std::swap(offs[b - 1], offs[b]);
       dia_ok = double(mnt / 2) / (double(K) * double(nt)) >= 0.5;
     }
     if (K == 0) dia_ok = false;

@@ -350,7 +350,8 @@ pirmcut_status reduce_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
     }
   }
   if (dia_ok && K > 0) {
-    std::sort(offs, offs + K);
+    for (int a = 1; a < K; ++a)  // ascending; K <= kMaxDiag
+      for (int b = a; b > 0 && offs[b - 1] > offs[b]; --b) std::swap(offs[b - 1], offs[b]);
     const double fill = double(g.n_edges) / (double(K) * double(nt));
     dia_ok = fill >= 0.5;
   }

@@ -792,7 +792,6 @@ int enqueue_mlp_post(Ctx& c, cudaStream_t st) {
   const int grid = grid_for(c.nt);
   const int form = c.opt.reweight_form;
   const bool predict = (c.mlp_mode & PIRMCUT_MLP_PREDICT) != 0;
-  const int keep_feat = (c.mlp_mode & PIRMCUT_MLP_TRAIN) ? 1 : 0;
   if (c.format == PIRMCUT_FORMAT_DIA) {
     PIRMCUT_DISPATCH_K(c.K, (k_features_dia32<KK><<<grid, kThreads, 0, st>>>(
                                 c.dd, c.gdia, b.gprev, c.cs, c.ct, c.x, c.eps_list, c.C, form,
