@@ -107,25 +107,32 @@ def irls_sweeps(prob, T, tol):
     return sweeps, iters
 
 
-def run_sequence(lo=SEQ_PROBLEMS // 2, hi=SEQ_PROBLEMS):
-    out = OUT_SEQ if (lo, hi) == (SEQ_PROBLEMS // 2, SEQ_PROBLEMS) else OUT_SEQ[:-5] + f".part{lo}-{hi}.json"
+def run_sequence(lo=None, hi=None, base=None, problems=SEQ_PROBLEMS, T=SEQ_T, tol=SEQ_TOL,
+                 main=OUT_SEQ):
+    """The sequence's evaluation problems lo..hi-1 (default: the second half)
+    into ``main``, or into a part file next to it when a range is given.
+    ``base`` (default: the 128^3 volume, gen.config_graph(5)), ``problems``,
+    ``T`` and ``tol`` are there so that a test can run a small sequence."""
+    lo = problems // 2 if lo is None else lo
+    hi = problems if hi is None else hi
+    out = main if (lo, hi) == (problems // 2, problems) else main[:-5] + f".part{lo}-{hi}.json"
     data = {"workload": "seq128", "generator": "gen.config_graph(5), gen.capacity_sequence(seed=5, sigma=0.01)",
-            "problems": SEQ_PROBLEMS, "evaluation": [SEQ_PROBLEMS // 2, SEQ_PROBLEMS - 1], "T": SEQ_T,
+            "problems": problems, "evaluation": [problems // 2, problems - 1], "T": T,
             "eps": "max(0.1 * 2^-(l-1), 1e-6)",
-            "pcg": f"oracle Jacobi-PCG, tol {SEQ_TOL}, x^(0) from zero, steps warm-started",
+            "pcg": f"oracle Jacobi-PCG, tol {tol}, x^(0) from zero, steps warm-started",
             "command": "python tests/golden/make_mu_ref.py seq128", "mu_ref": {}}
     if os.path.exists(out):
         with open(out) as f:
             data = json.load(f)
-    base = gen.config_graph(5)
+    base = gen.config_graph(5) if base is None else base
     t0 = time.time()
-    for k, c in enumerate(gen.capacity_sequence(base, SEQ_PROBLEMS, seed=5, sigma=0.01)):
+    for k, c in enumerate(gen.capacity_sequence(base, problems, seed=5, sigma=0.01)):
         if k >= hi:
             break
         if k < lo or str(k) in data["mu_ref"]:
             continue
         prob = O.Problem.from_graph(gen.Graph(base.n, base.row_ptr, base.col, c, base.s, base.t))
-        sweeps, iters = irls_sweeps(prob, SEQ_T, SEQ_TOL)
+        sweeps, iters = irls_sweeps(prob, T, tol)
         mu = sweeps[-1]
         first = next(l for l in range(len(sweeps))
                      if all(abs(v - mu) <= 1e-6 * mu for v in sweeps[l:]))
@@ -140,17 +147,18 @@ def run_sequence(lo=SEQ_PROBLEMS // 2, hi=SEQ_PROBLEMS):
               f"({time.time() - t0:.0f} s)", flush=True)
 
 
-def merge_sequence_parts():
-    """Fold the part files of run_sequence into tests/golden/mu_ref_seq128.json."""
+def merge_sequence_parts(main=OUT_SEQ):
+    """Fold the part files of run_sequence into ``main``
+    (tests/golden/mu_ref_seq128.json)."""
     import glob
-    with open(OUT_SEQ) as f:
+    with open(main) as f:
         data = json.load(f)
-    parts = sorted(glob.glob(OUT_SEQ[:-5] + ".part*.json"))
+    parts = sorted(glob.glob(main[:-5] + ".part*.json"))
     for path in parts:
         with open(path) as f:
             data["mu_ref"].update(json.load(f)["mu_ref"])
     data["mu_ref"] = {k: data["mu_ref"][k] for k in sorted(data["mu_ref"], key=int)}
-    with open(OUT_SEQ, "w") as f:
+    with open(main, "w") as f:
         json.dump(data, f, indent=1)
         f.write("\n")
     for path in parts:
